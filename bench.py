@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 sparse permutation / extraction / assignment path.
+
+Headline workload (printed as `value`): permutation at scale -- R-MAT (a,b,c,d) =
+(0.57, 0.19, 0.19, 0.05), scale 25 (33,554,432 rows), edge factor 16, symmetrised,
+duplicates merged, int64 row pointer, int32 columns, fp32 values.  One step applies the
+three permutations of that workload: P A P^T with a random p, P A P^T with the
+degree-descending p, and P A Q^T with independent random p, q.  Metric: output
+entries per second (whole job), inputs resident in HBM (each far larger than L2).
+
+Extra measured operations (key "ops"): extraction at scale (Erdos-Renyi n = 2^26,
+32 draws/row; A(I, J) with random distinct |I| = |J| = n/2) and assignment at scale
+(R-MAT scale 26, edge factor 24; A(I, J) = B with B an ER 2^22 x 2^22 matrix, 8/row,
+random distinct I, J of 2^22).
+
+`--impl reference` times the CPU oracle (the reference arm of this build) on a bounded
+sample of the same workload.  Under torchrun every rank runs an independent replica
+(the path has no exchange step on one GPU), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output nnz/s & %HBM peak for permute/extract/assign; served p50/p99 vs plain"
+UNIT = "output nnz/s"
+WORKLOAD = ("R-MAT scale 25 (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, symmetrised; "
+            "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=25, help="R-MAT scale of the headline workload")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extraction/assignment ops")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SP_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------
+def permute_workload(scale: int, device):
+    import torch
+    import synth
+    A = synth.rmat_csr(scale, 16, (0.57, 0.19, 0.19, 0.05), seed=0, symmetrize=True,
+                       value_kind="f32u01", rowptr_dtype=torch.int64, colidx_dtype=torch.int32,
+                       device=device)
+    n = A.nrows
+    p = synth.random_permutation(n, 1, 0, device=device)
+    pdeg = synth.degree_descending_permutation(A.rowptr)
+    q = synth.random_permutation(n, 1, 1, device=device)
+    return A, [("PAPt_random", p, p), ("PAPt_degree", pdeg, pdeg), ("PAQt_random", p, q)]
+
+
+def row_classes(rowptr):
+    """Entries / non-empty rows handled by the tile (<=2048), long and huge (>8192) kernels."""
+    import torch
+    L = (rowptr[1:] - rowptr[:-1]).to(torch.int64)
+    small = L <= 2048
+    huge = L > 8192
+    long_ = (~small) & (~huge)
+    out = {}
+    for name, m in (("tile", small), ("long", long_), ("huge", huge)):
+        out[name] = (int(L[m].sum()), int(((L > 0) & m).sum()))
+    return out
+
+
+def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs):
+    """Per-phase algorithmic bytes over measured phase time."""
+    e_tile, r_tile = classes["tile"]
+    e_long, r_long = classes["long"]
+    e_huge, _ = classes["huge"]
+    per_op = {
+        # 16 B/entry (read col+val, write col+val) + 28 B/row (p, rowptr pair, row start)
+        "tile": 16 * e_tile + 28 * r_tile,
+        "long": 16 * e_long + 28 * r_long + 16 * e_huge,
+        "huge": 16 * e_huge,
+        "scan": 28 * m,
+        "map": 8 * n,
+        "partition": 8 * m,
+    }
+    launches_total = ops_per_step * steps
+    best = None
+    for ph, (ms, cnt) in stats.items():
+        if cnt == 0 or ms <= 0:
+            continue
+        if best is None or ms > best[1]:
+            best = (ph, ms, cnt)
+    ph, ms, cnt = best
+    byts = per_op.get(ph, 0) * launches_total
+    achieved = byts / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": f"k_{ph}", "achieved": round(achieved, 1),
+            "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+            "traffic": None, "launches": cnt, "avg_launch_ms": round(ms / cnt, 4),
+            "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
+
+
+def time_steps(fn, steps, warmup, ws):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(s)
+    for _ in range(steps):
+        fn()
+    ev[1].record(s)
+    torch.cuda.synchronize()
+    barrier(ws)
+    return ev[0].elapsed_time(ev[1])
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2509_20776_gb300 import CSR, Context, SP_OPT_TIMING
+    dev = torch.device("cuda", local)
+    ctx = Context(local)
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    A, ops = permute_workload(args.scale, dev)
+    Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
+    nnz, m = A.nnz, A.nrows
+    outs = [ctx.sp_permute(Ad, p, q, sync=True) for _, p, q in ops]  # also validates
+
+    def step():
+        for (_, p, q), B in zip(ops, outs):
+            ctx.lib.sp_permute(ctx.handle, __import__("ctypes").byref(Ad.desc()),
+                               _p(p), _p(q), _it(p), __import__("ctypes").byref(B.desc()),
+                               _st())
+
+    import ctypes
+
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _it(t):
+        return 0 if t.dtype == torch.int32 else 1
+
+    def _st():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    classes = row_classes(A.rowptr)
+    # timed region: device-resident inputs, outputs preallocated
+    ctx.phase_stats(reset=True)
+    ctx.set_option(SP_OPT_TIMING, 1)
+    with Clocks(local) as clk:
+        ms = time_steps(step, args.steps, args.warmup, ws)
+    ctx.sync()
+    ctx.set_option(SP_OPT_TIMING, 0)
+    stats = ctx.phase_stats(reset=True)
+    # the phase timers include the warm-up steps: scale launches to timed steps only
+    total_steps = args.steps + args.warmup
+    stats_timed = {k: (v[0] * args.steps / total_steps, v[1] * args.steps // total_steps)
+                   for k, v in stats.items()}
+    launches_per_step = sum(v[1] for v in stats.values()) / total_steps
+    ms = max_over_ranks(ms, ws)
+    out_per_step = nnz * len(ops)
+    value = out_per_step * args.steps * ws / (ms * 1e-3)
+    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm)
+    alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols  # SURVEY 8(d) permutation formula
+    op_frac = alg_bytes_op * len(ops) * args.steps / (ms * 1e-3) / 1e9 / hbm
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 indices / fp32 values moved as 32-bit words",
+        "data": "synthetic (seeded R-MAT; the paper's SuiteSparse graphs are not available)",
+        "config": {"workload": WORKLOAD, "rows": m, "nnz": nnz, "ops_per_step": len(ops),
+                   "l2": "inputs larger than L2 (no flush needed)",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": roof,
+        "op_roofline": {"bytes_per_op": alg_bytes_op, "frac": round(op_frac, 4),
+                        "peak": hbm, "unit": "GB/s", "note": "whole op, algorithmic bytes"},
+        "row_classes": {k: {"entries": v[0], "rows": v[1]} for k, v in classes.items()},
+        "clocks": clk.summary(),
+        "peak_source": "measured (MEASURED_PEAKS.json)" if pk else "fallback",
+    }
+    # ---- end to end through the public API with host buffers -----------------------
+    if not args.no_e2e:
+        result["e2e"] = e2e_permute(ctx, A, ops, args, ws)
+    # ---- extra operations -------------------------------------------------------------
+    del outs
+    if not args.no_extra:
+        ops_res = {}
+        try:
+            ops_res["extract"] = bench_extract(ctx, args, dev, hbm, ws)
+        except Exception as e:  # noqa: BLE001
+            ops_res["extract"] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            ops_res["assign"] = bench_assign(ctx, args, dev, hbm, ws)
+        except Exception as e:  # noqa: BLE001
+            ops_res["assign"] = {"error": repr(e)[:300]}
+        result["ops"] = ops_res
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args)
+    ctx.close()
+    return result
+
+
+def e2e_permute(ctx, A, ops, args, ws):
+    """Host-resident inputs: H2D of A and p/q, the three ops, D2H of every result."""
+    import torch
+    from paper_2509_20776_gb300 import CSR
+    hA = [t.cpu().pin_memory() for t in (A.rowptr, A.colidx, A.values)]
+    hperm = [(p.cpu().pin_memory(), q.cpu().pin_memory() if q is not p else None)
+             for _, p, q in ops]
+    out_rp = torch.empty_like(hA[0], pin_memory=True)
+    out_ci = torch.empty_like(hA[1], pin_memory=True)
+    out_v = torch.empty_like(hA[2], pin_memory=True)
+    dev = A.rowptr.device
+    dA = [torch.empty_like(t, device=dev) for t in hA]
+    dperm = [(torch.empty_like(p, device=dev), torch.empty_like(q, device=dev) if q is not None
+              else None) for p, q in hperm]
+    h2d = sum(t.numel() * t.element_size() for t in hA) + sum(
+        p.numel() * p.element_size() + (q.numel() * q.element_size() if q is not None else 0)
+        for p, q in hperm)
+    d2h = len(ops) * (out_rp.numel() * 8 + out_ci.numel() * 4 + out_v.numel() * 4)
+
+    def step():
+        for d, h in zip(dA, hA):
+            d.copy_(h, non_blocking=True)
+        Ad = CSR(A.nrows, A.ncols, dA[0], dA[1], dA[2])
+        for (dp, dq), (hp, hq) in zip(dperm, hperm):
+            dp.copy_(hp, non_blocking=True)
+            if dq is not None:
+                dq.copy_(hq, non_blocking=True)
+            B = ctx.sp_permute(Ad, dp, dq if dq is not None else dp, sync=False)
+            out_rp.copy_(B.rowptr, non_blocking=True)
+            out_ci.copy_(B.colidx, non_blocking=True)
+            out_v.copy_(B.values, non_blocking=True)
+
+    steps = max(1, args.steps // 2)
+    ms = time_steps(step, steps, 1, ws)
+    ctx.sync()
+    ms = max_over_ranks(ms, ws)
+    value = A.nnz * len(ops) * steps * ws / (ms * 1e-3)
+    return {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(ms / steps, 3)}
+
+
+def bench_extract(ctx, args, dev, hbm, ws):
+    import torch
+    import synth
+    from paper_2509_20776_gb300 import CSR
+    n = 1 << 26
+    A = synth.er_csr(n, n, 32, seed=0, value_kind="f32u01", rowptr_dtype=torch.int64,
+                     colidx_dtype=torch.int32, device=dev)
+    I = synth.random_subset(n, n // 2, 3, 1, device=dev)
+    J = synth.random_subset(n, n // 2, 3, 2, device=dev)
+    Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
+    B = ctx.sp_extract(Ad, I, J)
+    nnz_out = B.nnz
+    del B
+    ctx.phase_stats(reset=True)
+
+    def step():
+        ctx.sp_extract(Ad, I, J, sync=False)
+
+    steps = max(1, args.steps // 2)
+    ms = time_steps(step, steps, 1, ws)
+    ctx.sync()
+    ms = max_over_ranks(ms, ws)
+    # nnz_sel*sc + nnz_out*(sv+sc+sv) + |I|(s_i+2 sr) + |J| s_i + n s_i + |J| s_i + |I| sr
+    L = (A.rowptr[1:] - A.rowptr[:-1])
+    nnz_sel = int(L[I.long()].sum())
+    ab = nnz_sel * 4 + nnz_out * 12 + (n // 2) * (4 + 16) + (n // 2) * 4 + n * 4 + (n // 2) * 4 + (n // 2) * 8
+    frac = ab * steps / (ms * 1e-3) / 1e9 / hbm
+    value = nnz_out * steps * ws / (ms * 1e-3)
+    return {"workload": "ER n=2^26, 32 draws/row; A(I,J), random distinct |I|=|J|=2^25",
+            "nnz_in": A.nnz, "nnz_out": nnz_out, "value": round(value, 1), "unit": UNIT,
+            "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
+            "alg_bytes_per_op": ab}
+
+
+def bench_assign(ctx, args, dev, hbm, ws):
+    import torch
+    import synth
+    from paper_2509_20776_gb300 import CSR
+    A = synth.rmat_csr(26, 24, (0.57, 0.19, 0.19, 0.05), seed=0, symmetrize=False,
+                       value_kind="f32u01", rowptr_dtype=torch.int64, colidx_dtype=torch.int32,
+                       device=dev)
+    k = 1 << 22
+    Bm = synth.er_csr(k, k, 8, seed=1, value_kind="f32u01", rowptr_dtype=torch.int64,
+                      colidx_dtype=torch.int32, device=dev)
+    I = synth.random_subset(A.nrows, k, 4, 1, device=dev)
+    J = synth.random_subset(A.ncols, k, 4, 2, device=dev)
+    Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
+    Bd = CSR(Bm.nrows, Bm.ncols, Bm.rowptr, Bm.colidx, Bm.values)
+    Ap = ctx.sp_assign(Ad, I, J, Bd)
+    nnz_out = Ap.nnz
+    # extract-after-assign returns B bit-exactly
+    E = ctx.sp_extract(CSR(Ap.nrows, Ap.ncols, Ap.rowptr, Ap.colidx, Ap.values), I, J)
+    roundtrip = bool(torch.equal(E.rowptr, Bd.rowptr) and torch.equal(E.colidx, Bd.colidx) and
+                     torch.equal(E.values.view(torch.int32), Bd.values.view(torch.int32)))
+    del Ap, E
+
+    def step():
+        ctx.sp_assign(Ad, I, J, Bd, sync=False)
+
+    steps = max(1, args.steps // 2)
+    ms = time_steps(step, steps, 1, ws)
+    ctx.sync()
+    ms = max_over_ranks(ms, ws)
+    m = A.nrows
+    ab = A.nnz * 8 + nnz_out * 8 + 2 * (m + 1) * 8 + Bm.nnz * 8 + (k + 1) * 8 + k * 4 + k * 4 + m * 4 + A.ncols // 8
+    frac = ab * steps / (ms * 1e-3) / 1e9 / hbm
+    value = nnz_out * steps * ws / (ms * 1e-3)
+    return {"workload": "R-MAT scale 26 ef 24; A(I,J)=B, B ER 2^22 x 2^22 8/row, random I,J",
+            "nnz_in": A.nnz, "nnz_B": Bm.nnz, "nnz_out": nnz_out, "value": round(value, 1),
+            "unit": UNIT, "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
+            "alg_bytes_per_op": ab, "extract_after_assign_equals_B": roundtrip}
+
+
+# ---------------------------------------------------------------------------------------
+CPU_SCALE = 20
+
+
+def _cpu_sample(scale, seed_perm, device):
+    """The headline generator at a smaller scale, copied to host numpy for the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    A = synth.rmat_csr(scale, 16, (0.57, 0.19, 0.19, 0.05), seed=0, symmetrize=True,
+                       value_kind="f32u01", device=device)
+    O = oracle.CSR.of(A.nrows, A.ncols, A.rowptr.cpu().numpy(), A.colidx.cpu().numpy(),
+                      A.values.cpu().numpy())
+    p = synth.random_permutation(A.nrows, seed_perm, 0, device=device).cpu().numpy()
+    pd = synth.degree_descending_permutation(A.rowptr).cpu().numpy()
+    q = synth.random_permutation(A.nrows, seed_perm, 1, device=device).cpu().numpy()
+    del np, torch
+    return O, [(p, p), (pd, pd), (p, q)]
+
+
+def cpu_baseline(args):
+    """The oracle (numpy, as it stands) on host cores, one P A P^T on a scale-20 sample."""
+    import oracle
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    O, perms = _cpu_sample(CPU_SCALE, 1, dev)
+    p, q = perms[0]
+    t = time.perf_counter()
+    B = oracle.permute(O, p, q)
+    dt = time.perf_counter() - t
+    return {"value": round(B.nnz / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {CPU_SCALE} (same a,b,c,d, edge factor 16, symmetrised, "
+                      f"{O.nnz} nnz), one P A P^T with a random p, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample per step (scale-18 R-MAT)."""
+    import oracle
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    scale = 18
+    O, perms = _cpu_sample(scale, 1, dev)
+
+    def step():
+        for p, q in perms:
+            oracle.permute(O, p, q)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = O.nnz * len(perms) * args.steps / dt
+    sample = (f"R-MAT scale {scale} (same a,b,c,d, edge factor 16, symmetrised, {O.nnz} nnz); "
+              "each step the three permutations of the workload")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64 indices / fp32 values",
+            "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    res = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * sp.h -- C ABI of the GB300 library for sparse matrix permutation, extraction and
+ * assignment on CSR matrices (arXiv 2509.20776: HipPerm, HipExtract, HipAssign).
+ *
+ * Conventions for every entry point
+ *  - Indices are 0-based (the paper writes them 1-based).
+ *  - All array pointers are DEVICE pointers of the context's device unless a
+ *    parameter says "host".  Scalars and descriptors (sp_csr) live in host memory.
+ *  - Every call is stream-ordered on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) and returns without waiting for the GPU unless it says
+ *    "synchronises".  Inputs must stay valid and unmodified until the work is done.
+ *  - Host-detectable errors (null pointers, shapes, types, sizes) are returned
+ *    immediately and nothing is launched.  Errors found on the device (index out of
+ *    range, repeated index, p not a permutation, look-back timeout) are recorded in
+ *    the context and returned by the next synchronising call on it (sp_ctx_sync,
+ *    sp_extract_count, sp_assign_count, ...); the outputs of the failed call are then
+ *    unspecified.
+ *  - A context's workspace is shared by all calls made through it: calls through one
+ *    context must be ordered (same stream, or synchronised between streams).  Use one
+ *    context per concurrently used stream.
+ *  - Matrices are canonical CSR: row pointer non-decreasing from 0 to nnz, column
+ *    indices in [0, ncols) and strictly ascending within each row.  Inputs are
+ *    assumed canonical (check with sp_csr_validate); outputs always are.
+ *  - Values are moved as opaque 4- or 8-byte words: no arithmetic touches them
+ *    (except SP_ASSIGN_PLUS), so -0.0, NaN payloads and stored zeros are preserved.
+ */
+#ifndef SP_H_
+#define SP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sp_stream_t; /* identical to cudaStream_t */
+
+/* Width of row pointers, column indices and index vectors. */
+typedef enum sp_itype { SP_I32 = 0, SP_I64 = 1 } sp_itype;
+/* Width of values: fp32 or fp64 (moved as 4- or 8-byte words). */
+typedef enum sp_vtype { SP_F32 = 0, SP_F64 = 1 } sp_vtype;
+
+typedef enum sp_status {
+  SP_OK = 0,
+  SP_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, inconsistent descriptor */
+  SP_ERR_SHAPE = 2,           /* dimensions or vector lengths do not match */
+  SP_ERR_INDEX_RANGE = 3,     /* an index vector entry lies outside its dimension */
+  SP_ERR_DUPLICATE_INDEX = 4, /* an index vector that must be distinct repeats a value */
+  SP_ERR_NOT_PERMUTATION = 5, /* p or q is not a permutation of its dimension */
+  SP_ERR_NOT_CANONICAL = 6,   /* an input matrix is not canonical CSR (sp_csr_validate) */
+  SP_ERR_OVERFLOW = 7,        /* a result does not fit the requested index width */
+  SP_ERR_OOM = 8,             /* the allocator returned NULL */
+  SP_ERR_TIMEOUT = 9,         /* a bounded device-side wait gave up (no hang) */
+  SP_ERR_CUDA = 10,           /* a CUDA runtime call failed */
+  SP_ERR_INTERNAL = 11        /* an internal invariant failed (a library bug) */
+} sp_status;
+
+/* How sp_assign combines B with the region A(I, J) (Sec. 2.3, "Variants of matrix
+ * assignment"). */
+typedef enum sp_assign_mode {
+  SP_ASSIGN_REPLACE = 0,   /* overwrite: A(I,J) is cleared, then B is written; afterwards
+                              A'(I,J) == B exactly */
+  SP_ASSIGN_SELECT2ND = 1, /* A (+) P B Q^T with select-second: A's entries inside the
+                              region that B does not store survive; B wins ties */
+  SP_ASSIGN_PLUS = 2       /* A (+) P B Q^T with arithmetic add (one IEEE add) */
+} sp_assign_mode;
+
+/* A CSR matrix descriptor (host struct, device arrays).
+ *   rowptr: nrows+1 entries of rowptr_type; colidx: nnz entries of colidx_type;
+ *   values: nnz entries of value_type. */
+typedef struct sp_csr {
+  int64_t nrows, ncols, nnz;
+  sp_itype rowptr_type;
+  sp_itype colidx_type;
+  sp_vtype value_type;
+  void* rowptr;
+  void* colidx;
+  void* values;
+} sp_csr;
+
+/* Device-memory allocator hook.  alloc returns device memory usable on `stream` (or
+ * NULL on failure); free releases it after the work queued on `stream`.  A NULL
+ * allocator in sp_ctx_create selects stream-ordered cudaMallocAsync/cudaFreeAsync. */
+typedef struct sp_allocator {
+  void* (*alloc)(void* user, size_t bytes, sp_stream_t stream);
+  void (*free)(void* user, void* ptr, size_t bytes, sp_stream_t stream);
+  void* user;
+} sp_allocator;
+
+typedef struct sp_ctx sp_ctx;   /* device, allocator, workspace, device error record */
+typedef struct sp_plan sp_plan; /* state kept between a count call and its fill call */
+
+/* Human-readable name of a status code (static string, never NULL). */
+SP_API const char* sp_status_str(sp_status s);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+SP_API int sp_version(void);
+
+/* Create a context on CUDA device `device`.  `allocator` may be NULL (see
+ * sp_allocator); it is copied.  *ctx receives the new context.
+ * Errors: SP_ERR_INVALID_ARG (ctx NULL), SP_ERR_CUDA (device unusable). */
+SP_API sp_status sp_ctx_create(sp_ctx** ctx, int device, const sp_allocator* allocator);
+
+/* Destroy a context: waits for the device, frees its workspace.  NULL is a no-op. */
+SP_API sp_status sp_ctx_destroy(sp_ctx* ctx);
+
+/* Synchronises `stream`, then returns and clears the first device-detected error
+ * recorded since the last synchronising call (SP_OK if none). */
+SP_API sp_status sp_ctx_sync(sp_ctx* ctx, sp_stream_t stream);
+
+/* Host: detail of the last error returned by a synchronising call (for index errors
+ * the offending position in the index vector; -1 if none). */
+SP_API int64_t sp_ctx_error_detail(const sp_ctx* ctx);
+
+/* Tuning and test knobs (values < 0 restore the default):
+ *   SP_OPT_SPIN_LIMIT      polls a look-back wait makes before it gives up with
+ *                          SP_ERR_TIMEOUT (default 1<<22, each poll sleeps ~100 ns);
+ *   SP_OPT_SCAN_HOLD_TILE  test hook: the scan tile with this index never publishes
+ *                          its status, so its successors' bounded waits run out and
+ *                          the call reports SP_ERR_TIMEOUT (default -1 = off);
+ *   SP_OPT_VALIDATE        1: every op first checks its input matrices are canonical
+ *                          (SP_ERR_NOT_CANONICAL); default 0. */
+typedef enum sp_option {
+  SP_OPT_SPIN_LIMIT = 0,
+  SP_OPT_SCAN_HOLD_TILE = 1,
+  SP_OPT_VALIDATE = 2,
+  SP_OPT_TIMING = 3 /* 1: bracket every kernel launch with CUDA events (see below) */
+} sp_option;
+SP_API sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value);
+
+/* Per-phase kernel statistics (tracing).  Every kernel the library launches belongs to
+ * one phase; the context counts launches per phase always, and with SP_OPT_TIMING=1
+ * also records CUDA events around each launch on the launching stream.
+ * sp_ctx_phase_stats waits for the recorded events, then writes SP_NUM_PHASES entries
+ * to ms[] (summed device milliseconds) and launches[] (host arrays, either may be
+ * NULL); reset != 0 clears the totals afterwards. */
+typedef enum sp_phase {
+  SP_PHASE_MAP = 0,       /* inverse maps, membership bitmaps, range checks */
+  SP_PHASE_COUNT = 1,     /* kept-entry counting passes */
+  SP_PHASE_SCAN = 2,      /* exclusive scans (row pointers) */
+  SP_PHASE_PARTITION = 3, /* tile partition / row classification */
+  SP_PHASE_TILE = 4,      /* gather + relabel + sort of short rows, many per CTA */
+  SP_PHASE_LONG = 5,      /* rows / runs of up to 8192 entries, one CTA each */
+  SP_PHASE_HUGE = 6,      /* key-range partition of longer rows */
+  SP_PHASE_GATHER = 7,    /* load-balanced row copy (identity map, assignment assembly) */
+  SP_PHASE_OTHER = 8,     /* row-pointer width conversion, validation */
+  SP_NUM_PHASES = 9
+} sp_phase;
+SP_API sp_status sp_ctx_phase_stats(sp_ctx* ctx, double* ms, int64_t* launches, int reset);
+/* Static name of a phase ("map", "count", ...; "?" when out of range). */
+SP_API const char* sp_phase_name(int phase);
+
+/* ------------------------------------------------------------------------------
+ * Permutation  (Sec. 2.1; HipPerm, Algorithm 1)
+ *   B[i, j] = A[p[i], q[j]], i.e. B = P A Q^T with P[i, p[i]] = 1, Q[j, q[j]] = 1.
+ *   p: A->nrows entries (new row -> old row), q: A->ncols entries (new column -> old
+ *   column), both of idx_type; NULL means the identity.  q == p (same pointer) with a
+ *   square A is the symmetric reordering P A P^T.
+ *   B (host descriptor): on entry B->rowptr_type selects the output row-pointer width;
+ *   colidx_type/value_type are taken from A.  If B->rowptr, B->colidx and B->values
+ *   are all NULL the library allocates them through the context allocator (release
+ *   with sp_csr_free); otherwise all three must be caller-owned device buffers of at
+ *   least nrows+1 / nnz / nnz entries.  On return B's shape fields are set.
+ *   Errors: SP_ERR_INVALID_ARG, SP_ERR_SHAPE, SP_ERR_OVERFLOW (nnz does not fit an
+ *   int32 B->rowptr); on the device SP_ERR_INDEX_RANGE / SP_ERR_NOT_PERMUTATION.
+ * ------------------------------------------------------------------------------ */
+SP_API sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, const void* q,
+                     sp_itype idx_type, sp_csr* B, sp_stream_t stream);
+
+/* ------------------------------------------------------------------------------
+ * Extraction  (Sec. 2.2; HipExtract, Algorithms 3 and 5)
+ *   B = A(I, J): B[i, j] = A[I[i], J[j]] for (i, j) in I x J; B is nI x nJ.
+ *   I: nI row indices (may repeat, any order); J: nJ column indices (distinct, any
+ *   order; unsorted J permutes the columns of the result).  Both of idx_type.
+ *
+ * sp_extract_count: builds the column map and the row pointer of B, and returns the
+ *   number of stored entries of B in *nnz_out (host).  Synchronises.  *plan receives
+ *   the state needed by sp_extract_fill; it borrows A, I and J, which must stay valid
+ *   until the plan is destroyed.
+ * sp_extract_fill: writes B (same allocation rule as sp_permute; B->nnz must be the
+ *   counted value when caller-owned).  The plan can be filled more than once.
+ * sp_extract: count + allocate + fill in one call (synchronises once).
+ *   Errors: SP_ERR_INVALID_ARG, SP_ERR_SHAPE, SP_ERR_OVERFLOW; from the device
+ *   SP_ERR_INDEX_RANGE, SP_ERR_DUPLICATE_INDEX (repeated J).
+ * ------------------------------------------------------------------------------ */
+SP_API sp_status sp_extract_count(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                           const void* J, int64_t nJ, sp_itype idx_type, sp_plan** plan,
+                           int64_t* nnz_out, sp_stream_t stream);
+SP_API sp_status sp_extract_fill(sp_ctx* ctx, sp_plan* plan, sp_csr* B, sp_stream_t stream);
+SP_API sp_status sp_extract(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI, const void* J,
+                     int64_t nJ, sp_itype idx_type, sp_csr* B, sp_stream_t stream);
+
+/* ------------------------------------------------------------------------------
+ * Assignment  (Sec. 2.3; HipAssign, Algorithm 4)
+ *   A' = A with A'(I, J) = B (REPLACE), or A (+) P B Q^T (SELECT2ND, PLUS); A is not
+ *   modified.  I: nI distinct rows of A, J: nJ distinct columns of A (any order), both
+ *   of idx_type; B: nI x nJ, with A's colidx and value types.
+ *   The count/fill/one-shot split, plan lifetime and output allocation rules are those
+ *   of extraction (the plan also borrows B).
+ *   Errors: SP_ERR_INVALID_ARG, SP_ERR_SHAPE, SP_ERR_OVERFLOW; from the device
+ *   SP_ERR_INDEX_RANGE, SP_ERR_DUPLICATE_INDEX.
+ * ------------------------------------------------------------------------------ */
+SP_API sp_status sp_assign_count(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                          const void* J, int64_t nJ, sp_itype idx_type, const sp_csr* B,
+                          sp_assign_mode mode, sp_plan** plan, int64_t* nnz_out,
+                          sp_stream_t stream);
+SP_API sp_status sp_assign_fill(sp_ctx* ctx, sp_plan* plan, sp_csr* Aprime, sp_stream_t stream);
+SP_API sp_status sp_assign(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI, const void* J,
+                    int64_t nJ, sp_itype idx_type, const sp_csr* B, sp_assign_mode mode,
+                    sp_csr* Aprime, sp_stream_t stream);
+
+/* Release a plan (stream-ordered on the stream of its last call).  NULL is a no-op. */
+SP_API sp_status sp_plan_destroy(sp_ctx* ctx, sp_plan* plan);
+
+/* Release the arrays of a library-allocated matrix and zero its pointers. */
+SP_API sp_status sp_csr_free(sp_ctx* ctx, sp_csr* M);
+
+/* ------------------------------------------------------------------------------
+ * Steps of the path, callable on their own
+ * ------------------------------------------------------------------------------ */
+
+/* Inverse index map (the index/value swap of the Identify step, Sec. 3.1 Step 1(a):
+ * pvec[pvec_inv[i]] = i; with -1 for absent positions, the sparse form of Sec. 4):
+ *   inv[idx[k]] = k for k < len, inv[x] = -1 for every other x in [0, n).
+ *   idx: len entries, inv: n entries, both of idx_type.  require_permutation != 0 also
+ *   demands len == n (host check) so that idx is a permutation.
+ *   Errors: host SP_ERR_SHAPE; device SP_ERR_INDEX_RANGE, SP_ERR_DUPLICATE_INDEX or
+ *   SP_ERR_NOT_PERMUTATION. */
+SP_API sp_status sp_inverse_map(sp_ctx* ctx, const void* idx, int64_t len, int64_t n,
+                         sp_itype idx_type, void* inv, int require_permutation,
+                         sp_stream_t stream);
+
+/* Exclusive prefix sum (the proc_pointer / thread_offset prefix sums of Algorithm 2,
+ * Fig. 3(ii), which become the output row pointer on one GPU):
+ *   out[i] = sum_{k<i} in[k] for i = 0..len (out has len+1 entries; out[len] = total).
+ *   in: len entries of in_type (non-negative); out: of out_type.  Single-pass
+ *   decoupled look-back scan; in and out must not overlap.
+ *   Errors: host SP_ERR_INVALID_ARG; device SP_ERR_OVERFLOW (int32 out overflows),
+ *   SP_ERR_TIMEOUT (a look-back wait exceeded SP_OPT_SPIN_LIMIT). */
+SP_API sp_status sp_exclusive_scan(sp_ctx* ctx, const void* in, sp_itype in_type, int64_t len,
+                            void* out, sp_itype out_type, sp_stream_t stream);
+
+/* Kept-entry counts of an extraction (the first, counting pass of Algorithm 5):
+ *   counts[i] = #{ k in row I[i] of A : colidx[k] is an entry of J }  (int64, nI).
+ *   J must be distinct.  Errors as sp_extract. */
+SP_API sp_status sp_kept_counts(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                         const void* J, int64_t nJ, sp_itype idx_type, int64_t* counts,
+                         sp_stream_t stream);
+
+/* Sort every row of M by column, in place, moving values with their columns (the
+ * Build step's sort, Sec. 3.1 Step 3).  Column indices must be distinct within each
+ * row and in [0, M->ncols).  Errors: SP_ERR_INVALID_ARG, SP_ERR_OVERFLOW (ncols too
+ * large for the 32-bit sort keys). */
+SP_API sp_status sp_sort_rows(sp_ctx* ctx, sp_csr* M, sp_stream_t stream);
+
+/* Check that A is canonical CSR.  Synchronises; returns SP_ERR_NOT_CANONICAL (detail:
+ * offending row) or SP_OK. */
+SP_API sp_status sp_csr_validate(sp_ctx* ctx, const sp_csr* A, sp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP_H_ */

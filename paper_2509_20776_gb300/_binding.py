@@ -1,0 +1,304 @@
+"""ctypes binding of the C ABI in ``include/sp.h`` (argument marshalling only).
+
+Every function here converts torch tensors to device pointers and sizes, calls the
+entry point of the same name in ``libspgb.so`` and turns a non-zero status into
+``SpError``.  No step of the path runs in Python: if the shared library is missing
+the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspgb.so")
+
+SP_I32, SP_I64 = 0, 1
+SP_F32, SP_F64 = 0, 1
+SP_ASSIGN_REPLACE, SP_ASSIGN_SELECT2ND, SP_ASSIGN_PLUS = 0, 1, 2
+SP_OPT_SPIN_LIMIT, SP_OPT_SCAN_HOLD_TILE, SP_OPT_VALIDATE, SP_OPT_TIMING = 0, 1, 2, 3
+PHASES = ["map", "count", "scan", "partition", "tile", "long", "huge", "gather", "other"]
+STATUS = ["SP_OK", "SP_ERR_INVALID_ARG", "SP_ERR_SHAPE", "SP_ERR_INDEX_RANGE",
+          "SP_ERR_DUPLICATE_INDEX", "SP_ERR_NOT_PERMUTATION", "SP_ERR_NOT_CANONICAL",
+          "SP_ERR_OVERFLOW", "SP_ERR_OOM", "SP_ERR_TIMEOUT", "SP_ERR_CUDA", "SP_ERR_INTERNAL"]
+
+
+class SpError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: int = -1):
+        name = STATUS[code] if 0 <= code < len(STATUS) else f"status {code}"
+        super().__init__(f"{where}: {name}" + (f" (detail {detail})" if detail != -1 else ""))
+        self.code = code
+        self.name = name
+        self.detail = detail
+
+
+class sp_csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr_type", ctypes.c_int), ("colidx_type", ctypes.c_int),
+                ("value_type", ctypes.c_int), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_PCSR = ctypes.POINTER(sp_csr)
+SIGNATURES = {
+    "sp_status_str": (ctypes.c_char_p, [_int]),
+    "sp_version": (_int, []),
+    "sp_ctx_create": (_int, [ctypes.POINTER(_vp), _int, _vp]),
+    "sp_ctx_destroy": (_int, [_vp]),
+    "sp_ctx_sync": (_int, [_vp, _vp]),
+    "sp_ctx_error_detail": (_i64, [_vp]),
+    "sp_ctx_set_option": (_int, [_vp, _int, _i64]),
+    "sp_permute": (_int, [_vp, _PCSR, _vp, _vp, _int, _PCSR, _vp]),
+    "sp_extract_count": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(_vp),
+                                ctypes.POINTER(_i64), _vp]),
+    "sp_extract_fill": (_int, [_vp, _vp, _PCSR, _vp]),
+    "sp_extract": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _vp]),
+    "sp_assign_count": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _int,
+                               ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp]),
+    "sp_assign_fill": (_int, [_vp, _vp, _PCSR, _vp]),
+    "sp_assign": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _int, _PCSR, _vp]),
+    "sp_plan_destroy": (_int, [_vp, _vp]),
+    "sp_csr_free": (_int, [_vp, _PCSR]),
+    "sp_inverse_map": (_int, [_vp, _vp, _i64, _i64, _int, _vp, _int, _vp]),
+    "sp_exclusive_scan": (_int, [_vp, _vp, _int, _i64, _vp, _int, _vp]),
+    "sp_kept_counts": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _vp, _vp]),
+    "sp_sort_rows": (_int, [_vp, _PCSR, _vp]),
+    "sp_csr_validate": (_int, [_vp, _PCSR, _vp]),
+    "sp_ctx_phase_stats": (_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _int]),
+    "sp_phase_name": (ctypes.c_char_p, [_int]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libspgb.so (built by ``paper_2509_20776_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run paper_2509_20776_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _itype(dtype: torch.dtype) -> int:
+    if dtype == torch.int32:
+        return SP_I32
+    if dtype == torch.int64:
+        return SP_I64
+    raise TypeError(f"index tensors must be int32 or int64, got {dtype}")
+
+
+def _vtype(dtype: torch.dtype) -> int:
+    if dtype == torch.float32:
+        return SP_F32
+    if dtype == torch.float64:
+        return SP_F64
+    raise TypeError(f"values must be float32 or float64, got {dtype}")
+
+
+_ITORCH = {SP_I32: torch.int32, SP_I64: torch.int64}
+_VTORCH = {SP_F32: torch.float32, SP_F64: torch.float64}
+
+
+def _ptr(t):
+    return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class CSR:
+    """CSR matrix whose arrays are CUDA tensors (rowptr/colidx int32|int64, values f32|f64)."""
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+    values: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    def desc(self) -> sp_csr:
+        for t in (self.rowptr, self.colidx, self.values):
+            if not t.is_contiguous():
+                raise ValueError("CSR arrays must be contiguous")
+        return sp_csr(self.nrows, self.ncols, self.nnz, _itype(self.rowptr.dtype),
+                      _itype(self.colidx.dtype), _vtype(self.values.dtype),
+                      ctypes.c_void_p(self.rowptr.data_ptr()) if self.rowptr.numel() else None,
+                      _ptr(self.colidx), _ptr(self.values))
+
+
+class Context:
+    """Owns an ``sp_ctx`` (workspace, device error record) for one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = load_library()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        h = ctypes.c_void_p()
+        self._check(self.lib.sp_ctx_create(ctypes.byref(h), device, None), "sp_ctx_create")
+        self.handle = h
+
+    def _check(self, code: int, where: str):
+        if code != 0:
+            detail = self.lib.sp_ctx_error_detail(self.handle) if getattr(self, "handle", None) else -1
+            raise SpError(code, where, detail)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: int, value: int):
+        self._check(self.lib.sp_ctx_set_option(self.handle, key, value), "sp_ctx_set_option")
+
+    def phase_stats(self, reset: bool = False) -> dict:
+        """{phase: (device ms, kernel launches)} accumulated since the last reset."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self._check(self.lib.sp_ctx_phase_stats(self.handle, ms, cnt, 1 if reset else 0),
+                    "sp_ctx_phase_stats")
+        return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise the first device-detected error (if any)."""
+        self._check(self.lib.sp_ctx_sync(self.handle, _stream(stream)), "sp_ctx_sync")
+
+    # ---- ops ---------------------------------------------------------------------
+    def sp_permute(self, A: CSR, p=None, q=None, rowptr_dtype=None, stream=None,
+                   sync: bool = True) -> CSR:
+        """B = P A Q^T, B[i, j] = A[p[i], q[j]] (p/q None = identity; q is p = symmetric)."""
+        idx_t = _itype((p if p is not None else q).dtype) if (p is not None or q is not None) \
+            else SP_I32
+        rp_t = _itype(rowptr_dtype or A.rowptr.dtype)
+        dev = A.colidx.device
+        B = CSR(A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=_ITORCH[rp_t], device=dev),
+                torch.empty(A.nnz, dtype=A.colidx.dtype, device=dev),
+                torch.empty(A.nnz, dtype=A.values.dtype, device=dev))
+        d = B.desc()
+        qp = _ptr(q)  # the same tensor for p and q gives the same pointer: P A P^T
+        self._check(self.lib.sp_permute(self.handle, ctypes.byref(A.desc()), _ptr(p), qp, idx_t,
+                                         ctypes.byref(d), _stream(stream)), "sp_permute")
+        if sync:
+            self.sync(stream)
+        return B
+
+    def sp_extract(self, A: CSR, I: torch.Tensor, J: torch.Tensor, rowptr_dtype=None,
+                   stream=None, sync: bool = True) -> CSR:
+        """B = A(I, J): B[i, j] = A[I[i], J[j]] (count, allocate with torch, fill)."""
+        idx_t = _itype(I.dtype)
+        if J.dtype != I.dtype:
+            raise TypeError("I and J must share a dtype")
+        plan = ctypes.c_void_p()
+        nnz = ctypes.c_int64()
+        st = _stream(stream)
+        self._check(self.lib.sp_extract_count(self.handle, ctypes.byref(A.desc()), _ptr(I),
+                                              I.numel(), _ptr(J), J.numel(), idx_t,
+                                              ctypes.byref(plan), ctypes.byref(nnz), st),
+                    "sp_extract_count")
+        try:
+            B = self._alloc(I.numel(), J.numel(), nnz.value, rowptr_dtype or A.rowptr.dtype, A)
+            d = B.desc()
+            self._check(self.lib.sp_extract_fill(self.handle, plan, ctypes.byref(d), st),
+                        "sp_extract_fill")
+        finally:
+            self.lib.sp_plan_destroy(self.handle, plan)
+        if sync:
+            self.sync(stream)
+        return B
+
+    def sp_assign(self, A: CSR, I: torch.Tensor, J: torch.Tensor, B: CSR,
+                  mode: int = SP_ASSIGN_REPLACE, rowptr_dtype=None, stream=None,
+                  sync: bool = True) -> CSR:
+        """A' = A with A'(I, J) = B (REPLACE), A is left unchanged."""
+        idx_t = _itype(I.dtype)
+        plan = ctypes.c_void_p()
+        nnz = ctypes.c_int64()
+        st = _stream(stream)
+        self._check(self.lib.sp_assign_count(self.handle, ctypes.byref(A.desc()), _ptr(I),
+                                             I.numel(), _ptr(J), J.numel(), idx_t,
+                                             ctypes.byref(B.desc()), mode, ctypes.byref(plan),
+                                             ctypes.byref(nnz), st), "sp_assign_count")
+        try:
+            Ap = self._alloc(A.nrows, A.ncols, nnz.value, rowptr_dtype or A.rowptr.dtype, A)
+            d = Ap.desc()
+            self._check(self.lib.sp_assign_fill(self.handle, plan, ctypes.byref(d), st),
+                        "sp_assign_fill")
+        finally:
+            self.lib.sp_plan_destroy(self.handle, plan)
+        if sync:
+            self.sync(stream)
+        return Ap
+
+    def _alloc(self, nrows, ncols, nnz, rowptr_dtype, like: CSR) -> CSR:
+        dev = like.colidx.device
+        return CSR(nrows, ncols, torch.empty(nrows + 1, dtype=rowptr_dtype, device=dev),
+                   torch.empty(nnz, dtype=like.colidx.dtype, device=dev),
+                   torch.empty(nnz, dtype=like.values.dtype, device=dev))
+
+    # ---- steps ------------------------------------------------------------------------
+    def sp_inverse_map(self, idx: torch.Tensor, n: int, require_permutation: bool = False,
+                       stream=None, sync: bool = True) -> torch.Tensor:
+        inv = torch.empty(n, dtype=idx.dtype, device=idx.device)
+        self._check(self.lib.sp_inverse_map(self.handle, _ptr(idx), idx.numel(), n,
+                                            _itype(idx.dtype), _ptr(inv),
+                                            1 if require_permutation else 0, _stream(stream)),
+                    "sp_inverse_map")
+        if sync:
+            self.sync(stream)
+        return inv
+
+    def sp_exclusive_scan(self, x: torch.Tensor, out_dtype=torch.int64, stream=None,
+                          sync: bool = True) -> torch.Tensor:
+        out = torch.empty(x.numel() + 1, dtype=out_dtype, device=x.device)
+        self._check(self.lib.sp_exclusive_scan(self.handle, _ptr(x), _itype(x.dtype), x.numel(),
+                                               ctypes.c_void_p(out.data_ptr()), _itype(out_dtype),
+                                               _stream(stream)), "sp_exclusive_scan")
+        if sync:
+            self.sync(stream)
+        return out
+
+    def sp_kept_counts(self, A: CSR, I: torch.Tensor, J: torch.Tensor, stream=None) -> torch.Tensor:
+        counts = torch.empty(I.numel(), dtype=torch.int64, device=I.device)
+        self._check(self.lib.sp_kept_counts(self.handle, ctypes.byref(A.desc()), _ptr(I),
+                                            I.numel(), _ptr(J), J.numel(), _itype(I.dtype),
+                                            _ptr(counts), _stream(stream)), "sp_kept_counts")
+        self.sync(stream)
+        return counts
+
+    def sp_sort_rows(self, M: CSR, stream=None, sync: bool = True) -> CSR:
+        """Sort each row of M by column in place (columns distinct within a row)."""
+        self._check(self.lib.sp_sort_rows(self.handle, ctypes.byref(M.desc()), _stream(stream)),
+                    "sp_sort_rows")
+        if sync:
+            self.sync(stream)
+        return M
+
+    def sp_csr_validate(self, A: CSR, stream=None):
+        self._check(self.lib.sp_csr_validate(self.handle, ctypes.byref(A.desc()),
+                                             _stream(stream)), "sp_csr_validate")

@@ -1,0 +1,367 @@
+// sp_assign: A' = A with A'(I, J) = B  (Sec. 2.3; HipAssign, Algorithm 4).
+//
+// HipAssign builds B' = P B Q^T (B's entry (i, j) moved to (I[i], J[j])) and adds it
+// into A with a user-chosen operator.  Here, with the overwrite (REPLACE) operator:
+//   * rows of A outside I are copied unchanged;
+//   * row I[i] becomes (A's row without the columns of J) merged with B's row i
+//     relabelled through J; both parts have distinct columns, so sorting their union
+//     gives the merged canonical row.
+// Identify: rowmap (row -> position in I, -1 elsewhere) and a bitmap of J; counting:
+// per row of I, len_A - |A[I[i],:] ∩ J| + len_B(i); two exclusive scans give the row
+// pointer of the rebuilt rows and of A'.  Fill: the rebuilt rows are produced by the
+// shared gather / relabel / sort pipeline into a staging buffer, then one load-balanced
+// pass assembles A' from A's untouched rows and the staged rows.
+#include "dispatch.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace sp {
+
+template <class RP, class CIt, class VTt, class IX>
+struct AssignLoader {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rpA;
+  const CI* colA;
+  const VT* valA;
+  const long long* rpB;
+  const CI* colB;
+  const VT* valB;
+  const IX* I;
+  const IX* J;
+  const uint32_t* jbits;
+  long long m, n, nnzA, nJ, nnzB;
+  __device__ RowSrc row(long long i) const {
+    const long long r = (long long)I[i];
+    RowSrc rs{0, 0, 0, 0};
+    if (r >= 0 && r < m) {
+      const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+      if (s >= 0 && e >= s && e <= nnzA) {
+        rs.s0 = s;
+        rs.n0 = e - s;
+      }
+    }
+    const long long s = rpB[i], e = rpB[i + 1];
+    if (s >= 0 && e >= s && e <= nnzB) {
+      rs.s1 = s;
+      rs.n1 = e - s;
+    }
+    return rs;
+  }
+  __device__ RowSrc runs(long long i) const { return row(i); }
+  __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
+  __device__ bool kept(int part, long long pos) const {
+    if (part == 0) {
+      const long long c = (long long)ld_stream(colA + pos);
+      return c >= 0 && c < n && !in_j(c);
+    }
+    const long long b = (long long)ld_stream(colB + pos);
+    return b >= 0 && b < nJ;
+  }
+  __device__ bool elem(int part, long long pos, uint32_t& key, VT& v) const {
+    if (part == 0) {
+      const long long c = (long long)ld_stream(colA + pos);
+      if (c < 0 || c >= n || in_j(c)) return false;
+      key = uint32_t(c);
+      v = ld_stream(valA + pos);
+      return true;
+    }
+    const long long b = (long long)ld_stream(colB + pos);
+    if (b < 0 || b >= nJ) return false;
+    key = uint32_t(ld_map(J + b));
+    v = ld_stream(valB + pos);
+    return true;
+  }
+};
+
+// length of row r of A': untouched rows keep len_A, rows of I take the rebuilt length
+template <class RP, class IX>
+struct AssignLen {
+  const RP* rpA;
+  const IX* rowmap;
+  const long long* vt;  // row pointer of the rebuilt rows
+  long long nnzA;
+  __device__ long long operator()(long long r) const {
+    const long long i = (long long)rowmap[r];
+    if (i >= 0) return vt[i + 1] - vt[i];
+    const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+    return (s >= 0 && e >= s && e <= nnzA) ? e - s : 0;
+  }
+};
+
+// source of row r of A': A itself (which 0) or the staged rebuilt row (which 1)
+template <class RP, class CIt, class VTt, class IX>
+struct AssignGather {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rpA;
+  const CI* colA;
+  const VT* valA;
+  const IX* rowmap;
+  const long long* vt;
+  const CI* tcol;
+  const VT* tval;
+  long long nnzA, ntemp;
+  __device__ void src(long long r, int& which, long long& off) const {
+    const long long i = (long long)rowmap[r];
+    if (i >= 0) {
+      which = 1;
+      off = vt[i];
+    } else {
+      which = 0;
+      off = (long long)rpA[r];
+    }
+  }
+  __device__ void get(int which, long long pos, CI& c, VT& v) const {
+    if (which) {
+      if (pos < 0 || pos >= ntemp) {
+        c = CI(0);
+        v = VT(0);
+        return;
+      }
+      c = ld_stream(tcol + pos);
+      v = ld_stream(tval + pos);
+    } else {
+      if (pos < 0 || pos >= nnzA) {
+        c = CI(0);
+        v = VT(0);
+        return;
+      }
+      c = ld_stream(colA + pos);
+      v = ld_stream(valA + pos);
+    }
+  }
+};
+
+template <class RP, class CI, class IX>
+sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const sp_csr& B = pl->B;
+  const long long m = A.nrows, n = A.ncols, nI = pl->nI, nJ = pl->nJ;
+  const IX* I = static_cast<const IX*>(pl->I);
+  const IX* J = static_cast<const IX*>(pl->J);
+  Carver cv;
+  const size_t o_rm = cv.reserve(size_t(m) * sizeof(IX));
+  const size_t o_jb = cv.reserve(size_t((n + 31) / 32) * 4);
+  const size_t o_vt = cv.reserve(size_t(nI + 1) * 8);
+  const size_t o_vo = cv.reserve(size_t(m + 1) * 8);
+  const size_t o_rb = cv.reserve(size_t(nI + 1) * 8);
+  pl->list_cap = nI + 1;
+  const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_lr = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_hr = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_cn = cv.reserve(64);
+  const size_t o_s1 = cv.reserve(scan_ws_bytes(nI));
+  const size_t o_s2 = cv.reserve(scan_ws_bytes(m));
+  SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
+  cv.bind(pl->buf);
+  IX* rowmap = cv.at<IX>(o_rm);
+  uint32_t* jbits = cv.at<uint32_t>(o_jb);
+  pl->rowmap = rowmap;
+  pl->jmap = jbits;
+  pl->vp = cv.at<long long>(o_vt);
+  pl->vp_out = cv.at<long long>(o_vo);
+  pl->rpB = cv.at<long long>(o_rb);
+  pl->cl_rows = cv.at<long long>(o_cl);
+  pl->long_rows = cv.at<long long>(o_lr);
+  pl->huge_rows = cv.at<long long>(o_hr);
+  pl->counters = cv.at<unsigned>(o_cn);
+  const int nsm = ctx->num_sms;
+  SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
+  SP_CUDA(cudaMemsetAsync(rowmap, 0xFF, size_t(m) * sizeof(IX), s));
+  SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
+  if (nI > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_inverse_map<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, rowmap, ctx->dstatus,
+                                                                    SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (nJ > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jbits, ctx->dstatus,
+                                                                  SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  SP_TRY(widen_rowptr(ctx, s, B.rowptr, B.rowptr_type, nI + 1, pl->rpB));
+  if (nI > 0) {
+    AssignLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
+                                          static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
+                                          static_cast<const CI*>(B.colidx), nullptr, I, J, jbits,
+                                          m, n, A.nnz, nJ, B.nnz};
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->long_rows, pl->counters + 1,
+                  pl->list_cap, pl->huge_rows, pl->counters + 2, pl->list_cap};
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_count_long<<<nsm, 1024, 0, s>>>(ct, pl->vp, cl, pl->counters + 3, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
+                     StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_s1)));
+  AssignLen<RP, IX> len{static_cast<const RP*>(A.rowptr), rowmap, pl->vp, A.nnz};
+  SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{pl->vp_out, nullptr, ctx->dstatus}, m,
+                     cv.at<char>(o_s2)));
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp_out + m, 8, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 1, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+  SP_TRY(ctx_collect(ctx, s));
+  pl->nnz_out = pl->h_tail[0];
+  pl->nnz_temp = pl->h_tail[1];
+  return SP_OK;
+}
+
+template <class RP, class CI, class VT, class IX>
+sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const sp_csr& B = pl->B;
+  const long long m = A.nrows, nI = pl->nI, nt = pl->nnz_temp, nnz_out = pl->nnz_out;
+  SP_TRY(store_rowptr(ctx, s, pl->vp_out, m + 1, Ap->rowptr_type, Ap->rowptr));
+  if (nnz_out == 0) return SP_OK;
+  Carver cv;
+  const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
+  const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
+  size_t po[6];
+  pipe_reserve(cv, nI, nt, sizeof(VT), po);
+  char* base;
+  SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+  cv.bind(base);
+  CI* tcol = cv.at<CI>(o_tc);
+  VT* tval = cv.at<VT>(o_tv);
+  if (nt > 0) {
+    PipeWs w = pipe_bind(cv, nt, po);
+    PipeLists lists;
+    lists.long_rows = pl->long_rows;
+    lists.n_long = pl->counters + 1;
+    lists.long_cap = pl->list_cap;
+    lists.huge_rows = pl->huge_rows;
+    lists.n_huge = pl->counters + 2;
+    lists.huge_cap = pl->list_cap;
+    AssignLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
+                                    static_cast<const CI*>(A.colidx),
+                                    static_cast<const VT*>(A.values), pl->rpB,
+                                    static_cast<const CI*>(B.colidx),
+                                    static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
+                                    static_cast<const IX*>(pl->J),
+                                    static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols,
+                                    A.nnz, pl->nJ, B.nnz};
+    const int kb = ceil_log2_u64(uint64_t(A.ncols));
+    SP_TRY(run_pipeline(ctx, s, ld, pl->vp, nI, nt, kb, false, lists, w, tcol, tval));
+  }
+  AssignGather<RP, CI, VT, IX> g{static_cast<const RP*>(A.rowptr),
+                                 static_cast<const CI*>(A.colidx),
+                                 static_cast<const VT*>(A.values),
+                                 static_cast<const IX*>(pl->rowmap), pl->vp, tcol, tval, A.nnz, nt};
+  const long long blocks = (nnz_out + GATHER_CH - 1) / GATHER_CH;
+  {
+    SP_PHASE(SP_PHASE_GATHER);
+    k_gather_rows<<<unsigned(blocks), GATHER_BLOCK, 0, s>>>(
+        g, pl->vp_out, m, nnz_out, static_cast<CI*>(Ap->colidx), static_cast<VT*>(Ap->values));
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
+}
+
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" sp_status sp_assign_count(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                     const void* J, int64_t nJ, sp_itype idx_type, const sp_csr* B,
+                                     sp_assign_mode mode, sp_plan** plan, int64_t* nnz_out,
+                                     sp_stream_t stream) {
+  if (!ctx || !A || !B || !plan || !nnz_out) return SP_ERR_INVALID_ARG;
+  *plan = nullptr;
+  SP_TRY(check_csr(A));
+  SP_TRY(check_csr(B));
+  if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (mode != SP_ASSIGN_REPLACE && mode != SP_ASSIGN_SELECT2ND && mode != SP_ASSIGN_PLUS)
+    return SP_ERR_INVALID_ARG;
+  if (mode != SP_ASSIGN_REPLACE) return SP_ERR_INVALID_ARG;  // see DESIGN: REPLACE only so far
+  if (nI < 0 || nJ < 0 || nI > A->nrows || nJ > A->ncols) return SP_ERR_SHAPE;
+  if ((nI > 0 && !I) || (nJ > 0 && !J)) return SP_ERR_INVALID_ARG;
+  if (B->nrows != nI || B->ncols != nJ) return SP_ERR_SHAPE;
+  if (B->colidx_type != A->colidx_type || B->value_type != A->value_type) return SP_ERR_INVALID_ARG;
+  if (idx_type == SP_I32 && (A->nrows > INT32_MAX || A->ncols > INT32_MAX)) return SP_ERR_OVERFLOW;
+  if (A->ncols > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  SP_TRY(validate_if_asked(ctx, A, s));
+  SP_TRY(validate_if_asked(ctx, B, s));
+  sp_plan* pl = new sp_plan();
+  pl->op = 1;
+  pl->A = *A;
+  pl->B = *B;
+  pl->I = I;
+  pl->J = J;
+  pl->nI = nI;
+  pl->nJ = nJ;
+  pl->idx_type = idx_type;
+  pl->mode = mode;
+  pl->stream = s;
+  sp_status st = dispatch_i(A->rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A->colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_i(idx_type, [&](auto ix) {
+        using IX = decltype(ix);
+        return assign_count_impl<RP, CI, IX>(ctx, pl, s);
+      });
+    });
+  });
+  if (st != SP_OK) {
+    plan_release(ctx, pl);
+    return st;
+  }
+  *plan = pl;
+  *nnz_out = pl->nnz_out;
+  return SP_OK;
+}
+
+extern "C" sp_status sp_assign_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, sp_stream_t stream) {
+  if (!ctx || !pl || !Ap || pl->op != 1) return SP_ERR_INVALID_ARG;
+  if (Ap->rowptr_type != SP_I32 && Ap->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (Ap->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  pl->stream = s;
+  Ap->nrows = pl->A.nrows;
+  Ap->ncols = pl->A.ncols;
+  Ap->nnz = pl->nnz_out;
+  Ap->colidx_type = pl->A.colidx_type;
+  Ap->value_type = pl->A.value_type;
+  SP_TRY(alloc_csr(ctx, Ap, s));
+  const sp_csr& A = pl->A;
+  return dispatch_i(A.rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A.colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(A.value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(pl->idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return assign_fill_impl<RP, CI, VT, IX>(ctx, pl, Ap, s);
+        });
+      });
+    });
+  });
+}
+
+extern "C" sp_status sp_assign(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                               const void* J, int64_t nJ, sp_itype idx_type, const sp_csr* B,
+                               sp_assign_mode mode, sp_csr* Aprime, sp_stream_t stream) {
+  if (!Aprime) return SP_ERR_INVALID_ARG;
+  sp_plan* pl = nullptr;
+  int64_t nnz = 0;
+  SP_TRY(sp_assign_count(ctx, A, I, nI, J, nJ, idx_type, B, mode, &pl, &nnz, stream));
+  sp_status st = sp_assign_fill(ctx, pl, Aprime, stream);
+  plan_release(ctx, pl);
+  return st;
+}

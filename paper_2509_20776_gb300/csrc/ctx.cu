@@ -1,0 +1,208 @@
+// Context lifecycle, allocator hook, workspace arena and device error reporting.
+#include <cstdlib>
+#include <new>
+
+#include "internal.h"
+
+using namespace sp;
+
+namespace sp {
+
+void* ctx_alloc(sp_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 1;
+  if (!ctx->default_alloc) return ctx->alloc.alloc(ctx->alloc.user, bytes, s);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void ctx_free(sp_ctx* ctx, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (!ctx->default_alloc) {
+    ctx->alloc.free(ctx->alloc.user, p, bytes, s);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+sp_status ctx_workspace(sp_ctx* ctx, size_t bytes, cudaStream_t s, char** base) {
+  if (bytes <= ctx->ws_cap) {
+    *base = ctx->ws;
+    return SP_OK;
+  }
+  size_t cap = bytes + bytes / 4;
+  // release the old arena after the work already queued on its stream
+  if (ctx->ws) ctx_free(ctx, ctx->ws, ctx->ws_cap, s);
+  ctx->ws = static_cast<char*>(ctx_alloc(ctx, cap, s));
+  if (!ctx->ws) {
+    ctx->ws_cap = 0;
+    return SP_ERR_OOM;
+  }
+  ctx->ws_cap = cap;
+  ctx->ws_stream = s;
+  *base = ctx->ws;
+  return SP_OK;
+}
+
+sp_status ctx_collect(sp_ctx* ctx, cudaStream_t s) {
+  SP_CUDA(cudaMemcpyAsync(ctx->hstatus, ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaStreamSynchronize(s));
+  DevStatus h = *ctx->hstatus;
+  if (h.code != 0) {
+    ctx->last_detail = h.detail;
+    SP_CUDA(cudaMemsetAsync(ctx->dstatus, 0, sizeof(DevStatus), s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    return sp_status(h.code);
+  }
+  return SP_OK;
+}
+
+cudaEvent_t ctx_event(sp_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+sp_status check_csr(const sp_csr* A, bool allow_null_arrays) {
+  if (!A) return SP_ERR_INVALID_ARG;
+  if (A->nrows < 0 || A->ncols < 0 || A->nnz < 0) return SP_ERR_SHAPE;
+  if ((A->rowptr_type != SP_I32 && A->rowptr_type != SP_I64) ||
+      (A->colidx_type != SP_I32 && A->colidx_type != SP_I64) ||
+      (A->value_type != SP_F32 && A->value_type != SP_F64))
+    return SP_ERR_INVALID_ARG;
+  if (!allow_null_arrays) {
+    if (!A->rowptr) return SP_ERR_INVALID_ARG;
+    if (A->nnz > 0 && (!A->colidx || !A->values)) return SP_ERR_INVALID_ARG;
+  }
+  if (A->rowptr_type == SP_I32 && A->nnz > INT32_MAX) return SP_ERR_OVERFLOW;
+  if (A->colidx_type == SP_I32 && A->ncols > (int64_t(1) << 31)) return SP_ERR_OVERFLOW;
+  return SP_OK;
+}
+
+}  // namespace sp
+
+extern "C" {
+
+const char* sp_status_str(sp_status s) {
+  switch (s) {
+    case SP_OK: return "SP_OK";
+    case SP_ERR_INVALID_ARG: return "SP_ERR_INVALID_ARG";
+    case SP_ERR_SHAPE: return "SP_ERR_SHAPE";
+    case SP_ERR_INDEX_RANGE: return "SP_ERR_INDEX_RANGE";
+    case SP_ERR_DUPLICATE_INDEX: return "SP_ERR_DUPLICATE_INDEX";
+    case SP_ERR_NOT_PERMUTATION: return "SP_ERR_NOT_PERMUTATION";
+    case SP_ERR_NOT_CANONICAL: return "SP_ERR_NOT_CANONICAL";
+    case SP_ERR_OVERFLOW: return "SP_ERR_OVERFLOW";
+    case SP_ERR_OOM: return "SP_ERR_OOM";
+    case SP_ERR_TIMEOUT: return "SP_ERR_TIMEOUT";
+    case SP_ERR_CUDA: return "SP_ERR_CUDA";
+    case SP_ERR_INTERNAL: return "SP_ERR_INTERNAL";
+  }
+  return "SP_ERR_UNKNOWN";
+}
+
+int sp_version(void) { return 100; }
+
+sp_status sp_ctx_create(sp_ctx** out, int device, const sp_allocator* allocator) {
+  if (!out) return SP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (allocator && (!allocator->alloc || !allocator->free)) return SP_ERR_INVALID_ARG;
+  SP_CUDA(cudaSetDevice(device));
+  sp_ctx* ctx = new (std::nothrow) sp_ctx();
+  if (!ctx) return SP_ERR_OOM;
+  ctx->device = device;
+  if (allocator) {
+    ctx->alloc = *allocator;
+    ctx->default_alloc = false;
+  }
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&ctx->dstatus, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&ctx->hstatus, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMemset(ctx->dstatus, 0, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->dstatus) cudaFree(ctx->dstatus);
+    delete ctx;
+    return SP_ERR_CUDA;
+  }
+  *out = ctx;
+  return SP_OK;
+}
+
+sp_status sp_ctx_destroy(sp_ctx* ctx) {
+  if (!ctx) return SP_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) ctx_free(ctx, ctx->ws, ctx->ws_cap, ctx->ws_stream);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->dstatus);
+  cudaFreeHost(ctx->hstatus);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+  return SP_OK;
+}
+
+sp_status sp_ctx_sync(sp_ctx* ctx, sp_stream_t stream) {
+  if (!ctx) return SP_ERR_INVALID_ARG;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  return ctx_collect(ctx, (cudaStream_t)stream);
+}
+
+int64_t sp_ctx_error_detail(const sp_ctx* ctx) { return ctx ? ctx->last_detail : -1; }
+
+sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
+  if (!ctx) return SP_ERR_INVALID_ARG;
+  switch (key) {
+    case SP_OPT_SPIN_LIMIT: ctx->spin_limit = value < 0 ? (int64_t(1) << 22) : value; return SP_OK;
+    case SP_OPT_SCAN_HOLD_TILE: ctx->hold_tile = value < 0 ? -1 : value; return SP_OK;
+    case SP_OPT_VALIDATE: ctx->validate = value > 0 ? 1 : 0; return SP_OK;
+    case SP_OPT_TIMING: ctx->timing = value > 0 ? 1 : 0; return SP_OK;
+  }
+  return SP_ERR_INVALID_ARG;
+}
+
+sp_status sp_ctx_phase_stats(sp_ctx* ctx, double* ms, int64_t* launches, int reset) {
+  if (!ctx) return SP_ERR_INVALID_ARG;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  for (auto& p : ctx->pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess)
+      ctx->phase_ms[p.phase] += t;
+    else
+      cudaGetLastError();
+    ctx->ev_pool.push_back(p.a);
+    ctx->ev_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int i = 0; i < SP_NUM_PHASES; ++i) {
+    if (ms) ms[i] = ctx->phase_ms[i];
+    if (launches) launches[i] = ctx->phase_launches[i];
+    if (reset) {
+      ctx->phase_ms[i] = 0;
+      ctx->phase_launches[i] = 0;
+    }
+  }
+  return SP_OK;
+}
+
+const char* sp_phase_name(int phase) {
+  static const char* names[SP_NUM_PHASES] = {"map", "count", "scan", "partition", "tile",
+                                             "long", "huge", "gather", "other"};
+  return (phase >= 0 && phase < SP_NUM_PHASES) ? names[phase] : "?";
+}
+
+}  // extern "C"

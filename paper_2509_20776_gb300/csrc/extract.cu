@@ -1,0 +1,315 @@
+// sp_extract: B = A(I, J), B[i, j] = A[I[i], J[j]]  (Sec. 2.2; HipExtract, Algorithms 3, 5).
+//
+// Identify: J becomes a dense inverse map jinv (old column -> position in J, -1 when
+// absent: the SpQvec_inv of Algorithm 3); the first pass of Algorithm 5 counts the
+// entries of each selected row that survive (a warp ballot + popc per 32 entries);
+// the exclusive scan of the counts is B's row pointer.  Fill: the surviving entries
+// are gathered, relabelled through jinv and sorted per row (Algorithm 5's second pass
+// and the Build step).  Rows of I may repeat; J must be distinct.
+#include "dispatch.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace sp {
+
+template <class RP, class CIt, class VTt, class IX>
+struct ExtractLoader {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rowptr;
+  const CI* col;
+  const VT* val;
+  const IX* I;
+  const IX* jinv;
+  long long m, n, nnz;
+  __device__ RowSrc row(long long i) const {
+    const long long r = (long long)I[i];
+    if (r < 0 || r >= m) return RowSrc{0, 0, 0, 0};
+    const long long s = (long long)rowptr[r], e = (long long)rowptr[r + 1];
+    if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
+    return RowSrc{s, 0, e - s, 0};
+  }
+  __device__ bool kept(int, long long pos) const {
+    const long long c = (long long)ld_stream(col + pos);
+    return c >= 0 && c < n && ld_map(jinv + c) >= 0;
+  }
+  __device__ RowSrc runs(long long i) const { return row(i); }
+  __device__ bool elem(int, long long pos, uint32_t& key, VT& v) const {
+    const long long c = (long long)ld_stream(col + pos);
+    if (c < 0 || c >= n) return false;
+    const long long j = (long long)ld_map(jinv + c);
+    if (j < 0) return false;
+    key = uint32_t(j);
+    v = ld_stream(val + pos);
+    return true;
+  }
+};
+
+// copy an int64 row pointer into a typed output row pointer
+sp_status store_rowptr(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n1,
+                       sp_itype t, void* out) {
+  if (t == SP_I64) {
+    if ((void*)vp != out) SP_CUDA(cudaMemcpyAsync(out, vp, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
+    return SP_OK;
+  }
+  {
+    SP_PHASE(SP_PHASE_OTHER);
+    k_narrow<int32_t><<<grid_for(n1, 256, ctx->num_sms * 8), 256, 0, s>>>(vp, n1, static_cast<int32_t*>(out),
+                                                                         ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
+}
+
+sp_status widen_rowptr(sp_ctx* ctx, cudaStream_t s, const void* in, sp_itype t, long long n1,
+                       long long* out) {
+  if (t == SP_I64) {
+    SP_CUDA(cudaMemcpyAsync(out, in, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
+    return SP_OK;
+  }
+  {
+    SP_PHASE(SP_PHASE_OTHER);
+    k_widen<int32_t><<<grid_for(n1, 256, ctx->num_sms * 8), 256, 0, s>>>(static_cast<const int32_t*>(in), n1, out);
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
+}
+
+sp_status plan_alloc(sp_ctx* ctx, sp_plan* pl, size_t bytes, cudaStream_t s) {
+  pl->buf = static_cast<char*>(ctx_alloc(ctx, bytes, s));
+  if (!pl->buf) return SP_ERR_OOM;
+  pl->buf_bytes = bytes;
+  if (cudaMallocHost(&pl->h_tail, 64) != cudaSuccess) {
+    cudaGetLastError();
+    return SP_ERR_CUDA;
+  }
+  return SP_OK;
+}
+
+template <class RP, class CI, class IX>
+sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const long long m = A.nrows, n = A.ncols, nnz = A.nnz, nI = pl->nI, nJ = pl->nJ;
+  const IX* I = static_cast<const IX*>(pl->I);
+  const IX* J = static_cast<const IX*>(pl->J);
+  Carver cv;
+  const size_t o_jinv = cv.reserve(size_t(n) * sizeof(IX));
+  const size_t o_vp = cv.reserve(size_t(nI + 1) * 8);
+  pl->list_cap = nI + 1;
+  const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_lr = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_hr = cv.reserve(size_t(pl->list_cap) * 8);
+  const size_t o_cn = cv.reserve(64);
+  const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
+  SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
+  cv.bind(pl->buf);
+  IX* jinv = cv.at<IX>(o_jinv);
+  pl->jmap = jinv;
+  pl->vp = cv.at<long long>(o_vp);
+  pl->cl_rows = cv.at<long long>(o_cl);
+  pl->long_rows = cv.at<long long>(o_lr);
+  pl->huge_rows = cv.at<long long>(o_hr);
+  pl->counters = cv.at<unsigned>(o_cn);
+  const int nsm = ctx->num_sms;
+  SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
+  SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
+  if (nJ > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_inverse_map<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jinv, ctx->dstatus,
+                                                                    SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (nI > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_range_check<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    ExtractLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
+                                           static_cast<const CI*>(A.colidx), nullptr, I, jinv,
+                                           m, n, nnz};
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->long_rows, pl->counters + 1,
+                  pl->list_cap, pl->huge_rows, pl->counters + 2, pl->list_cap};
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_count_long<<<nsm, 1024, 0, s>>>(ct, pl->vp, cl, pl->counters + 3, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
+                     StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_scan)));
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+  SP_TRY(ctx_collect(ctx, s));
+  pl->nnz_out = pl->h_tail[0];
+  return SP_OK;
+}
+
+template <class RP, class CI, class VT, class IX>
+sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const long long nI = pl->nI, nnz_out = pl->nnz_out;
+  SP_TRY(store_rowptr(ctx, s, pl->vp, nI + 1, B->rowptr_type, B->rowptr));
+  if (nnz_out == 0) return SP_OK;
+  Carver cv;
+  size_t po[6];
+  pipe_reserve(cv, nI, nnz_out, sizeof(VT), po);
+  char* base;
+  SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+  cv.bind(base);
+  PipeWs w = pipe_bind(cv, nnz_out, po);
+  PipeLists lists;
+  lists.long_rows = pl->long_rows;
+  lists.n_long = pl->counters + 1;
+  lists.long_cap = pl->list_cap;
+  lists.huge_rows = pl->huge_rows;
+  lists.n_huge = pl->counters + 2;
+  lists.huge_cap = pl->list_cap;
+  ExtractLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
+                                   static_cast<const CI*>(A.colidx),
+                                   static_cast<const VT*>(A.values), static_cast<const IX*>(pl->I),
+                                   static_cast<const IX*>(pl->jmap), A.nrows, A.ncols, A.nnz};
+  const int kb = ceil_log2_u64(uint64_t(pl->nJ));
+  return run_pipeline(ctx, s, ld, pl->vp, nI, nnz_out, kb, false, lists, w,
+                      static_cast<CI*>(B->colidx), static_cast<VT*>(B->values));
+}
+
+sp_status plan_release(sp_ctx* ctx, sp_plan* pl) {
+  if (!pl) return SP_OK;
+  if (pl->buf) ctx_free(ctx, pl->buf, pl->buf_bytes, pl->stream);
+  if (pl->h_tail) {
+    cudaStreamSynchronize(pl->stream);
+    cudaFreeHost(pl->h_tail);
+  }
+  delete pl;
+  return SP_OK;
+}
+
+}  // namespace sp
+
+using namespace sp;
+
+static sp_status check_index_args(const sp_csr* A, const void* I, long long nI, const void* J,
+                                  long long nJ, sp_itype idx_type) {
+  if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (nI < 0 || nJ < 0) return SP_ERR_SHAPE;
+  if ((nI > 0 && !I) || (nJ > 0 && !J)) return SP_ERR_INVALID_ARG;
+  if (idx_type == SP_I32 && (A->nrows > INT32_MAX || A->ncols > INT32_MAX || nI > INT32_MAX ||
+                             nJ > INT32_MAX))
+    return SP_ERR_OVERFLOW;
+  return SP_OK;
+}
+
+extern "C" sp_status sp_extract_count(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                      const void* J, int64_t nJ, sp_itype idx_type,
+                                      sp_plan** plan, int64_t* nnz_out, sp_stream_t stream) {
+  if (!ctx || !A || !plan || !nnz_out) return SP_ERR_INVALID_ARG;
+  *plan = nullptr;
+  SP_TRY(check_csr(A));
+  SP_TRY(check_index_args(A, I, nI, J, nJ, idx_type));
+  if (nJ > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
+  if (nJ > A->ncols) return SP_ERR_SHAPE;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  SP_TRY(validate_if_asked(ctx, A, s));
+  sp_plan* pl = new sp_plan();
+  pl->op = 0;
+  pl->A = *A;
+  pl->I = I;
+  pl->J = J;
+  pl->nI = nI;
+  pl->nJ = nJ;
+  pl->idx_type = idx_type;
+  pl->stream = s;
+  sp_status st = dispatch_i(A->rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A->colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_i(idx_type, [&](auto ix) {
+        using IX = decltype(ix);
+        return extract_count_impl<RP, CI, IX>(ctx, pl, s);
+      });
+    });
+  });
+  if (st != SP_OK) {
+    plan_release(ctx, pl);
+    return st;
+  }
+  *plan = pl;
+  *nnz_out = pl->nnz_out;
+  return SP_OK;
+}
+
+extern "C" sp_status sp_extract_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* B, sp_stream_t stream) {
+  if (!ctx || !pl || !B || pl->op != 0) return SP_ERR_INVALID_ARG;
+  if (B->rowptr_type != SP_I32 && B->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (B->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  pl->stream = s;
+  B->nrows = pl->nI;
+  B->ncols = pl->nJ;
+  B->nnz = pl->nnz_out;
+  B->colidx_type = pl->A.colidx_type;
+  B->value_type = pl->A.value_type;
+  SP_TRY(alloc_csr(ctx, B, s));
+  const sp_csr& A = pl->A;
+  return dispatch_i(A.rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A.colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(A.value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(pl->idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return extract_fill_impl<RP, CI, VT, IX>(ctx, pl, B, s);
+        });
+      });
+    });
+  });
+}
+
+extern "C" sp_status sp_extract(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                const void* J, int64_t nJ, sp_itype idx_type, sp_csr* B,
+                                sp_stream_t stream) {
+  if (!B) return SP_ERR_INVALID_ARG;
+  sp_plan* pl = nullptr;
+  int64_t nnz = 0;
+  SP_TRY(sp_extract_count(ctx, A, I, nI, J, nJ, idx_type, &pl, &nnz, stream));
+  sp_status st = sp_extract_fill(ctx, pl, B, stream);
+  plan_release(ctx, pl);
+  return st;
+}
+
+extern "C" sp_status sp_kept_counts(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                    const void* J, int64_t nJ, sp_itype idx_type,
+                                    int64_t* counts, sp_stream_t stream) {
+  if (!ctx || !A || (nI > 0 && !counts)) return SP_ERR_INVALID_ARG;
+  sp_plan* pl = nullptr;
+  int64_t nnz = 0;
+  SP_TRY(sp_extract_count(ctx, A, I, nI, J, nJ, idx_type, &pl, &nnz, stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  // counts[i] = vp[i+1] - vp[i]
+  sp_status st = SP_OK;
+  if (nI > 0) {
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_diff<0><<<grid_for(nI, 256, ctx->num_sms * 8), 256, 0, s>>>(pl->vp, nI, reinterpret_cast<long long*>(counts));
+    }
+    if (cudaGetLastError() != cudaSuccess) st = SP_ERR_CUDA;
+  }
+  plan_release(ctx, pl);
+  return st;
+}
+
+extern "C" sp_status sp_plan_destroy(sp_ctx* ctx, sp_plan* plan) {
+  if (!plan) return SP_OK;
+  if (!ctx) return SP_ERR_INVALID_ARG;
+  return plan_release(ctx, plan);
+}

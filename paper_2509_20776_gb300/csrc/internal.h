@@ -1,0 +1,131 @@
+// Host-side internals shared by the translation units of the library: the context,
+// its workspace arena, status plumbing and the type dispatch used by every op.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "sp.h"
+
+struct sp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  sp_allocator alloc{};
+  bool default_alloc = true;
+  // grow-only workspace shared by the calls made through this context
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  cudaStream_t ws_stream = nullptr;
+  sp::DevStatus* dstatus = nullptr;  // device error record
+  sp::DevStatus* hstatus = nullptr;  // pinned host mirror
+  int64_t spin_limit = int64_t(1) << 22;
+  int64_t hold_tile = -1;
+  int validate = 0;
+  int64_t last_detail = -1;
+  // tracing: launches per phase, and (with timing on) event pairs per launch
+  int timing = 0;
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double phase_ms[SP_NUM_PHASES] = {};
+  long long phase_launches[SP_NUM_PHASES] = {};
+};
+
+namespace sp {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+inline size_t itype_size(sp_itype t) { return t == SP_I64 ? 8 : 4; }
+inline size_t vtype_size(sp_vtype t) { return t == SP_F64 ? 8 : 4; }
+
+#define SP_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return SP_ERR_CUDA;            \
+  } while (0)
+
+#define SP_TRY(call)                                      \
+  do {                                                    \
+    sp_status s_ = (call);                                \
+    if (s_ != SP_OK) return s_;                           \
+  } while (0)
+
+void* ctx_alloc(sp_ctx* ctx, size_t bytes, cudaStream_t s);
+void ctx_free(sp_ctx* ctx, void* p, size_t bytes, cudaStream_t s);
+
+// Carves 256-byte aligned slices from one allocation.  Sizes are first declared
+// (reserve), then the backing store is obtained once (commit), then slices are taken
+// in the same order (take).
+class Carver {
+ public:
+  size_t reserve(size_t bytes) {
+    size_t off = total_;
+    total_ += align_up(bytes ? bytes : 1);
+    return off;
+  }
+  size_t total() const { return total_; }
+  void bind(char* base) { base_ = base; }
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(base_ + off); }
+
+ private:
+  size_t total_ = 0;
+  char* base_ = nullptr;
+};
+
+// Ensure the context workspace holds at least `bytes`; returns its base.
+sp_status ctx_workspace(sp_ctx* ctx, size_t bytes, cudaStream_t s, char** base);
+
+// After a synchronising point: read, clear and return the device error record.
+sp_status ctx_collect(sp_ctx* ctx, cudaStream_t s);
+
+inline int grid_for(int64_t work, int block, int cap) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return int(g);
+}
+
+sp_status check_csr(const sp_csr* A, bool allow_null_arrays = false);
+
+// Scope around one kernel launch: counts it under `phase` and, with timing on, records
+// CUDA events before and after it on the launching stream.
+cudaEvent_t ctx_event(sp_ctx* ctx);
+struct PhaseScope {
+  sp_ctx* ctx;
+  cudaStream_t s;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(sp_ctx* c, cudaStream_t st, int ph) : ctx(c), s(st), phase(ph) {
+    ctx->phase_launches[ph]++;
+    if (ctx->timing) {
+      a = ctx_event(ctx);
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t b = ctx_event(ctx);
+    if (!b) return;
+    cudaEventRecord(b, s);
+    ctx->pending.push_back({phase, a, b});
+  }
+};
+#define SP_PHASE(ph) ::sp::PhaseScope sp_phase_scope_##__LINE__(ctx, s, ph)
+
+// Allocate B's arrays through the context allocator when all three are NULL.
+sp_status alloc_csr(sp_ctx* ctx, sp_csr* B, cudaStream_t s);
+
+// With SP_OPT_VALIDATE set, check A is canonical (synchronises); else SP_OK.
+sp_status validate_if_asked(sp_ctx* ctx, const sp_csr* A, cudaStream_t s);
+
+}  // namespace sp

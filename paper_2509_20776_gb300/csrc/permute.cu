@@ -1,0 +1,220 @@
+// sp_permute: B = P A Q^T, B[i, j] = A[p[i], q[j]]  (Sec. 2.1; HipPerm, Algorithm 1).
+//
+// One-GPU restatement of Identify-Exchange-Build: the inverse column map qinv is the
+// index/value swap of the Identify step; every output row i is the source row p[i]
+// (so its length is known without counting), the exclusive scan of those lengths is
+// the row pointer of B (the proc_pointer of Algorithm 2), and the gather + column
+// relabelling + per-row sort is the fill pass plus the Build step's sort.  There is no
+// exchange: all rows live in one address space.
+#include "dispatch.h"
+#include "kernels.cuh"
+
+namespace sp {
+
+template <class RP, class CIt, class VTt, class IX>
+struct PermLoader {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rowptr;
+  const CI* col;
+  const VT* val;
+  const IX* p;     // new row -> old row (null: identity)
+  const IX* qinv;  // old column -> new column (null: identity)
+  long long m, n, nnz;
+  __device__ RowSrc row(long long r) const {
+    const long long src = p ? (long long)p[r] : r;
+    if (src < 0 || src >= m) return RowSrc{0, 0, 0, 0};
+    const long long s = (long long)rowptr[src], e = (long long)rowptr[src + 1];
+    if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
+    return RowSrc{s, 0, e - s, 0};
+  }
+  __device__ bool elem(int, long long pos, uint32_t& key, VT& v) const {
+    const long long c = (long long)ld_stream(col + pos);
+    if (c < 0 || c >= n) return false;
+    key = qinv ? uint32_t(ld_map(qinv + c)) : uint32_t(c);
+    v = ld_stream(val + pos);
+    return true;
+  }
+};
+
+template <class RP, class IX>
+struct PermLen {
+  const RP* rowptr;
+  const IX* p;
+  long long m, nnz;
+  __device__ long long operator()(long long i) const {
+    const long long src = p ? (long long)p[i] : i;
+    if (src < 0 || src >= m) return 0;
+    const long long s = (long long)rowptr[src], e = (long long)rowptr[src + 1];
+    if (s < 0 || e < s || e > nnz) return 0;
+    return e - s;
+  }
+};
+
+// Plain row gather for the identity column map (columns keep their order, no sort).
+template <class RP, class CIt, class VTt, class IX>
+struct PermGather {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rowptr;
+  const CI* col;
+  const VT* val;
+  const IX* p;
+  long long m, nnz;
+  __device__ void src(long long r, int& which, long long& off) const {
+    which = 0;
+    const long long s = p ? (long long)p[r] : r;
+    off = (s >= 0 && s < m) ? (long long)rowptr[s] : 0;
+  }
+  __device__ void get(int, long long pos, CI& c, VT& v) const {
+    if (pos < 0 || pos >= nnz) {
+      c = CI(0);
+      v = VT(0);
+      return;
+    }
+    c = ld_stream(col + pos);
+    v = ld_stream(val + pos);
+  }
+};
+
+template <class RP, class CI, class VT, class IX>
+sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, sp_csr* B,
+                       cudaStream_t s) {
+  const long long m = A->nrows, n = A->ncols, nnz = A->nnz;
+  const bool sym = p && q && (const void*)p == (const void*)q && m == n;
+  const bool out64 = B->rowptr_type == SP_I64;
+  Carver cv;
+  const size_t o_qinv = cv.reserve(q ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_pbits = cv.reserve((p && !sym) ? size_t((m + 31) / 32) * 4 : 0);
+  const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
+  const size_t o_scan = cv.reserve(scan_ws_bytes(m));
+  const long long long_cap = nnz / TILE_CP + 1, huge_cap = nnz / LONG_CAP + 1;
+  const size_t o_long = cv.reserve(size_t(long_cap) * 8);
+  const size_t o_huge = cv.reserve(size_t(huge_cap) * 8);
+  const size_t o_cnt = cv.reserve(64);
+  size_t po[6];
+  pipe_reserve(cv, m, nnz, sizeof(VT), po);
+  char* base;
+  SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+  cv.bind(base);
+  IX* qinv = q ? cv.at<IX>(o_qinv) : nullptr;
+  long long* vp = out64 ? static_cast<long long*>(B->rowptr) : cv.at<long long>(o_vp);
+  const int nsm = ctx->num_sms;
+  // Identify: inverse column map (validates q), row permutation check (validates p)
+  if (q) {
+    SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(n) * sizeof(IX), s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_inverse_map<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, ctx->dstatus,
+                                                                   SP_ERR_NOT_PERMUTATION);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (p && !sym) {
+    uint32_t* bits = cv.at<uint32_t>(o_pbits);
+    SP_CUDA(cudaMemsetAsync(bits, 0, size_t((m + 31) / 32) * 4, s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(m, 256, nsm * 8), 256, 0, s>>>(p, m, m, bits, ctx->dstatus,
+                                                                SP_ERR_NOT_PERMUTATION);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  // row pointer of B: exclusive scan of the permuted row lengths
+  PermLen<RP, IX> len{static_cast<const RP*>(A->rowptr), p, m, nnz};
+  if (out64) {
+    SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{vp, nullptr, ctx->dstatus}, m,
+                       cv.at<char>(o_scan)));
+  } else {
+    SP_TRY(launch_scan(ctx, s, len,
+                       StoreDual<int32_t>{vp, static_cast<int32_t*>(B->rowptr), ctx->dstatus}, m,
+                       cv.at<char>(o_scan)));
+  }
+  if (nnz == 0 || m == 0) return SP_OK;
+  CI* out_col = static_cast<CI*>(B->colidx);
+  VT* out_val = static_cast<VT*>(B->values);
+  if (!q) {  // identity column map: rows move whole, no relabel, no sort
+    PermGather<RP, CI, VT, IX> g{static_cast<const RP*>(A->rowptr),
+                                 static_cast<const CI*>(A->colidx),
+                                 static_cast<const VT*>(A->values), p, m, nnz};
+    const long long blocks = (nnz + GATHER_CH - 1) / GATHER_CH;
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_gather_rows<<<unsigned(blocks), GATHER_BLOCK, 0, s>>>(g, vp, m, nnz, out_col, out_val);
+    }
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+  }
+  PermLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A->rowptr),
+                                static_cast<const CI*>(A->colidx),
+                                static_cast<const VT*>(A->values), p, qinv, m, n, nnz};
+  PipeLists lists;
+  lists.long_rows = cv.at<long long>(o_long);
+  lists.huge_rows = cv.at<long long>(o_huge);
+  lists.n_long = cv.at<unsigned>(o_cnt);
+  lists.n_huge = lists.n_long + 1;
+  lists.long_cap = long_cap;
+  lists.huge_cap = huge_cap;
+  SP_CUDA(cudaMemsetAsync(lists.n_long, 0, 64, s));
+  PipeWs w = pipe_bind(cv, nnz, po);
+  const int kb = ceil_log2_u64(uint64_t(n));
+  return run_pipeline(ctx, s, ld, vp, m, nnz, kb, true, lists, w, out_col, out_val);
+}
+
+sp_status alloc_csr(sp_ctx* ctx, sp_csr* B, cudaStream_t s) {
+  // caller-owned arrays are used as given; none at all means library-allocated
+  const bool none = !B->rowptr && !B->colidx && !B->values;
+  const bool all = B->rowptr && (B->nnz == 0 || (B->colidx && B->values));
+  if (!none && !all) return SP_ERR_INVALID_ARG;
+  if (all) return SP_OK;
+  const size_t rb = size_t(B->nrows + 1) * itype_size(B->rowptr_type);
+  B->rowptr = ctx_alloc(ctx, rb, s);
+  B->colidx = ctx_alloc(ctx, size_t(B->nnz) * itype_size(B->colidx_type), s);
+  B->values = ctx_alloc(ctx, size_t(B->nnz) * vtype_size(B->value_type), s);
+  if (!B->rowptr || !B->colidx || !B->values) {
+    ctx_free(ctx, B->rowptr, rb, s);
+    ctx_free(ctx, B->colidx, 0, s);
+    ctx_free(ctx, B->values, 0, s);
+    B->rowptr = B->colidx = B->values = nullptr;
+    return SP_ERR_OOM;
+  }
+  return SP_OK;
+}
+
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, const void* q,
+                                sp_itype idx_type, sp_csr* B, sp_stream_t stream) {
+  if (!ctx || !A || !B) return SP_ERR_INVALID_ARG;
+  SP_TRY(check_csr(A));
+  if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (B->rowptr_type != SP_I32 && B->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (idx_type == SP_I32 && (A->nrows > INT32_MAX || A->ncols > INT32_MAX)) return SP_ERR_OVERFLOW;
+  if (B->rowptr_type == SP_I32 && A->nnz > INT32_MAX) return SP_ERR_OVERFLOW;
+  if (A->ncols > (int64_t(1) << 32)) return SP_ERR_OVERFLOW;  // 32-bit sort keys
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  SP_TRY(validate_if_asked(ctx, A, s));
+  B->nrows = A->nrows;
+  B->ncols = A->ncols;
+  B->nnz = A->nnz;
+  B->colidx_type = A->colidx_type;
+  B->value_type = A->value_type;
+  SP_TRY(alloc_csr(ctx, B, s));
+  return dispatch_i(A->rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A->colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(A->value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return permute_impl<RP, CI, VT, IX>(ctx, A, static_cast<const IX*>(p),
+                                              static_cast<const IX*>(q), B, s);
+        });
+      });
+    });
+  });
+}

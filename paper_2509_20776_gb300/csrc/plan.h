@@ -1,0 +1,40 @@
+// The state kept between a count call and its fill call (extraction / assignment).
+#pragma once
+
+#include "internal.h"
+
+struct sp_plan {
+  int op = 0;  // 0 = extraction, 1 = assignment
+  sp_csr A{}, B{};
+  const void* I = nullptr;
+  const void* J = nullptr;
+  long long nI = 0, nJ = 0;
+  sp_itype idx_type = SP_I32;
+  sp_assign_mode mode = SP_ASSIGN_REPLACE;
+  long long nnz_out = 0;   // entries of the result
+  long long nnz_temp = 0;  // assignment: entries of the rebuilt rows I
+  char* buf = nullptr;     // plan-owned device memory
+  size_t buf_bytes = 0;
+  cudaStream_t stream = nullptr;
+  // device pointers inside buf
+  void* jmap = nullptr;        // extraction: jinv (nJ positions); assignment: J bitmap
+  void* rowmap = nullptr;      // assignment: rowmap (m entries of idx type)
+  long long* vp = nullptr;     // extraction: row pointer of B; assignment: of rows I (temp)
+  long long* vp_out = nullptr; // assignment: row pointer of A'
+  long long* rpB = nullptr;    // assignment: B's row pointer widened to int64
+  long long* cl_rows = nullptr;
+  long long* long_rows = nullptr;
+  long long* huge_rows = nullptr;
+  long long list_cap = 0;
+  unsigned* counters = nullptr;  // [0] n_cl [1] n_long [2] n_huge [3] count ticket
+  long long* h_tail = nullptr;   // pinned host: totals read back by the count call
+};
+
+namespace sp {
+sp_status store_rowptr(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n1, sp_itype t,
+                       void* out);
+sp_status widen_rowptr(sp_ctx* ctx, cudaStream_t s, const void* in, sp_itype t, long long n1,
+                       long long* out);
+sp_status plan_alloc(sp_ctx* ctx, sp_plan* pl, size_t bytes, cudaStream_t s);
+sp_status plan_release(sp_ctx* ctx, sp_plan* pl);
+}  // namespace sp

@@ -1,0 +1,371 @@
+"""CUDA path vs the oracle, bit-exact, through the C ABI (small and medium sizes).
+
+Sizes span many tiles, the long-row and huge-row kernels (hub rows beyond the
+shared-memory capacities) and ragged tails; values include -0.0 and NaN payloads.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import assert_same, from_oracle, to_dev, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_20776_gb300 import build
+    build.build()
+    from paper_2509_20776_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def er(n=4096, draws=8, seed=0, kind="f64um11", rp=torch.int32, ci=torch.int32, m=None):
+    return synth.er_csr(m or n, n, draws, seed=seed, value_kind=kind, rowptr_dtype=rp,
+                        colidx_dtype=ci)
+
+
+def special_values(A):
+    v = A.values.clone()
+    if v.numel() >= 4:
+        v[0] = -0.0
+        v[1] = float("nan")
+        if v.dtype == torch.float64:
+            v[2:3] = torch.tensor([0x7FF8DEADBEEF0001], dtype=torch.int64).view(torch.float64)
+        else:
+            v[2:3] = torch.tensor([0x7FC0BEEF], dtype=torch.int32).view(torch.float32)
+        v[3] = 0.0
+    return synth.CSRTensors(A.nrows, A.ncols, A.rowptr, A.colidx, v)
+
+
+# ---- config 1: the tiny workload ----------------------------------------------------
+def test_cfg1a_permute(ctx):
+    A = special_values(er())
+    p = synth.random_permutation(4096, 1, 0)
+    q = synth.random_permutation(4096, 1, 1)
+    B = ctx.sp_permute(to_dev(A), p.cuda(), q.cuda())
+    assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "cfg1a")
+
+
+def test_cfg1b_extract(ctx):
+    A = er()
+    I = synth.random_subset(4096, 1024, 1, 2)
+    J = synth.random_subset(4096, 1024, 1, 3)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), "cfg1b")
+
+
+def test_cfg1c_assign(ctx):
+    A = er()
+    Bm = synth.er_csr(1024, 1024, 4, seed=5, value_kind="f64um11", rowptr_dtype=torch.int32)
+    I = synth.random_subset(4096, 1024, 1, 4)
+    J = synth.random_subset(4096, 1024, 1, 5)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), to_dev(Bm))
+    want = oracle.assign(to_oracle(A), I.numpy(), J.numpy(), to_oracle(Bm))
+    assert_same(Ap, want, "cfg1c")
+    # extract-after-assign returns B (REPLACE region semantics)
+    E = ctx.sp_extract(Ap, I.cuda(), J.cuda())
+    assert_same(E, to_oracle(Bm), "extract after assign")
+
+
+# ---- permutation variants ------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["sym", "p_only", "q_only", "identity"])
+def test_permute_variants(ctx, mode):
+    A = er(2000, 7, seed=3)
+    p = synth.random_permutation(2000, 3, 0).cuda()
+    q = synth.random_permutation(2000, 3, 1).cuda()
+    args = {"sym": (p, p), "p_only": (p, None), "q_only": (None, q), "identity": (None, None)}[mode]
+    B = ctx.sp_permute(to_dev(A), *args)
+    pa = None if args[0] is None else args[0].cpu().numpy()
+    qa = None if args[1] is None else args[1].cpu().numpy()
+    assert_same(B, oracle.permute(to_oracle(A), pa, qa), mode)
+
+
+@pytest.mark.parametrize("rp,ci,ix,kind", [
+    (torch.int64, torch.int32, torch.int32, "f32u01"),
+    (torch.int64, torch.int64, torch.int64, "f64um11"),
+    (torch.int32, torch.int64, torch.int32, "f32u01"),
+    (torch.int32, torch.int32, torch.int64, "f64um11"),
+])
+def test_permute_types(ctx, rp, ci, ix, kind):
+    A = er(3000, 9, seed=4, kind=kind, rp=rp, ci=ci)
+    p = synth.random_permutation(3000, 4, 0, dtype=ix)
+    q = synth.random_permutation(3000, 4, 1, dtype=ix)
+    B = ctx.sp_permute(to_dev(A), p.cuda(), q.cuda(), rowptr_dtype=torch.int64)
+    assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), str(rp))
+    assert B.colidx.dtype == ci
+
+
+def test_rectangular_permute(ctx):
+    A = synth.er_csr(700, 5000, 12, seed=9)
+    p = synth.random_permutation(700, 9, 0)
+    q = synth.random_permutation(5000, 9, 1)
+    B = ctx.sp_permute(to_dev(A), p.cuda(), q.cuda())
+    assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "rect")
+
+
+def rmat(scale, ef=16, seed=0, kind="f32u01", sym=True):
+    return synth.rmat_csr(scale, ef, seed=seed, symmetrize=sym, value_kind=kind)
+
+
+@pytest.mark.parametrize("order", ["random", "degree"])
+def test_rmat_permute_hubs(ctx, order):
+    """Power-law rows: tiles, long rows and huge rows (> shared-memory capacity)."""
+    A = rmat(16)
+    lens = (A.rowptr[1:] - A.rowptr[:-1])
+    assert int(lens.max()) > 8192, "needs rows beyond the long-row capacity"
+    n = A.nrows
+    p = synth.random_permutation(n, 7, 0) if order == "random" else \
+        synth.degree_descending_permutation(A.rowptr)
+    B = ctx.sp_permute(to_dev(A), p.cuda(), p.cuda())
+    assert_same(B, oracle.permute(to_oracle(A), p.numpy(), p.numpy()), order)
+
+
+def boundary_matrix(lengths, ncols, seed=0, kind="f32u01"):
+    """Rows of the given lengths with random distinct columns (rows sorted)."""
+    g = torch.Generator().manual_seed(seed)
+    cols, counts = [], []
+    for L in lengths:
+        c = torch.randperm(ncols, generator=g)[:L]
+        cols.append(torch.sort(c).values)
+        counts.append(L)
+    colidx = torch.cat(cols).to(torch.int32) if cols else torch.zeros(0, dtype=torch.int32)
+    rowptr = torch.zeros(len(lengths) + 1, dtype=torch.int64)
+    rowptr[1:] = torch.cumsum(torch.tensor(counts, dtype=torch.int64), 0)
+    vals = synth.draw_values(colidx.numel(), seed, kind, "cpu")
+    return synth.CSRTensors(len(lengths), ncols, rowptr, colidx, vals)
+
+
+def test_row_length_boundaries(ctx):
+    Ls = [0, 1, 2, 15, 16, 17, 31, 32, 33, 0, 0, 2047, 2048, 2049, 0, 4095, 4096, 4097, 8191,
+          8192, 8193, 16384, 3, 0, 70000, 1, 5]
+    A = boundary_matrix(Ls, 200000, seed=2)
+    q = synth.random_permutation(200000, 2, 1)
+    p = synth.random_permutation(len(Ls), 2, 0)
+    B = ctx.sp_permute(to_dev(A), p.cuda(), q.cuda())
+    assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "boundaries")
+
+
+def test_skewed_keys_long_row(ctx):
+    """Keys packed into a narrow range with outliers (forces several refine rounds)."""
+    n = 1 << 22
+    L = 6000
+    g = torch.Generator().manual_seed(5)
+    dense = torch.randperm(5000, generator=g)[:L - 200]
+    far = torch.randperm(n - 5000, generator=g)[:200] + 5000
+    c = torch.sort(torch.cat([dense, far])).values.to(torch.int32)
+    A = synth.CSRTensors(1, n, torch.tensor([0, c.numel()], dtype=torch.int64), c,
+                         synth.draw_values(c.numel(), 1, "f32u01", "cpu"))
+    q = synth.random_permutation(n, 5, 1)
+    # identity-like q on the dense block keeps the skew in the new keys
+    q[:5000] = torch.arange(5000, dtype=q.dtype)
+    rest = torch.arange(5000, n, dtype=q.dtype)
+    q[5000:] = rest[torch.randperm(n - 5000, generator=g)]
+    B = ctx.sp_permute(to_dev(A), None, q.cuda())
+    assert_same(B, oracle.permute(to_oracle(A), None, q.numpy()), "skew")
+
+
+# ---- extraction ------------------------------------------------------------------------
+def test_extract_repeated_rows_and_full(ctx):
+    A = er(3000, 10, seed=6, kind="f32u01", rp=torch.int64)
+    g = torch.Generator().manual_seed(1)
+    I = torch.randint(0, 3000, (5000,), generator=g, dtype=torch.int32)
+    J = synth.random_subset(3000, 1700, 6, 1)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), "repeat I")
+    I = torch.arange(3000, dtype=torch.int32)
+    J = torch.arange(3000, dtype=torch.int32)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, to_oracle(A), "extract all")
+
+
+def test_extract_empty(ctx):
+    A = er(500, 5, seed=7)
+    e = torch.zeros(0, dtype=torch.int32)
+    J = synth.random_subset(500, 100, 7, 1)
+    B = ctx.sp_extract(to_dev(A), e.cuda(), J.cuda())
+    assert B.nrows == 0 and B.nnz == 0
+    I = synth.random_subset(500, 50, 7, 2)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), e.cuda())
+    assert B.nrows == 50 and B.ncols == 0 and B.nnz == 0
+    assert torch.all(B.rowptr == 0)
+
+
+def test_extract_hubs(ctx):
+    A = rmat(15)
+    n = A.nrows
+    I = synth.random_subset(n, n // 2, 8, 1)
+    J = synth.random_subset(n, n // 2, 8, 2)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), "extract rmat")
+    kc = ctx.sp_kept_counts(to_dev(A), I.cuda(), J.cuda())
+    assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
+
+
+def test_extract_mesh(ctx):
+    M = synth.mesh5_csr(60, 70)
+    n = M.nrows
+    I = synth.random_subset(n, n // 8, 9, 1)
+    B = ctx.sp_extract(to_dev(M), I.cuda(), I.cuda())
+    assert_same(B, oracle.extract(to_oracle(M), I.numpy(), I.numpy()), "mesh")
+
+
+# ---- assignment --------------------------------------------------------------------------
+def test_assign_hubs_and_roundtrip(ctx):
+    A = rmat(15, sym=False)
+    n = A.nrows
+    Bm = synth.er_csr(4096, 4096, 8, seed=3)
+    # the first 8 rows (the R-MAT hubs) plus 4088 random others, in random order
+    rest = synth.random_subset(n - 8, 4088, 3, 1) + 8
+    I = torch.cat([torch.arange(8, dtype=rest.dtype), rest])
+    I = I[torch.randperm(4096, generator=torch.Generator().manual_seed(3))]
+    J = synth.random_subset(n, 4096, 3, 2)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), to_dev(Bm))
+    assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), to_oracle(Bm)), "assign")
+    E = ctx.sp_extract(Ap, I.cuda(), J.cuda())
+    assert_same(E, to_oracle(Bm), "extract after assign")
+
+
+def test_assign_contiguous(ctx):
+    A = er(3000, 8, seed=8, kind="f32u01", rp=torch.int64)
+    Bm = synth.er_csr(300, 400, 6, seed=9)
+    I = torch.arange(1000, 1300, dtype=torch.int32)
+    J = torch.arange(2000, 2400, dtype=torch.int32)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), to_dev(Bm))
+    assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), to_oracle(Bm)), "contig")
+
+
+def test_split_reassign_replace_disjoint(ctx):
+    """Streaming update (Sec. 6.3) with disjoint row blocks: parts re-assigned give A."""
+    A = er(2000, 6, seed=10, kind="f32u01", rp=torch.int64)
+    O = to_oracle(A)
+    cur = from_oracle(oracle.assign(O, np.arange(0, 400), np.arange(2000),
+                                    oracle.CSR.of(400, 2000, np.zeros(401, np.int64), [],
+                                                  np.zeros(0, np.float32))))
+    for r0 in range(0, 400, 100):
+        I = np.arange(r0, r0 + 100)
+        J = np.arange(2000)
+        part = oracle.extract(O, I, J)
+        cur = ctx.sp_assign(cur, torch.from_numpy(I).int().cuda(), torch.from_numpy(J).int().cuda(),
+                            from_oracle(part))
+    assert_same(cur, O, "split/re-assign")
+
+
+# ---- steps on their own -------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 4095, 4096, 4097, 1 << 20, 3_000_001])
+def test_scan(ctx, n):
+    g = torch.Generator().manual_seed(n)
+    x = torch.randint(0, 50, (n,), generator=g, dtype=torch.int32)
+    out = ctx.sp_exclusive_scan(x.cuda())
+    assert np.array_equal(out.cpu().numpy(), oracle.exclusive_scan(x.numpy()))
+
+
+def test_scan_int64_large_values(ctx):
+    x = torch.full((100000,), 1 << 40, dtype=torch.int64)
+    out = ctx.sp_exclusive_scan(x.cuda())
+    assert int(out[-1]) == 100000 << 40
+
+
+def test_scan_timeout_hook(ctx):
+    """A tile that never publishes: successors give up with SP_ERR_TIMEOUT, no hang."""
+    from paper_2509_20776_gb300 import SP_OPT_SCAN_HOLD_TILE, SP_OPT_SPIN_LIMIT, SpError
+    x = torch.ones(4096 * 8, dtype=torch.int32).cuda()
+    ctx.set_option(SP_OPT_SPIN_LIMIT, 2000)
+    ctx.set_option(SP_OPT_SCAN_HOLD_TILE, 1)
+    try:
+        with pytest.raises(SpError) as e:
+            ctx.sp_exclusive_scan(x)
+        assert e.value.name == "SP_ERR_TIMEOUT"
+    finally:
+        ctx.set_option(SP_OPT_SCAN_HOLD_TILE, -1)
+        ctx.set_option(SP_OPT_SPIN_LIMIT, -1)
+    out = ctx.sp_exclusive_scan(x)  # the context still works
+    assert np.array_equal(out.cpu().numpy(), np.arange(x.numel() + 1))
+
+
+def test_inverse_map(ctx):
+    p = synth.random_permutation(100000, 11, 0)
+    inv = ctx.sp_inverse_map(p.cuda(), 100000, True)
+    assert np.array_equal(inv.cpu().numpy(), oracle.inverse_map(p.numpy(), 100000, True))
+    sub = synth.random_subset(100000, 777, 11, 1, dtype=torch.int64)
+    inv = ctx.sp_inverse_map(sub.cuda(), 100000)
+    assert np.array_equal(inv.cpu().numpy(), oracle.inverse_map(sub.numpy(), 100000))
+
+
+def test_sort_rows(ctx):
+    """Rows with shuffled columns (incl. a 2-round huge row: keys need > 27 bits)."""
+    Ls = [0, 3, 40, 5000, 9000, 30000, 7, 0, 1]
+    n = 1 << 30
+    g = torch.Generator().manual_seed(12)
+    cols = [torch.unique(torch.randint(0, n, (L * 2 + 8,), generator=g))[:L] for L in Ls]
+    cols = [c[torch.randperm(c.numel(), generator=g)] for c in cols]
+    counts = [c.numel() for c in cols]
+    colidx = torch.cat(cols).to(torch.int32)
+    rowptr = torch.zeros(len(Ls) + 1, dtype=torch.int64)
+    rowptr[1:] = torch.cumsum(torch.tensor(counts), 0)
+    vals = synth.draw_values(colidx.numel(), 12, "f64um11", "cpu")
+    M = synth.CSRTensors(len(Ls), n, rowptr, colidx, vals)
+    D = to_dev(M)
+    ctx.sp_sort_rows(D)
+    O = to_oracle(M)
+    r, c, v = O.triplets()
+    assert_same(D, oracle.build_csr(O.nrows, O.ncols, r, c, v), "sort rows")
+
+
+# ---- errors -------------------------------------------------------------------------------
+def test_errors(ctx):
+    from paper_2509_20776_gb300 import SpError
+    A = to_dev(er(100, 4, seed=1))
+    bad = torch.arange(100, dtype=torch.int32).cuda()
+    bad[5] = 7
+    with pytest.raises(SpError) as e:
+        ctx.sp_permute(A, bad, None)
+    assert e.value.name == "SP_ERR_NOT_PERMUTATION"
+    oob = torch.arange(100, dtype=torch.int32).cuda()
+    oob[3] = 1000
+    with pytest.raises(SpError) as e:
+        ctx.sp_permute(A, None, oob)
+    assert e.value.name == "SP_ERR_INDEX_RANGE"
+    with pytest.raises(SpError) as e:
+        ctx.sp_extract(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
+                       torch.tensor([3, 3], dtype=torch.int32).cuda())
+    assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
+    with pytest.raises(SpError) as e:
+        ctx.sp_extract(A, torch.tensor([0, 100], dtype=torch.int32).cuda(),
+                       torch.tensor([3], dtype=torch.int32).cuda())
+    assert e.value.name == "SP_ERR_INDEX_RANGE"
+    Bm = to_dev(synth.er_csr(3, 3, 2, seed=1))
+    with pytest.raises(SpError) as e:
+        ctx.sp_assign(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
+                      torch.tensor([0, 1, 2], dtype=torch.int32).cuda(), Bm)
+    assert e.value.name == "SP_ERR_SHAPE"
+    # the context is still usable
+    p = synth.random_permutation(100, 1, 0).cuda()
+    B = ctx.sp_permute(A, p, p)
+    assert B.nnz == A.nnz
+
+
+def test_validate(ctx):
+    from paper_2509_20776_gb300 import SpError
+    A = er(200, 5, seed=2)
+    ctx.sp_csr_validate(to_dev(A))
+    bad = to_dev(A)
+    bad.colidx[3], bad.colidx[4] = bad.colidx[4].clone(), bad.colidx[3].clone()
+    with pytest.raises(SpError) as e:
+        ctx.sp_csr_validate(bad)
+    assert e.value.name == "SP_ERR_NOT_CANONICAL"
+
+
+def test_deterministic(ctx):
+    A = rmat(14)
+    p = synth.random_permutation(A.nrows, 1, 0).cuda()
+    B1 = ctx.sp_permute(to_dev(A), p, p)
+    B2 = ctx.sp_permute(to_dev(A), p, p)
+    assert torch.equal(B1.colidx, B2.colidx) and torch.equal(B1.values.view(torch.int32),
+                                                             B2.values.view(torch.int32))
