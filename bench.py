@@ -37,6 +37,13 @@ WORKLOAD = ("R-MAT scale 25 (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, sym
             "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
 
 
+_T0 = time.time()
+
+
+def log(msg):
+    print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,28 +226,18 @@ def run_ours(args, ws, rank, local):
     ctx = Context(local)
     pk = peaks()
     hbm = pk["hbm_gbs"] if pk else 6800.0
+    log("generating the permutation workload")
     A, ops = permute_workload(args.scale, dev)
+    log(f"generated: {A.nrows} rows, {A.nnz} entries")
     Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
     nnz, m = A.nnz, A.nrows
     outs = [ctx.sp_permute(Ad, p, q, sync=True) for _, p, q in ops]  # also validates
 
     def step():
         for (_, p, q), B in zip(ops, outs):
-            ctx.lib.sp_permute(ctx.handle, __import__("ctypes").byref(Ad.desc()),
-                               _p(p), _p(q), _it(p), __import__("ctypes").byref(B.desc()),
-                               _st())
+            ctx.sp_permute(Ad, p, q, sync=False, out=B)
 
-    import ctypes
-
-    def _p(t):
-        return ctypes.c_void_p(t.data_ptr())
-
-    def _it(t):
-        return 0 if t.dtype == torch.int32 else 1
-
-    def _st():
-        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-
+    log("validated the three permutations")
     classes = row_classes(A.rowptr)
     # timed region: device-resident inputs, outputs preallocated
     ctx.phase_stats(reset=True)
@@ -278,25 +275,30 @@ def run_ours(args, ws, rank, local):
         "clocks": clk.summary(),
         "peak_source": "measured (MEASURED_PEAKS.json)" if pk else "fallback",
     }
+    log(f"timed permutations: {ms / args.steps:.3f} ms/step")
     # ---- end to end through the public API with host buffers -----------------------
     if not args.no_e2e:
         result["e2e"] = e2e_permute(ctx, A, ops, args, ws)
+        log("e2e done")
     # ---- extra operations -------------------------------------------------------------
     del outs
     if not args.no_extra:
         ops_res = {}
         try:
             ops_res["extract"] = bench_extract(ctx, args, dev, hbm, ws)
+            log("extract done")
         except Exception as e:  # noqa: BLE001
             ops_res["extract"] = {"error": repr(e)[:300]}
         torch.cuda.empty_cache()
         try:
             ops_res["assign"] = bench_assign(ctx, args, dev, hbm, ws)
+            log("assign done")
         except Exception as e:  # noqa: BLE001
             ops_res["assign"] = {"error": repr(e)[:300]}
         result["ops"] = ops_res
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
+        log("cpu baseline done")
     ctx.close()
     return result
 

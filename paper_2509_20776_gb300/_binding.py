@@ -191,15 +191,18 @@ class Context:
 
     # ---- ops ---------------------------------------------------------------------
     def sp_permute(self, A: CSR, p=None, q=None, rowptr_dtype=None, stream=None,
-                   sync: bool = True) -> CSR:
-        """B = P A Q^T, B[i, j] = A[p[i], q[j]] (p/q None = identity; q is p = symmetric)."""
+                   sync: bool = True, out: CSR | None = None) -> CSR:
+        """B = P A Q^T, B[i, j] = A[p[i], q[j]] (p/q None = identity; q is p = symmetric).
+
+        ``out``: a preallocated result (same shape and types) to write into."""
         idx_t = _itype((p if p is not None else q).dtype) if (p is not None or q is not None) \
             else SP_I32
         rp_t = _itype(rowptr_dtype or A.rowptr.dtype)
         dev = A.colidx.device
-        B = CSR(A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=_ITORCH[rp_t], device=dev),
-                torch.empty(A.nnz, dtype=A.colidx.dtype, device=dev),
-                torch.empty(A.nnz, dtype=A.values.dtype, device=dev))
+        B = out if out is not None else CSR(
+            A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=_ITORCH[rp_t], device=dev),
+            torch.empty(A.nnz, dtype=A.colidx.dtype, device=dev),
+            torch.empty(A.nnz, dtype=A.values.dtype, device=dev))
         d = B.desc()
         qp = _ptr(q)  # the same tensor for p and q gives the same pointer: P A P^T
         self._check(self.lib.sp_permute(self.handle, ctypes.byref(A.desc()), _ptr(p), qp, idx_t,

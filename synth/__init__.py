@@ -104,11 +104,19 @@ class CSRTensors:
                           self.colidx.to(colidx_dtype or self.colidx.dtype), self.values)
 
 
-def draw_values(nnz: int, seed: int, kind: str, device, start: int = 0) -> torch.Tensor:
+def draw_values(nnz: int, seed: int, kind: str, device, start: int = 0,
+                chunk: int = 1 << 26) -> torch.Tensor:
     """Values for stored entries ``start .. start+nnz`` (global positions).
 
     kind 'f32u01': fp32 U(0,1) from 24 bits; 'f64um11': fp64 U(-1,1) from 53 bits.
     """
+    if nnz > chunk:
+        dt = torch.float32 if kind == "f32u01" else torch.float64
+        out = torch.empty(nnz, dtype=dt, device=device)
+        for s0 in range(0, nnz, chunk):
+            s1 = min(nnz, s0 + chunk)
+            out[s0:s1] = draw_values(s1 - s0, seed, kind, device, start + s0, chunk)
+        return out
     pos = torch.arange(start, start + nnz, dtype=torch.int64, device=device)
     if kind == "f32u01":
         h = hash32(seed, S_VALUE, pos)
