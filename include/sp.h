@@ -247,6 +247,27 @@ SP_API sp_status sp_inverse_map(sp_ctx* ctx, const void* idx, int64_t len, int64
 SP_API sp_status sp_exclusive_scan(sp_ctx* ctx, const void* in, sp_itype in_type, int64_t len,
                             void* out, sp_itype out_type, sp_stream_t stream);
 
+/* Exclusive prefix sum that allocates nothing (the paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory when they need the scan --
+ * a device allocator doing its own bookkeeping, which cannot recurse into itself; a
+ * service that reserved all device memory up front; a latency-critical loop that must
+ * not pay for or synchronise on an allocation.  Such callers cannot create an sp_ctx,
+ * whose error record is allocated, so no context is taken).
+ *   Same result as sp_exclusive_scan: out[i] = sum_{k<i} in[k], i = 0..len.
+ *   The scan's tile-status words, tile ticket and error record live in a fixed device
+ *   array inside the library (about 512 KB, held by every GPU that loads the library
+ *   until the process exits); no cudaMalloc, cudaFree or allocating routine is called.
+ *   len must not exceed SP_SCAN_NOALLOC_MAX_LEN (else SP_ERR_SHAPE, nothing launched).
+ *   The first call on a device looks up the array's device address (once per device,
+ *   with that device current); make that first call before any stream capture.
+ *   Every call reuses the same array: calls that overlap on the GPU (other streams,
+ *   other host threads, the same device) race and must be serialised by the caller.
+ *   Synchronises `stream` and returns the scan's device status (SP_ERR_OVERFLOW,
+ *   SP_ERR_TIMEOUT) or SP_OK. */
+#define SP_SCAN_NOALLOC_MAX_LEN (INT64_C(1) << 28)
+SP_API sp_status sp_exclusive_scan_noalloc(const void* in, sp_itype in_type, int64_t len,
+                                           void* out, sp_itype out_type, sp_stream_t stream);
+
 /* Kept-entry counts of an extraction (the first, counting pass of Algorithm 5):
  *   counts[i] = #{ k in row I[i] of A : colidx[k] is an entry of J }  (int64, nI).
  *   J must be distinct.  Errors as sp_extract. */

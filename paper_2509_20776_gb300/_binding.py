@@ -67,6 +67,7 @@ SIGNATURES = {
     "sp_csr_free": (_int, [_vp, _PCSR]),
     "sp_inverse_map": (_int, [_vp, _vp, _i64, _i64, _int, _vp, _int, _vp]),
     "sp_exclusive_scan": (_int, [_vp, _vp, _int, _i64, _vp, _int, _vp]),
+    "sp_exclusive_scan_noalloc": (_int, [_vp, _int, _i64, _vp, _int, _vp]),
     "sp_kept_counts": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _vp, _vp]),
     "sp_sort_rows": (_int, [_vp, _PCSR, _vp]),
     "sp_csr_validate": (_int, [_vp, _PCSR, _vp]),
