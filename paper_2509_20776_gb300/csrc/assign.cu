@@ -48,28 +48,22 @@ struct AssignLoader {
     }
     return rs;
   }
-  __device__ RowSrc runs(long long i) const { return row(i); }
+  static constexpr bool kAllKept = false;
+  static constexpr bool kLoadVals = true;
   __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
-  __device__ bool kept(int part, long long pos) const {
-    if (part == 0) {
-      const long long c = (long long)ld_stream(colA + pos);
-      return c >= 0 && c < n && !in_j(c);
-    }
-    const long long b = (long long)ld_stream(colB + pos);
-    return b >= 0 && b < nJ;
+  __device__ const CI* cols(int part) const { return part ? colB : colA; }
+  __device__ const VT* vals(int part) const { return part ? valB : valA; }
+  __device__ bool test(int part, long long c) const {
+    return part == 0 ? (c >= 0 && c < n && !in_j(c)) : (c >= 0 && c < nJ);
   }
-  __device__ bool elem(int part, long long pos, uint32_t& key, VT& v) const {
-    if (part == 0) {
-      const long long c = (long long)ld_stream(colA + pos);
+  __device__ bool map(int part, long long c, uint32_t& key) const {
+    if (part == 0) {  // A's entry survives unless its column is assigned
       if (c < 0 || c >= n || in_j(c)) return false;
       key = uint32_t(c);
-      v = ld_stream(valA + pos);
       return true;
     }
-    const long long b = (long long)ld_stream(colB + pos);
-    if (b < 0 || b >= nJ) return false;
-    key = uint32_t(ld_map(J + b));
-    v = ld_stream(valB + pos);
+    if (c < 0 || c >= nJ) return false;  // B's column b lands in column J[b]
+    key = uint32_t(ld_map(J + c));
     return true;
   }
 };

@@ -190,4 +190,32 @@ __device__ __forceinline__ void smem_incl_max(uint32_t* a, int n, uint32_t* tmp)
   __syncthreads();
 }
 
+// In-place inclusive max over a shared array of 16-bit values a[0..n), n <= BLOCK*ITEMS.
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ void smem_incl_max16(uint16_t* a, int n, uint32_t* tmp) {
+  const int t = threadIdx.x;
+  uint32_t v[ITEMS];
+  uint32_t m = 0;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int x = t * ITEMS + j;
+    v[j] = x < n ? a[x] : 0u;
+    m = v[j] > m ? v[j] : m;
+  }
+  const uint32_t incl = block_incl_max<BLOCK>(m, tmp);
+  uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 1);
+  __shared__ uint32_t warp_last16[BLOCK / 32];
+  if ((t & 31) == 31) warp_last16[t >> 5] = incl;
+  __syncthreads();
+  if ((t & 31) == 0) prev = (t >> 5) ? warp_last16[(t >> 5) - 1] : 0u;
+  uint32_t run = prev;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int x = t * ITEMS + j;
+    run = v[j] > run ? v[j] : run;
+    if (x < n) a[x] = uint16_t(run);
+  }
+  __syncthreads();
+}
+
 }  // namespace sp

@@ -1,4 +1,5 @@
 // Context lifecycle, allocator hook, workspace arena and device error reporting.
+#include <cstdio>
 #include <cstdlib>
 #include <new>
 
@@ -125,6 +126,15 @@ sp_status sp_ctx_create(sp_ctx** out, int device, const sp_allocator* allocator)
   if (allocator) {
     ctx->alloc = *allocator;
     ctx->default_alloc = false;
+  } else {
+    // keep freed blocks in this process's stream-ordered pool between calls instead of
+    // returning them to the driver at every synchronisation (plans take GBs per call)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      unsigned long long keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
   }
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&ctx->dstatus, sizeof(DevStatus)) != cudaSuccess ||
@@ -178,12 +188,14 @@ sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
 sp_status sp_ctx_phase_stats(sp_ctx* ctx, double* ms, int64_t* launches, int reset) {
   if (!ctx) return SP_ERR_INVALID_ARG;
   SP_CUDA(cudaSetDevice(ctx->device));
+  static const bool trace = std::getenv("SP_TRACE") != nullptr;
   for (auto& p : ctx->pending) {
     float t = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess)
       ctx->phase_ms[p.phase] += t;
     else
       cudaGetLastError();
+    if (trace) std::fprintf(stderr, "[sp trace] %-9s %10.4f ms\n", sp_phase_name(p.phase), t);
     ctx->ev_pool.push_back(p.a);
     ctx->ev_pool.push_back(p.b);
   }

@@ -20,7 +20,8 @@ struct ExtractLoader {
   const CI* col;
   const VT* val;
   const IX* I;
-  const IX* jinv;
+  const IX* jinv;         // column -> position in J, -1 when absent
+  const uint32_t* jbits;  // membership bitmap of J (n bits, small enough to stay in L2)
   long long m, n, nnz;
   __device__ RowSrc row(long long i) const {
     const long long r = (long long)I[i];
@@ -29,19 +30,18 @@ struct ExtractLoader {
     if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
     return RowSrc{s, 0, e - s, 0};
   }
-  __device__ bool kept(int, long long pos) const {
-    const long long c = (long long)ld_stream(col + pos);
-    return c >= 0 && c < n && ld_map(jinv + c) >= 0;
+  static constexpr bool kAllKept = false;
+  static constexpr bool kLoadVals = true;
+  __device__ const CI* cols(int) const { return col; }
+  __device__ const VT* vals(int) const { return val; }
+  __device__ bool test(int, long long c) const {
+    return c >= 0 && c < n && ((ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u);
   }
-  __device__ RowSrc runs(long long i) const { return row(i); }
-  __device__ bool elem(int, long long pos, uint32_t& key, VT& v) const {
-    const long long c = (long long)ld_stream(col + pos);
-    if (c < 0 || c >= n) return false;
+  __device__ bool map(int, long long c, uint32_t& key) const {
+    if (!test(0, c)) return false;  // the inverse map is read only for kept entries
     const long long j = (long long)ld_map(jinv + c);
-    if (j < 0) return false;
     key = uint32_t(j);
-    v = ld_stream(val + pos);
-    return true;
+    return j >= 0;
   }
 };
 
@@ -94,6 +94,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const IX* J = static_cast<const IX*>(pl->J);
   Carver cv;
   const size_t o_jinv = cv.reserve(size_t(n) * sizeof(IX));
+  const size_t o_jb = cv.reserve(size_t((n + 31) / 32) * 4);
   const size_t o_vp = cv.reserve(size_t(nI + 1) * 8);
   pl->list_cap = nI + 1;
   const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
@@ -104,7 +105,9 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
   IX* jinv = cv.at<IX>(o_jinv);
+  uint32_t* jbits = cv.at<uint32_t>(o_jb);
   pl->jmap = jinv;
+  pl->jbits = jbits;
   pl->vp = cv.at<long long>(o_vp);
   pl->cl_rows = cv.at<long long>(o_cl);
   pl->long_rows = cv.at<long long>(o_lr);
@@ -113,7 +116,14 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
   SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
+  SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
   if (nJ > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jbits, ctx->dstatus,
+                                                                  SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
     {
       SP_PHASE(SP_PHASE_MAP);
       k_inverse_map<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jinv, ctx->dstatus,
@@ -129,7 +139,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     SP_CUDA(cudaGetLastError());
     ExtractLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
                                            static_cast<const CI*>(A.colidx), nullptr, I, jinv,
-                                           m, n, nnz};
+                                           jbits, m, n, nnz};
     CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->long_rows, pl->counters + 1,
                   pl->list_cap, pl->huge_rows, pl->counters + 2, pl->list_cap};
     {
@@ -174,7 +184,8 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   ExtractLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
                                    static_cast<const CI*>(A.colidx),
                                    static_cast<const VT*>(A.values), static_cast<const IX*>(pl->I),
-                                   static_cast<const IX*>(pl->jmap), A.nrows, A.ncols, A.nnz};
+                                   static_cast<const IX*>(pl->jmap),
+                                   static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz};
   const int kb = ceil_log2_u64(uint64_t(pl->nJ));
   return run_pipeline(ctx, s, ld, pl->vp, nI, nnz_out, kb, false, lists, w,
                       static_cast<CI*>(B->colidx), static_cast<VT*>(B->values));

@@ -103,34 +103,62 @@ __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long
   else dev_fail(st, SP_ERR_INTERNAL, -12);
 }
 
-// Counter: for listed row i, the source runs and a per-element "kept" test.
-//   RowSrc runs(long long i) const;   bool kept(int part, long long pos) const;
-//   long long extra(long long i) const;  (entries added regardless, e.g. B's row)
+// Count kernels take a loader (see segsort.cuh) and count the entries its map keeps.
+// Short rows: one warp handles COUNT_RB rows per step, reading the first 32 entries of
+// all of them in one batch (ballot + popc per row); the rest of longer rows follows
+// in batches of LOAD_U x 32.  Source-long rows (> TILE_CP entries) are listed for
+// k_count_long (one CTA per row) and later handled by k_long / k_huge.
+constexpr int COUNT_RB = 4;
+
 template <class Ct>
 __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ counts,
                              CountLists cl, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = w0; i < nlisted; i += nw) {
-    const RowSrc rs = ct.runs(i);
-    const long long Ls = rs.n0 + rs.n1;
-    if (Ls > TILE_CP) {
-      if (lane == 0) push_row(cl.cl_rows, cl.n_cl, cl.cl_cap, i, st);
-      continue;
+  const CountOnly<Ct> ko{ct};
+  for (long long i0 = w0 * COUNT_RB; i0 < nlisted; i0 += nw * COUNT_RB) {
+    RowSrc rs[COUNT_RB];
+    long long Ls[COUNT_RB], cnt[COUNT_RB];
+    bool lng[COUNT_RB];
+    Batch<CountOnly<Ct>, COUNT_RB> bt;
+#pragma unroll
+    for (int u = 0; u < COUNT_RB; ++u) {
+      const long long i = i0 + u;
+      rs[u] = i < nlisted ? ct.row(i) : RowSrc{0, 0, 0, 0};
+      Ls[u] = rs[u].n0 + rs[u].n1;
+      lng[u] = Ls[u] > TILE_CP;
+      bt.valid[u] = !lng[u] && lane < Ls[u];
+      if (bt.valid[u]) bt.at(u, rs[u], lane);
     }
-    long long cnt = 0;
-    for (long long e0 = 0; e0 < rs.n0; e0 += 32) {
-      const long long e = e0 + lane;
-      const bool k = e < rs.n0 && ct.kept(0, rs.s0 + e);
-      cnt += __popc(__ballot_sync(0xffffffffu, k));
+    bt.run(ko);
+#pragma unroll
+    for (int u = 0; u < COUNT_RB; ++u) cnt[u] = __popc(__ballot_sync(0xffffffffu, bt.kept[u]));
+#pragma unroll
+    for (int u = 0; u < COUNT_RB; ++u) {
+      if (lng[u] || Ls[u] <= 32) continue;
+      for (long long e0 = 32; e0 < Ls[u]; e0 += 32 * LOAD_U) {
+        Batch<CountOnly<Ct>, LOAD_U> b2;
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const long long e = e0 + v * 32 + lane;
+          b2.valid[v] = e < Ls[u];
+          if (b2.valid[v]) b2.at(v, rs[u], e);
+        }
+        b2.run(ko);
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) cnt[u] += __popc(__ballot_sync(0xffffffffu, b2.kept[v]));
+      }
     }
-    for (long long e0 = 0; e0 < rs.n1; e0 += 32) {
-      const long long e = e0 + lane;
-      const bool k = e < rs.n1 && ct.kept(1, rs.s1 + e);
-      cnt += __popc(__ballot_sync(0xffffffffu, k));
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < COUNT_RB; ++u) {
+        const long long i = i0 + u;
+        if (i >= nlisted) break;
+        if (lng[u]) push_row(cl.cl_rows, cl.n_cl, cl.cl_cap, i, st);
+        else counts[i] = cnt[u];
+      }
     }
-    if (lane == 0) counts[i] = cnt;
   }
 }
 
@@ -140,6 +168,7 @@ __global__ void __launch_bounds__(1024) k_count_long(Ct ct, long long* __restric
   __shared__ unsigned s_item;
   __shared__ long long red[33];
   const int t = threadIdx.x;
+  const CountOnly<Ct> ko{ct};
   unsigned count = *cl.n_cl;
   if (count > cl.cl_cap) count = unsigned(cl.cl_cap);
   for (;;) {
@@ -148,10 +177,21 @@ __global__ void __launch_bounds__(1024) k_count_long(Ct ct, long long* __restric
     const unsigned item = s_item;
     if (item >= count) break;
     const long long i = cl.cl_rows[item];
-    const RowSrc rs = ct.runs(i);
+    const RowSrc rs = ct.row(i);
+    const long long Ls = rs.n0 + rs.n1;
     long long c = 0;
-    for (long long e = t; e < rs.n0; e += blockDim.x) c += ct.kept(0, rs.s0 + e);
-    for (long long e = t; e < rs.n1; e += blockDim.x) c += ct.kept(1, rs.s1 + e);
+    for (long long e0 = 0; e0 < Ls; e0 += (long long)blockDim.x * LOAD_U) {
+      Batch<CountOnly<Ct>, LOAD_U> bt;
+#pragma unroll
+      for (int u = 0; u < LOAD_U; ++u) {
+        const long long e = e0 + (long long)u * blockDim.x + t;
+        bt.valid[u] = e < Ls;
+        if (bt.valid[u]) bt.at(u, rs, e);
+      }
+      bt.run(ko);
+#pragma unroll
+      for (int u = 0; u < LOAD_U; ++u) c += bt.kept[u];
+    }
     c = warp_sum(c);
     if ((t & 31) == 0) red[t >> 5] = c;
     __syncthreads();
@@ -237,22 +277,36 @@ __global__ void __launch_bounds__(GATHER_BLOCK) k_gather_rows(Gs gs, const long 
     }
     __syncthreads();
     smem_incl_max<B, ITEMS>(owner, GATHER_CH, tmp32);
+    // all loads first, then all stores: the stores may not be moved above later loads
+    // (the compiler cannot rule out aliasing), so interleaving would serialise them
+    constexpr int H = 8;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t + j * B;
-      const long long g = c0 + x;
-      const uint32_t ow = owner[x];
-      if (g < c1 && ow > 0) {
-        const int k = int(ow) - 1;
-        const long long o = r_o0[k];
-        // positions beyond the chunk's rows belong to the next chunk of rows
-        if (g >= o && g < r_o1[k]) {
-          CI c;
-          VT v;
-          gs.get(r_which[k], r_off[k] + (g - o), c, v);
-          out_col[g] = c;
-          out_val[g] = v;
+    for (int h = 0; h < ITEMS; h += H) {
+      CI c[H];
+      VT v[H];
+      bool ok[H];
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        const int x = t + (h + u) * B;
+        const long long g = c0 + x;
+        const uint32_t ow = owner[x];
+        ok[u] = false;
+        if (g < c1 && ow > 0) {
+          const int k = int(ow) - 1;
+          const long long o = r_o0[k];
+          // positions beyond the chunk's rows belong to the next chunk of rows
+          if (g >= o && g < r_o1[k]) {
+            ok[u] = true;
+            gs.get(r_which[k], r_off[k] + (g - o), c[u], v[u]);
+          }
         }
+      }
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        if (!ok[u]) continue;
+        const long long g = c0 + t + (h + u) * B;
+        out_col[g] = c[u];
+        out_val[g] = v[u];
       }
     }
     __syncthreads();

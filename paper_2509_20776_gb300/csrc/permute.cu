@@ -18,35 +18,42 @@ struct PermLoader {
   const RP* rowptr;
   const CI* col;
   const VT* val;
-  const IX* p;     // new row -> old row (null: identity)
-  const IX* qinv;  // old column -> new column (null: identity)
-  long long m, n, nnz;
+  const IX* qinv;          // old column -> new column (null: identity)
+  const long long* sstart;  // source start of output row r (written by the scan)
+  const long long* vp;      // output row pointer (row r has vp[r+1]-vp[r] entries)
+  long long n;
   __device__ RowSrc row(long long r) const {
-    const long long src = p ? (long long)p[r] : r;
-    if (src < 0 || src >= m) return RowSrc{0, 0, 0, 0};
-    const long long s = (long long)rowptr[src], e = (long long)rowptr[src + 1];
-    if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
-    return RowSrc{s, 0, e - s, 0};
+    return RowSrc{sstart[r], 0, vp[r + 1] - vp[r], 0};
   }
-  __device__ bool elem(int, long long pos, uint32_t& key, VT& v) const {
-    const long long c = (long long)ld_stream(col + pos);
-    if (c < 0 || c >= n) return false;
+  static constexpr bool kAllKept = true;
+  static constexpr bool kLoadVals = true;
+  __device__ const CI* cols(int) const { return col; }
+  __device__ const VT* vals(int) const { return val; }
+  __device__ bool test(int, long long c) const { return c >= 0 && c < n; }
+  __device__ bool map(int, long long c, uint32_t& key) const {
+    if (c < 0 || c >= n) return false;  // not canonical (sp_csr_validate reports it)
     key = qinv ? uint32_t(ld_map(qinv + c)) : uint32_t(c);
-    v = ld_stream(val + pos);
     return true;
   }
 };
 
+// Scan input for the permutation: len(A[p[i], :]); records the source start of every
+// output row on the way, so the fill kernels need no second lookup through p.
 template <class RP, class IX>
 struct PermLen {
   const RP* rowptr;
   const IX* p;
   long long m, nnz;
+  long long* sstart;
   __device__ long long operator()(long long i) const {
     const long long src = p ? (long long)p[i] : i;
-    if (src < 0 || src >= m) return 0;
-    const long long s = (long long)rowptr[src], e = (long long)rowptr[src + 1];
-    if (s < 0 || e < s || e > nnz) return 0;
+    long long s = 0, e = 0;
+    if (src >= 0 && src < m) {
+      s = (long long)rowptr[src];
+      e = (long long)rowptr[src + 1];
+      if (s < 0 || e < s || e > nnz) s = e = 0;
+    }
+    sstart[i] = s;
     return e - s;
   }
 };
@@ -88,6 +95,7 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   const size_t o_pbits = cv.reserve((p && !sym) ? size_t((m + 31) / 32) * 4 : 0);
   const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
   const size_t o_scan = cv.reserve(scan_ws_bytes(m));
+  const size_t o_ss = cv.reserve(size_t(m) * 8);
   const long long long_cap = nnz / TILE_CP + 1, huge_cap = nnz / LONG_CAP + 1;
   const size_t o_long = cv.reserve(size_t(long_cap) * 8);
   const size_t o_huge = cv.reserve(size_t(huge_cap) * 8);
@@ -121,7 +129,8 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
     SP_CUDA(cudaGetLastError());
   }
   // row pointer of B: exclusive scan of the permuted row lengths
-  PermLen<RP, IX> len{static_cast<const RP*>(A->rowptr), p, m, nnz};
+  long long* sstart = cv.at<long long>(o_ss);
+  PermLen<RP, IX> len{static_cast<const RP*>(A->rowptr), p, m, nnz, sstart};
   if (out64) {
     SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{vp, nullptr, ctx->dstatus}, m,
                        cv.at<char>(o_scan)));
@@ -147,7 +156,7 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   }
   PermLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A->rowptr),
                                 static_cast<const CI*>(A->colidx),
-                                static_cast<const VT*>(A->values), p, qinv, m, n, nnz};
+                                static_cast<const VT*>(A->values), qinv, sstart, vp, n};
   PipeLists lists;
   lists.long_rows = cv.at<long long>(o_long);
   lists.huge_rows = cv.at<long long>(o_huge);

@@ -298,7 +298,7 @@ sp_status run_pipeline(sp_ctx* ctx, cudaStream_t s, const Ld& ld, const long lon
     {
       SP_PHASE(SP_PHASE_TILE);
       k_tile<Ld><<<unsigned(g), TILE_BLOCK, sm, s>>>(ld, vp, w.tile_first, w.ntiles, out_col,
-                                                      out_val, ctx->dstatus);
+                                                      out_val, key_bits, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
   }
@@ -307,9 +307,9 @@ sp_status run_pipeline(sp_ctx* ctx, cudaStream_t s, const Ld& ld, const long lon
   (void)once_l;
   {
     SP_PHASE(SP_PHASE_LONG);
-    k_long<Ld><<<nsm, LONG_BLOCK, lsm, s>>>(ld, vp, lists.long_rows, lists.n_long, nullptr,
+    k_long<Ld><<<2 * nsm, LONG_BLOCK, lsm, s>>>(ld, vp, lists.long_rows, lists.n_long, nullptr,
                                              nullptr, lists.long_cap, w.counters + 0, nullptr, nullptr, out_col,
-                                             out_val, ctx->dstatus);
+                                             out_val, key_bits, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   if (nnz_out > LONG_CAP) {
@@ -337,9 +337,9 @@ sp_status run_pipeline(sp_ctx* ctx, cudaStream_t s, const Ld& ld, const long lon
     }
     {
       SP_PHASE(SP_PHASE_LONG);
-      k_long<Ld><<<nsm, LONG_BLOCK, lsm, s>>>(ld, vp, nullptr, nullptr, w.fin, w.counters + 4,
+      k_long<Ld><<<2 * nsm, LONG_BLOCK, lsm, s>>>(ld, vp, nullptr, nullptr, w.fin, w.counters + 4,
                                                w.fin_cap, w.counters + 3, w.tkey, tval, out_col, out_val,
-                                               ctx->dstatus);
+                                               key_bits, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
   }

@@ -19,11 +19,14 @@ struct SortLoader {
     if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
     return RowSrc{s, 0, e - s, 0};
   }
-  __device__ bool elem(int, long long pos, uint32_t& key, VT& v) const {
-    const long long c = (long long)ld_stream(col + pos);
+  static constexpr bool kAllKept = true;
+  static constexpr bool kLoadVals = true;
+  __device__ const CI* cols(int) const { return col; }
+  __device__ const VT* vals(int) const { return val; }
+  __device__ bool test(int, long long c) const { return c >= 0 && c < n; }
+  __device__ bool map(int, long long c, uint32_t& key) const {
     if (c < 0 || c >= n) return false;
     key = uint32_t(c);
-    v = ld_stream(val + pos);
     return true;
   }
 };

@@ -208,6 +208,22 @@ def test_extract_hubs(ctx):
     assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
 
 
+def test_extract_long_sources_short_outputs(ctx):
+    """Hub rows whose sources exceed the tile limit but keep few entries sit between
+    ordinary rows of a tile (the tile must leave their output positions alone)."""
+    A = rmat(15)
+    n = A.nrows
+    I = synth.random_permutation(n, 13, 0)
+    J = synth.random_subset(n, n // 64, 13, 1)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), "long src, short out")
+    Bm = synth.er_csr(n, n // 64, 2, seed=13)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), to_dev(Bm))
+    assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), to_oracle(Bm)), "assign")
+    E = ctx.sp_extract(Ap, I.cuda(), J.cuda())
+    assert_same(E, to_oracle(Bm), "extract after assign")
+
+
 def test_extract_mesh(ctx):
     M = synth.mesh5_csr(60, 70)
     n = M.nrows
