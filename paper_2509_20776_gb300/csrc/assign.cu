@@ -230,7 +230,7 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   CI* tcol = cv.at<CI>(o_tc);
   VT* tval = cv.at<VT>(o_tv);
   if (nt > 0) {
-    PipeWs w = pipe_bind(cv, nt, po);
+    PipeWs w = pipe_bind(cv, nI, nt, po);
     PipeLists lists;
     lists.long_rows = pl->long_rows;
     lists.n_long = pl->counters + 1;

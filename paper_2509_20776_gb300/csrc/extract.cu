@@ -173,7 +173,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
-  PipeWs w = pipe_bind(cv, nnz_out, po);
+  PipeWs w = pipe_bind(cv, nI, nnz_out, po);
   PipeLists lists;
   lists.long_rows = pl->long_rows;
   lists.n_long = pl->counters + 1;

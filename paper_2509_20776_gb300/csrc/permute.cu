@@ -165,7 +165,7 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   lists.long_cap = long_cap;
   lists.huge_cap = huge_cap;
   SP_CUDA(cudaMemsetAsync(lists.n_long, 0, 64, s));
-  PipeWs w = pipe_bind(cv, nnz, po);
+  PipeWs w = pipe_bind(cv, m, nnz, po);
   const int kb = ceil_log2_u64(uint64_t(n));
   return run_pipeline(ctx, s, ld, vp, m, nnz, kb, true, lists, w, out_col, out_val);
 }

@@ -195,12 +195,14 @@ __global__ void k_partition(const long long* __restrict__ vp, long long nrows, l
   }
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows;
        r += (long long)gridDim.x * blockDim.x) {
-    const long long s = vp[r], e = vp[r + 1];
+    // tiles cut the coordinate vp[r] + TILE_ROW_W * r, so a tile holds at most
+    // TILE_CP / TILE_ROW_W + 1 rows even where many rows are empty
+    const long long s = vp[r] + TILE_ROW_W * r, e = vp[r + 1] + TILE_ROW_W * (r + 1);
     long long t_lo = s / TILE_CP + 1, t_hi = e / TILE_CP;
     if (t_hi > ntiles - 1) t_hi = ntiles - 1;
     for (long long t = t_lo; t <= t_hi; ++t) tile_first[t] = r + 1;
     if (classify) {
-      const long long L = e - s;
+      const long long L = vp[r + 1] - vp[r];
       if (L > TILE_CP) {
         if (L <= LONG_CAP) {
           const unsigned q = atomicAdd(n_long, 1u);
@@ -238,8 +240,12 @@ struct PipeWs {
   void* tval = nullptr;
 };
 
+inline long long pipe_ntiles(long long nrows, long long nnz_out) {
+  return (nnz_out + TILE_ROW_W * nrows) / TILE_CP + 1;
+}
+
 inline void pipe_reserve(Carver& cv, long long nrows, long long nnz_out, size_t vbytes, size_t* off) {
-  const long long ntiles = nnz_out / TILE_CP + 1;
+  const long long ntiles = pipe_ntiles(nrows, nnz_out);
   off[0] = cv.reserve(size_t(ntiles + 1) * 8);
   off[1] = cv.reserve(16 * 4);
   const long long fin_cap = 2 * (3 * (nnz_out / GROUP_CAP) + nnz_out / LONG_CAP + 16);
@@ -249,12 +255,11 @@ inline void pipe_reserve(Carver& cv, long long nrows, long long nnz_out, size_t 
   const bool need_temp = nnz_out > LONG_CAP;
   off[4] = cv.reserve(need_temp ? size_t(nnz_out) * 4 : 0);
   off[5] = cv.reserve(need_temp ? size_t(nnz_out) * vbytes : 0);
-  (void)nrows;
 }
 
-inline PipeWs pipe_bind(const Carver& cv, long long nnz_out, const size_t* off) {
+inline PipeWs pipe_bind(const Carver& cv, long long nrows, long long nnz_out, const size_t* off) {
   PipeWs w;
-  w.ntiles = nnz_out / TILE_CP + 1;
+  w.ntiles = pipe_ntiles(nrows, nnz_out);
   w.tile_first = cv.at<long long>(off[0]);
   w.counters = cv.at<unsigned>(off[1]);
   w.fin_cap = 2 * (3 * (nnz_out / GROUP_CAP) + nnz_out / LONG_CAP + 16);

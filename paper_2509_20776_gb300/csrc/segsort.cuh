@@ -17,18 +17,22 @@
 // column loads of U entries, then their map lookups, then their value loads, so that
 // U independent chains of dependent loads are in flight per thread.
 // Rows are routed by length:
-//   * rows whose source is at most CP = TILE_CAP/2 entries go through k_tile: one CTA
-//     gathers all rows of a tile of output positions into shared memory, sorts every
-//     row there and writes the tile back with the positions of a canonical CSR;
+//   * rows whose source is at most TILE_CP entries go through k_tile: one CTA gathers
+//     the rows of a tile (rows starting in one TILE_CP-wide window of the coordinate
+//     vp[r] + TILE_ROW_W * r) into shared memory, packed back to back, sorts every row
+//     there and writes them to their output positions;
 //   * rows with longer sources but at most LONG_CAP output entries: k_long, one CTA per
-//     row with a larger shared-memory capacity;
+//     row;
 //   * rows with more than LONG_CAP output entries: k_huge partitions the row by key
 //     range into 2^14 buckets (two streaming passes, through a global buffer) and hands
 //     groups of consecutive buckets of at most LONG_CAP entries to k_long.
-// The shared-memory sort ("bucket refine") splits each segment into ~len/2 buckets by
-// the high bits of its key range, scatters, and repeats on buckets larger than
-// T_SMALL; buckets of at most T_SMALL keys are finished by ranking (keys are unique
-// within a row, so every sort gives the same canonical order).
+// The shared-memory sort ("bucket-rank"): a segment of length len gets
+// 2^(ceil(log2 len) - 1) buckets spaced evenly in sqrt(key); the histogram is built
+// while loading, one block-wide exclusive scan of the counts gives every bucket's
+// output position, keys are scattered to their buckets and ranked inside them.
+// Buckets of more than T_RANK keys (rare) are refined by repeated bucketing over their
+// own [min, max] until at most T_SMALL keys remain, then ranked.  Keys are unique
+// within a row, so every correct sort gives the same canonical order.
 #pragma once
 
 #include "common.cuh"
@@ -112,6 +116,7 @@ constexpr int T_RANK = 32;   // bucket-rank ranks buckets of up to this many key
 constexpr int TILE_BLOCK = 256;
 constexpr int TILE_CAP = 2048;
 constexpr int TILE_CP = TILE_CAP / 2;  // longest source row a tile accepts
+constexpr int TILE_ROW_W = 4;          // tile partition weight of a row (bounds rows/tile)
 constexpr int LONG_BLOCK = 512;
 constexpr int LONG_CAP = 4096;
 constexpr int HUGE_BLOCK = 1024;
@@ -335,15 +340,22 @@ __device__ __forceinline__ BRView carve_br(unsigned char* raw) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t br_slot(uint32_t sg, uint32_t k, int key_bits) {
+// Bucket of key k in its segment: nb = 2^(ceil(log2 len) - 1) buckets spaced evenly in
+// sqrt(k) over [0, 2^key_bits).  Any non-decreasing map keeps buckets in key order;
+// the square root stays balanced both for uniformly relabelled columns and for
+// orderings that crowd keys at the low end (degree-descending relabelling of a
+// power-law graph), where evenly spaced buckets in k overflow.  `isr` is
+// 2^(-key_bits/2).
+__device__ __forceinline__ uint32_t br_slot(uint32_t sg, uint32_t k, float isr) {
   const uint32_t len = sg & 0xFFFFu, s = sg >> 16;
   const int nbl = len > 1 ? ceil_log2_u32(len) - 1 : 0;
-  const int sh = key_bits > nbl ? key_bits - nbl : 0;
-  uint32_t b = sh < 32 ? (k >> sh) : 0u;
   const uint32_t nb = 1u << nbl;
+  uint32_t b = uint32_t(sqrtf(float(k)) * (float(nb) * isr));
   if (b >= nb) b = nb - 1;  // keys beyond key_bits only come from invalid input
   return s + b;
 }
+
+__device__ __forceinline__ float br_isr(int key_bits) { return exp2f(-0.5f * float(key_bits)); }
 
 // Sorts the segments of entries [0, E); on return ord[0 .. n) holds the entry index for
 // every sorted position (n = number of used entries) and key[] is unchanged.
@@ -369,12 +381,13 @@ __device__ int bucket_rank_sort(const BRView& v, int E, int key_bits, uint32_t* 
                                 DevStatus* st, bool hist_done = false) {
   constexpr int ITEMS = CAP / BLOCK;
   const int t = threadIdx.x;
+  const float isr = br_isr(key_bits);
   if (!hist_done) {
     for (int x = t; x < E; x += BLOCK) v.cnt[x] = 0;
     __syncthreads();
     for (int x = t; x < E; x += BLOCK) {
       const uint32_t sg = v.seg[x];
-      if (sg & 0xFFFFu) atomicAdd(&v.cnt[br_slot(sg, v.key[x], key_bits)], 1u);
+      if (sg & 0xFFFFu) atomicAdd(&v.cnt[br_slot(sg, v.key[x], isr)], 1u);
     }
   }
   __syncthreads();
@@ -384,7 +397,7 @@ __device__ int bucket_rank_sort(const BRView& v, int E, int key_bits, uint32_t* 
     const uint32_t sg = v.seg[x];
     if (!(sg & 0xFFFFu)) continue;
     const uint32_t k = v.key[x];
-    const uint32_t slot = br_slot(sg, k, key_bits);
+    const uint32_t slot = br_slot(sg, k, isr);
     const uint32_t p = atomicAdd(&v.cnt[slot], 1u);
     if (p < uint32_t(CAP)) {
       v.tkey[p] = k;
@@ -444,12 +457,13 @@ __device__ void br_finish(const BRView& v, int E, int key_bits, uint32_t* tmp32,
                           const Out& out) {
   constexpr int ITEMS = CAP / BLOCK;
   const int t = threadIdx.x;
+  const float isr = br_isr(key_bits);
   const int n = int(smem_excl_sum<BLOCK, ITEMS>(v.cnt, E, tmp32));
   for (int x = t; x < E; x += BLOCK) {
     const uint32_t sg = v.seg[x];
     if (!(sg & 0xFFFFu)) continue;
     const uint32_t k = v.key[x];
-    const uint32_t slot = br_slot(sg, k, key_bits);
+    const uint32_t slot = br_slot(sg, k, isr);
     const uint32_t p = atomicAdd(&v.cnt[slot], 1u);
     if (p < uint32_t(CAP)) {
       v.tkey[p] = k;
@@ -552,6 +566,7 @@ __global__ void __launch_bounds__(TILE_BLOCK, 3)
   __shared__ uint32_t tmp32[BLOCK / 32 + 1];
   __shared__ uint32_t sE;
   const int t = threadIdx.x;
+  const float isr = br_isr(key_bits);
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long r0 = tile_first[tile], r1 = tile_first[tile + 1];
@@ -649,7 +664,7 @@ __global__ void __launch_bounds__(TILE_BLOCK, 3)
               sval[lp] = bt.v[u];
               b.seg[lp] = sg;
               sdel[lp] = uint16_t(r_os[kr[u]] - r_ls[kr[u]]);
-              atomicAdd(&b.cnt[br_slot(sg, bt.key[u], key_bits)], 1u);  // histogram
+              atomicAdd(&b.cnt[br_slot(sg, bt.key[u], isr)], 1u);  // histogram
             } else {
               dev_fail(st, SP_ERR_INTERNAL, -3);
             }
@@ -691,6 +706,7 @@ __global__ void __launch_bounds__(LONG_BLOCK, 2)
   __shared__ unsigned s_item;
   __shared__ uint32_t s_cur;
   const int t = threadIdx.x;
+  const float isr = br_isr(key_bits);
   const bool src_mode = rows != nullptr;
   unsigned count = src_mode ? *nrows_p : *nruns_p;
   if (count > list_cap) count = unsigned(list_cap);  // overflow was reported by the producer
@@ -741,7 +757,7 @@ __global__ void __launch_bounds__(LONG_BLOCK, 2)
           if (c < uint32_t(E)) {
             b.key[c] = bt.key[u];
             eoff[c] = uint32_t(e);
-            atomicAdd(&b.cnt[br_slot(uint32_t(E), bt.key[u], key_bits)], 1u);  // histogram
+            atomicAdd(&b.cnt[br_slot(uint32_t(E), bt.key[u], isr)], 1u);  // histogram
           } else {
             dev_fail(st, SP_ERR_INTERNAL, -4);
           }
@@ -763,7 +779,7 @@ __global__ void __launch_bounds__(LONG_BLOCK, 2)
         const uint32_t k = buf == BUF_TEMP ? ld_stream(tkey + g0 + x) : uint32_t(out_col[g0 + x]);
         b.key[x] = k;
         eoff[x] = uint32_t(x);
-        atomicAdd(&b.cnt[br_slot(uint32_t(E), k, key_bits)], 1u);  // histogram
+        atomicAdd(&b.cnt[br_slot(uint32_t(E), k, isr)], 1u);  // histogram
       }
     }
     for (int x = t; x < E; x += BLOCK) b.seg[x] = uint32_t(E);  // one segment at 0

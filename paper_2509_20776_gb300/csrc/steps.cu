@@ -72,7 +72,7 @@ sp_status sort_rows_impl(sp_ctx* ctx, sp_csr* M, cudaStream_t s) {
   lists.long_cap = long_cap;
   lists.huge_cap = huge_cap;
   SP_CUDA(cudaMemsetAsync(lists.n_long, 0, 64, s));
-  PipeWs w = pipe_bind(cv, nnz, po);
+  PipeWs w = pipe_bind(cv, m, nnz, po);
   SortLoader<RP, CI, VT> ld{static_cast<const RP*>(M->rowptr), static_cast<const CI*>(M->colidx),
                             static_cast<const VT*>(M->values), m, M->ncols, nnz};
   const int kb = ceil_log2_u64(uint64_t(M->ncols));
