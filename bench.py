@@ -155,12 +155,16 @@ def permute_workload(scale: int, device):
     return A, [("PAPt_random", p, p), ("PAPt_degree", pdeg, pdeg), ("PAQt_random", p, q)]
 
 
+TILE_CP, LONG_CAP = 1024, 4096  # row-length limits of the tile and long-row kernels
+
+
 def row_classes(rowptr):
-    """Entries / non-empty rows handled by the tile (<=2048), long and huge (>8192) kernels."""
+    """Entries / non-empty rows handled by the tile (<= TILE_CP), long and huge
+    (> LONG_CAP) kernels of the permutation (row lengths move with the rows)."""
     import torch
     L = (rowptr[1:] - rowptr[:-1]).to(torch.int64)
-    small = L <= 2048
-    huge = L > 8192
+    small = L <= TILE_CP
+    huge = L > LONG_CAP
     long_ = (~small) & (~huge)
     out = {}
     for name, m in (("tile", small), ("long", long_), ("huge", huge)):
@@ -357,14 +361,18 @@ def bench_extract(ctx, args, dev, hbm, ws):
     B = ctx.sp_extract(Ad, I, J)
     nnz_out = B.nnz
     del B
-    ctx.phase_stats(reset=True)
+    from paper_2509_20776_gb300 import SP_OPT_TIMING
 
     def step():
         ctx.sp_extract(Ad, I, J, sync=False)
 
     steps = max(1, args.steps // 2)
+    ctx.phase_stats(reset=True)
+    ctx.set_option(SP_OPT_TIMING, 1)
     ms = time_steps(step, steps, 1, ws)
     ctx.sync()
+    ctx.set_option(SP_OPT_TIMING, 0)
+    phases = {k: round(v[0] / (steps + 1), 3) for k, v in ctx.phase_stats(reset=True).items() if v[1]}
     ms = max_over_ranks(ms, ws)
     # nnz_sel*sc + nnz_out*(sv+sc+sv) + |I|(s_i+2 sr) + |J| s_i + n s_i + |J| s_i + |I| sr
     L = (A.rowptr[1:] - A.rowptr[:-1])
@@ -375,7 +383,7 @@ def bench_extract(ctx, args, dev, hbm, ws):
     return {"workload": "ER n=2^26, 32 draws/row; A(I,J), random distinct |I|=|J|=2^25",
             "nnz_in": A.nnz, "nnz_out": nnz_out, "value": round(value, 1), "unit": UNIT,
             "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
-            "alg_bytes_per_op": ab}
+            "alg_bytes_per_op": ab, "phase_ms_per_op": phases}
 
 
 def bench_assign(ctx, args, dev, hbm, ws):
@@ -399,13 +407,18 @@ def bench_assign(ctx, args, dev, hbm, ws):
     roundtrip = bool(torch.equal(E.rowptr, Bd.rowptr) and torch.equal(E.colidx, Bd.colidx) and
                      torch.equal(E.values.view(torch.int32), Bd.values.view(torch.int32)))
     del Ap, E
+    from paper_2509_20776_gb300 import SP_OPT_TIMING
 
     def step():
         ctx.sp_assign(Ad, I, J, Bd, sync=False)
 
     steps = max(1, args.steps // 2)
+    ctx.phase_stats(reset=True)
+    ctx.set_option(SP_OPT_TIMING, 1)
     ms = time_steps(step, steps, 1, ws)
     ctx.sync()
+    ctx.set_option(SP_OPT_TIMING, 0)
+    phases = {k: round(v[0] / (steps + 1), 3) for k, v in ctx.phase_stats(reset=True).items() if v[1]}
     ms = max_over_ranks(ms, ws)
     m = A.nrows
     ab = A.nnz * 8 + nnz_out * 8 + 2 * (m + 1) * 8 + Bm.nnz * 8 + (k + 1) * 8 + k * 4 + k * 4 + m * 4 + A.ncols // 8
@@ -414,7 +427,8 @@ def bench_assign(ctx, args, dev, hbm, ws):
     return {"workload": "R-MAT scale 26 ef 24; A(I,J)=B, B ER 2^22 x 2^22 8/row, random I,J",
             "nnz_in": A.nnz, "nnz_B": Bm.nnz, "nnz_out": nnz_out, "value": round(value, 1),
             "unit": UNIT, "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
-            "alg_bytes_per_op": ab, "extract_after_assign_equals_B": roundtrip}
+            "alg_bytes_per_op": ab, "extract_after_assign_equals_B": roundtrip,
+            "phase_ms_per_op": phases}
 
 
 # ---------------------------------------------------------------------------------------

@@ -41,13 +41,50 @@ template <class T>
 __device__ __forceinline__ T ld_stream(const T* p) {
   return __ldcs(p);
 }
-template <class T>
-__device__ __forceinline__ T ld_map(const T* p) {
-  return __ldg(p);
+// Index-map lookups (random, reused) are tagged L2 evict-last through a cache policy,
+// so the write-once output and streamed inputs (evict-first) leave the maps in L2.
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
+__device__ __forceinline__ int ld_map(const int* p) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;"
+               : "=r"(v)
+               : "l"(p), "l"(l2_keep_policy()));
+  return v;
+}
+__device__ __forceinline__ long long ld_map(const long long* p) {
+  long long v;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;"
+               : "=l"(v)
+               : "l"(p), "l"(l2_keep_policy()));
+  return v;
+}
+__device__ __forceinline__ long ld_map(const long* p) {
+  return (long)ld_map(reinterpret_cast<const long long*>(p));
+}
+__device__ __forceinline__ unsigned ld_map(const unsigned* p) {
+  unsigned v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;"
+               : "=r"(v)
+               : "l"(p), "l"(l2_keep_policy()));
+  return v;
+}
+// Write-once output: store with the evict-first (streaming) hint.
 template <class T>
 __device__ __forceinline__ void st_stream(T* p, T v) {
-  __stcs(p, v);
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte words");
+  if constexpr (sizeof(T) == 4) {
+    unsigned u;
+    memcpy(&u, &v, 4);
+    __stcs(reinterpret_cast<unsigned*>(p), u);
+  } else {
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    __stcs(reinterpret_cast<unsigned long long*>(p), u);
+  }
 }
 
 // ---- relaxed 64-bit status words (decoupled look-back) -------------------------

@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(GATHER_BLOCK) k_gather_rows(Gs gs, const long 
       for (int u = 0; u < H; ++u) {
         if (!ok[u]) continue;
         const long long g = c0 + t + (h + u) * B;
-        out_col[g] = c[u];
-        out_val[g] = v[u];
+        st_stream(out_col + g, c[u]);
+        st_stream(out_val + g, v[u]);
       }
     }
     __syncthreads();

@@ -531,8 +531,8 @@ struct TileOut {
   long long base;
   __device__ __forceinline__ void operator()(uint32_t f, uint32_t x, uint32_t k) const {
     const long long g = base + f + sdel[x];
-    out_col[g] = CI(k);
-    out_val[g] = sval[x];
+    st_stream(out_col + g, CI(k));
+    st_stream(out_val + g, sval[x]);
   }
 };
 
@@ -810,8 +810,8 @@ __global__ void __launch_bounds__(LONG_BLOCK, 2)
     for (int j = 0; j < ITEMS; ++j) {
       const int f = t + j * BLOCK;
       if (f < n) {
-        out_col[g0 + f] = CI(kk[j]);
-        out_val[g0 + f] = vv[j];
+        st_stream(out_col + g0 + f, CI(kk[j]));
+        st_stream(out_val + g0 + f, vv[j]);
       }
     }
     __syncthreads();
