@@ -222,7 +222,7 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   Carver cv;
   const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
   const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
-  size_t po[6];
+  size_t po[kPipeSlots];
   pipe_reserve(cv, nI, nt, sizeof(VT), po);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));

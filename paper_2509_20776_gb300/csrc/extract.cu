@@ -168,7 +168,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   SP_TRY(store_rowptr(ctx, s, pl->vp, nI + 1, B->rowptr_type, B->rowptr));
   if (nnz_out == 0) return SP_OK;
   Carver cv;
-  size_t po[6];
+  size_t po[kPipeSlots];
   pipe_reserve(cv, nI, nnz_out, sizeof(VT), po);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));

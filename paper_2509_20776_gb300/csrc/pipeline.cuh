@@ -155,7 +155,8 @@ inline size_t scan_ws_bytes(long long n) {
 
 // Exclusive scan of n values into n+1 outputs; `ws` must hold scan_ws_bytes(n).
 template <class Load, class Store>
-sp_status launch_scan(sp_ctx* ctx, cudaStream_t s, Load load, Store store, long long n, char* ws) {
+sp_status launch_scan(sp_ctx* ctx, cudaStream_t s, Load load, Store store, long long n, char* ws,
+                      int phase = SP_PHASE_SCAN) {
   long long tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (tiles == 0) tiles = 1;
   ScanCtl c;
@@ -168,7 +169,7 @@ sp_status launch_scan(sp_ctx* ctx, cudaStream_t s, Load load, Store store, long 
   SP_CUDA(cudaMemsetAsync(ws, 0, scan_ws_bytes(n), s));
   if (tiles > 0x7fffffffll) return SP_ERR_OVERFLOW;
   {
-    SP_PHASE(SP_PHASE_SCAN);
+    SP_PHASE(phase);
     k_scan<Load, Store><<<unsigned(tiles), SCAN_BLOCK, 0, s>>>(load, store, c);
   }
   SP_CUDA(cudaGetLastError());
@@ -176,30 +177,54 @@ sp_status launch_scan(sp_ctx* ctx, cudaStream_t s, Load load, Store store, long 
 }
 
 // ------------------------------------------------------------------------------
-// Tile partition: tile t of the output covers the rows whose first output position
-// lies in [t*CP, (t+1)*CP).  Rows whose source is longer than CP are skipped by the
-// tile kernel, so a tile never holds more than 2*CP entries.  With `classify`, rows
-// longer than CP (source = output length, e.g. permutation) are also listed for the
-// long-row or huge-row kernels.
+// Tile partition, computed by one more scan over the listed rows.  Row r weighs
+// TILE_ROW_W plus its output length when the tile kernel sorts it (output length at
+// most TILE_CP), so that rows left to k_long / k_huge take no room; c(r) is the
+// exclusive prefix of the weights and tile t holds the rows with c(r) in
+// [t*TILE_CP, (t+1)*TILE_CP): at most 2*TILE_CP entries and TILE_CP/TILE_ROW_W rows.
+// The store of the scan writes tile_first[] directly; with `classify` (source length =
+// output length, e.g. permutation) it also lists the rows left to k_long / k_huge.
+// The number of tiles is written to *ntiles (tile_first[*ntiles] = nrows).
 // ------------------------------------------------------------------------------
-// ---- tile partition --------------------------------------------------------------
-template <int kDummy = 0>
-__global__ void k_partition(const long long* __restrict__ vp, long long nrows, long long ntiles,
-                              long long* __restrict__ tile_first, int classify,
-                              long long* long_rows, unsigned* n_long, long long long_cap,
-                              long long* huge_rows, unsigned* n_huge, long long huge_cap,
-                              DevStatus* st) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    tile_first[0] = 0;
-    tile_first[ntiles] = nrows;
-  }
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows;
-       r += (long long)gridDim.x * blockDim.x) {
-    // tiles cut the coordinate vp[r] + TILE_ROW_W * r, so a tile holds at most
-    // TILE_CP / TILE_ROW_W + 1 rows even where many rows are empty
-    const long long s = vp[r] + TILE_ROW_W * r, e = vp[r + 1] + TILE_ROW_W * (r + 1);
-    long long t_lo = s / TILE_CP + 1, t_hi = e / TILE_CP;
-    if (t_hi > ntiles - 1) t_hi = ntiles - 1;
+__device__ __forceinline__ long long tile_weight(const long long* vp, long long r) {
+  const long long L = vp[r + 1] - vp[r];
+  return TILE_ROW_W + (L <= TILE_CP ? L : 0);
+}
+
+struct TileWeight {
+  const long long* vp;
+  __device__ long long operator()(long long r) const { return tile_weight(vp, r); }
+};
+
+struct PartitionStore {
+  const long long* vp;
+  long long nrows;
+  long long ntiles_cap;  // tile_first holds ntiles_cap + 1 entries
+  long long* tile_first;
+  long long* ntiles;
+  int classify;
+  long long* long_rows;
+  unsigned* n_long;
+  long long long_cap;
+  long long* huge_rows;
+  unsigned* n_huge;
+  long long huge_cap;
+  DevStatus* st;
+  __device__ void operator()(long long r, long long c) const {
+    if (r == nrows) {  // c = total weight
+      long long nt = c / TILE_CP + 1;
+      if (nt > ntiles_cap) {
+        dev_fail(st, SP_ERR_INTERNAL, -14);
+        nt = ntiles_cap;
+      }
+      *ntiles = nt;
+      tile_first[nt] = nrows;
+      return;
+    }
+    if (r == 0) tile_first[0] = 0;
+    const long long e = c + tile_weight(vp, r);
+    long long t_lo = c / TILE_CP + 1, t_hi = e / TILE_CP;
+    if (t_hi > ntiles_cap - 1) t_hi = ntiles_cap - 1;
     for (long long t = t_lo; t <= t_hi; ++t) tile_first[t] = r + 1;
     if (classify) {
       const long long L = vp[r + 1] - vp[r];
@@ -216,7 +241,7 @@ __global__ void k_partition(const long long* __restrict__ vp, long long nrows, l
       }
     }
   }
-}
+};
 
 struct PipeLists {
   long long* long_rows = nullptr;  // rows for k_long in source mode
@@ -232,6 +257,8 @@ struct PipeWs {
   long long* tile_first = nullptr;
   long long ntiles = 0;
   unsigned* counters = nullptr;  // [0..3] tickets, [4] n_final, [5] n_next
+  long long* ntiles_dev = nullptr;  // number of tiles, written by the partition
+  char* scan_ws = nullptr;          // workspace of the partition scan
   FinalEntry* fin = nullptr;
   long long fin_cap = 0;
   HugeEntry* nxt = nullptr;
@@ -244,6 +271,8 @@ inline long long pipe_ntiles(long long nrows, long long nnz_out) {
   return (nnz_out + TILE_ROW_W * nrows) / TILE_CP + 1;
 }
 
+constexpr int kPipeSlots = 8;  // workspace slots reserved by pipe_reserve
+
 inline void pipe_reserve(Carver& cv, long long nrows, long long nnz_out, size_t vbytes, size_t* off) {
   const long long ntiles = pipe_ntiles(nrows, nnz_out);
   off[0] = cv.reserve(size_t(ntiles + 1) * 8);
@@ -255,6 +284,8 @@ inline void pipe_reserve(Carver& cv, long long nrows, long long nnz_out, size_t 
   const bool need_temp = nnz_out > LONG_CAP;
   off[4] = cv.reserve(need_temp ? size_t(nnz_out) * 4 : 0);
   off[5] = cv.reserve(need_temp ? size_t(nnz_out) * vbytes : 0);
+  off[6] = cv.reserve(scan_ws_bytes(nrows));
+  off[7] = cv.reserve(8);
 }
 
 inline PipeWs pipe_bind(const Carver& cv, long long nrows, long long nnz_out, const size_t* off) {
@@ -268,6 +299,8 @@ inline PipeWs pipe_bind(const Carver& cv, long long nrows, long long nnz_out, co
   w.nxt = cv.at<HugeEntry>(off[3]);
   w.tkey = cv.at<uint32_t>(off[4]);
   w.tval = cv.at<void>(off[5]);
+  w.scan_ws = cv.at<char>(off[6]);
+  w.ntiles_dev = cv.at<long long>(off[7]);
   return w;
 }
 
@@ -288,21 +321,20 @@ sp_status run_pipeline(sp_ctx* ctx, cudaStream_t s, const Ld& ld, const long lon
   if (nrows == 0 || nnz_out == 0) return SP_OK;
   SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
   const int nsm = ctx->num_sms;
-  {
-    SP_PHASE(SP_PHASE_PARTITION);
-    k_partition<0><<<grid_for(nrows, 256, nsm * 16), 256, 0, s>>>(
-        vp, nrows, w.ntiles, w.tile_first, classify ? 1 : 0, lists.long_rows, lists.n_long,
-        lists.long_cap, lists.huge_rows, lists.n_huge, lists.huge_cap, ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
+  SP_TRY(launch_scan(ctx, s, TileWeight{vp},
+                     PartitionStore{vp, nrows, w.ntiles, w.tile_first, w.ntiles_dev, classify ? 1 : 0,
+                                    lists.long_rows, lists.n_long, lists.long_cap, lists.huge_rows,
+                                    lists.n_huge, lists.huge_cap, ctx->dstatus},
+                     nrows, w.scan_ws, SP_PHASE_PARTITION));
   {
     constexpr size_t sm = tile_smem_bytes<Ld>();
     static bool once = (set_smem(k_tile<Ld>, sm), true);
     (void)once;
-    const long long g = w.ntiles < 0x7fffffffll ? w.ntiles : 0x7fffffffll;
+    // persistent: TILE_PER_SM resident CTAs per SM walk the tiles
+    const long long g = w.ntiles < (long long)nsm * TILE_PER_SM ? w.ntiles : (long long)nsm * TILE_PER_SM;
     {
       SP_PHASE(SP_PHASE_TILE);
-      k_tile<Ld><<<unsigned(g), TILE_BLOCK, sm, s>>>(ld, vp, w.tile_first, w.ntiles, out_col,
+      k_tile<Ld><<<unsigned(g), TILE_BLOCK, sm, s>>>(ld, vp, w.tile_first, w.ntiles_dev, out_col,
                                                       out_val, key_bits, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());

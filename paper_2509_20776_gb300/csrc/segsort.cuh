@@ -511,8 +511,6 @@ __device__ void br_finish(const BRView& v, int E, int key_bits, uint32_t* tmp32,
   __syncthreads();
 }
 
-struct TileOutBase {};
-
 // ------------------------------------------------------------------------------
 // Tile kernel: rows with short sources, many rows per CTA.
 // ------------------------------------------------------------------------------
@@ -527,10 +525,11 @@ struct TileOut {
   CI* out_col;
   VT* out_val;
   const VT* sval;
-  const uint16_t* sdel;
+  const uint16_t* srow;  // row (within the tile) of each packed entry
+  const uint32_t* rdel;  // per row: output offset - packed offset
   long long base;
   __device__ __forceinline__ void operator()(uint32_t f, uint32_t x, uint32_t k) const {
-    const long long g = base + f + sdel[x];
+    const long long g = base + f + rdel[srow[x]];
     st_stream(out_col + g, CI(k));
     st_stream(out_val + g, sval[x]);
   }
@@ -538,144 +537,146 @@ struct TileOut {
 
 // Tile layout: the rows of a tile that the tile handles are packed back to back in
 // shared memory (rows whose source is long are skipped and may sit anywhere in the
-// tile); sdel[x] = output position - packed position of entry x.
+// tile's output range); srow[x] is the row of packed entry x and rdel[row] = output
+// offset - packed offset of that row.  A tile holds at most TILE_BLOCK rows (the
+// partition gives every row a weight of TILE_ROW_W in a window of TILE_CP).
+constexpr int TILE_PER_SM = 3;
+
 template <class Ld>
-__global__ void __launch_bounds__(TILE_BLOCK, 3)
+__global__ void __launch_bounds__(TILE_BLOCK, TILE_PER_SM)
     k_tile(Ld ld, const long long* __restrict__ vp, const long long* __restrict__ tile_first,
-           long long ntiles, typename Ld::CI* __restrict__ out_col,
+           const long long* __restrict__ ntiles_p, typename Ld::CI* __restrict__ out_col,
            typename Ld::VT* __restrict__ out_val, int key_bits, DevStatus* st) {
   using VT = typename Ld::VT;
   using CI = typename Ld::CI;
   constexpr int BLOCK = TILE_BLOCK, CAP = TILE_CAP, ITEMS = CAP / BLOCK;
+  static_assert(TILE_CP / TILE_ROW_W <= BLOCK, "a tile's rows must fit one pass");
   extern __shared__ __align__(16) unsigned char smem[];
   VT* sval = reinterpret_cast<VT*>(smem);
   BRView b = carve_br<CAP>(smem + size_t(CAP) * sizeof(VT));
-  uint16_t* sdel = reinterpret_cast<uint16_t*>(smem + size_t(CAP) * sizeof(VT) + br_smem_bytes<CAP>());
-  uint16_t* owner = sdel + CAP;  // row (within the chunk) of each source position
+  uint16_t* srow = reinterpret_cast<uint16_t*>(smem + size_t(CAP) * sizeof(VT) + br_smem_bytes<CAP>());
+  uint16_t* owner = srow + CAP;  // row of each source position
   unsigned char* p = smem + ((size_t(CAP) * sizeof(VT) + br_smem_bytes<CAP>() + size_t(CAP) * 4 + 15) &
                              ~size_t(15));
   long long* r_s0 = reinterpret_cast<long long*>(p);
   long long* r_s1 = r_s0 + BLOCK;
   uint32_t* r_n0 = reinterpret_cast<uint32_t*>(r_s1 + BLOCK);
   uint32_t* r_ls = r_n0 + BLOCK;   // packed start
-  uint32_t* r_os = r_ls + BLOCK;   // output start (relative to the tile base)
-  uint32_t* r_lo = r_os + BLOCK;   // output length
-  uint32_t* r_sp = r_lo + BLOCK;   // source prefix within the chunk
+  uint32_t* r_del = r_ls + BLOCK;  // output offset (from the tile base) - packed start
+  uint32_t* r_lo = r_del + BLOCK;  // output length
+  uint32_t* r_sp = r_lo + BLOCK;   // source prefix within the tile
   uint32_t* r_cur = r_sp + BLOCK;  // kept cursor
   __shared__ unsigned long long tmp64[BLOCK / 32 + 1];
   __shared__ uint32_t tmp32[BLOCK / 32 + 1];
-  __shared__ uint32_t sE;
   const int t = threadIdx.x;
   const float isr = br_isr(key_bits);
+  const long long ntiles = *ntiles_p;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long r0 = tile_first[tile], r1 = tile_first[tile + 1];
+    if (r1 - r0 > BLOCK) {  // cannot happen: see the partition
+      if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -13);
+      continue;
+    }
     const long long base = vp[r0];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       b.seg[t + j * BLOCK] = 0;
       b.cnt[t + j * BLOCK] = 0;
     }
-    if (t == 0) sE = 0;
-    __syncthreads();
-    for (long long rc = r0; rc < r1; rc += BLOCK) {
-      const long long r = rc + t;
-      uint32_t Ls = 0, Lk = 0;
-      long long o0 = 0;
-      RowSrc rs{0, 0, 0, 0};
-      if (r < r1) {
-        o0 = vp[r];
-        const long long Lo = vp[r + 1] - o0;
-        if (Lo > 0) {
-          rs = ld.row(r);
-          const long long ls = rs.n0 + rs.n1;
-          if (ls <= TILE_CP) {  // longer sources are handled by k_long / k_huge
-            if (o0 - base + Lo > CAP || Lo > TILE_CP) {
-              dev_fail(st, SP_ERR_INTERNAL, r);
-            } else {
-              Ls = uint32_t(ls);
-              Lk = uint32_t(Lo);
-            }
+    const long long r = r0 + t;
+    uint32_t Ls = 0, Lk = 0;
+    long long o0 = 0;
+    RowSrc rs{0, 0, 0, 0};
+    if (r < r1) {
+      o0 = vp[r];
+      const long long Lo = vp[r + 1] - o0;
+      if (Lo > 0) {
+        rs = ld.row(r);
+        const long long ls = rs.n0 + rs.n1;
+        if (ls <= TILE_CP) {  // longer sources are handled by k_long / k_huge
+          if (Lo > TILE_CP || o0 - base + Lo > 0xFFFFFFFFll) {
+            dev_fail(st, SP_ERR_INTERNAL, r);
+          } else {
+            Ls = uint32_t(ls);
+            Lk = uint32_t(Lo);
           }
         }
       }
-      // packed starts (low half) and source prefixes (high half) in one block scan
-      unsigned long long tot;
-      const unsigned long long pre =
-          block_excl_sum<BLOCK>((unsigned long long)Lk | ((unsigned long long)Ls << 32), tmp64, &tot);
-      const uint32_t e_base = sE;
-      const uint32_t ls_packed = e_base + uint32_t(pre & 0xFFFFFFFFull);
-      const uint32_t sp = uint32_t(pre >> 32);
-      uint32_t S = uint32_t(tot >> 32);
-      if (e_base + uint32_t(tot & 0xFFFFFFFFull) > uint32_t(CAP)) {  // cannot happen: see k_partition
-        if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -13);
-        Ls = 0;
-        S = 0;
-      }
-      if (Ls > 0) {
-        r_s0[t] = rs.s0;
-        r_s1[t] = rs.s1;
-        r_n0[t] = uint32_t(rs.n0);
-        r_ls[t] = ls_packed;
-        r_os[t] = uint32_t(o0 - base);
-        r_lo[t] = Lk;
-        r_cur[t] = 0;
-      }
-      r_sp[t] = sp;
-      __syncthreads();
-      if (t == 0 && e_base + uint32_t(tot & 0xFFFFFFFFull) <= uint32_t(CAP))
-        sE = e_base + uint32_t(tot & 0xFFFFFFFFull);
-      for (uint32_t w0 = 0; w0 < S; w0 += CAP) {
-        const uint32_t W = S - w0 < uint32_t(CAP) ? S - w0 : uint32_t(CAP);
-        for (uint32_t x = t; x < W; x += BLOCK) owner[x] = 0;
-        __syncthreads();
-        if (Ls > 0) {
-          if (sp >= w0 && sp < w0 + W) owner[sp - w0] = uint16_t(t);
-          else if (sp < w0 && sp + Ls > w0) owner[0] = uint16_t(t);
-        }
-        __syncthreads();
-        smem_incl_max16<BLOCK, ITEMS>(owner, int(W), tmp32);
-        for (uint32_t x0 = t; x0 < W; x0 += BLOCK * LOAD_U) {
-          Batch<Ld, LOAD_U> bt;
-          uint32_t kr[LOAD_U], off[LOAD_U];
-#pragma unroll
-          for (int u = 0; u < LOAD_U; ++u) {
-            const uint32_t x = x0 + u * BLOCK;
-            bt.valid[u] = x < W;
-            kr[u] = 0;
-            off[u] = 0;
-            if (bt.valid[u]) {
-              kr[u] = owner[x];
-              off[u] = w0 + x - r_sp[kr[u]];
-              const uint32_t n0 = r_n0[kr[u]];
-              bt.part[u] = off[u] < n0 ? 0 : 1;
-              bt.pos[u] = bt.part[u] ? r_s1[kr[u]] + (off[u] - n0) : r_s0[kr[u]] + off[u];
-            }
-          }
-          bt.run(ld);
-#pragma unroll
-          for (int u = 0; u < LOAD_U; ++u) {
-            if (!bt.kept[u]) continue;
-            const uint32_t c = Ld::kAllKept ? off[u] : atomicAdd(&r_cur[kr[u]], 1u);
-            if (c < r_lo[kr[u]]) {
-              const uint32_t lp = r_ls[kr[u]] + c;
-              const uint32_t sg = (r_ls[kr[u]] << 16) | r_lo[kr[u]];
-              b.key[lp] = bt.key[u];
-              sval[lp] = bt.v[u];
-              b.seg[lp] = sg;
-              sdel[lp] = uint16_t(r_os[kr[u]] - r_ls[kr[u]]);
-              atomicAdd(&b.cnt[br_slot(sg, bt.key[u], isr)], 1u);  // histogram
-            } else {
-              dev_fail(st, SP_ERR_INTERNAL, -3);
-            }
-          }
-        }
-        __syncthreads();
-      }
-      __syncthreads();  // sE of this chunk is visible before the next chunk reads it
     }
-    const int E = int(sE);
-    br_finish<BLOCK, CAP>(b, E, key_bits, tmp32, st, TileOut<CI, VT>{out_col, out_val, sval, sdel, base});
+    // packed starts (low half) and source prefixes (high half) in one block scan
+    unsigned long long tot;
+    const unsigned long long pre =
+        block_excl_sum<BLOCK>((unsigned long long)Lk | ((unsigned long long)Ls << 32), tmp64, &tot);
+    const uint32_t ls_packed = uint32_t(pre & 0xFFFFFFFFull);
+    const uint32_t sp = uint32_t(pre >> 32);
+    uint32_t S = uint32_t(tot >> 32);
+    int E = int(tot & 0xFFFFFFFFull);
+    if (E > CAP) {  // cannot happen: see the partition
+      if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -12);
+      Ls = 0;
+      S = 0;
+      E = 0;
+    }
+    if (Ls > 0) {
+      r_s0[t] = rs.s0;
+      r_s1[t] = rs.s1;
+      r_n0[t] = uint32_t(rs.n0);
+      r_ls[t] = ls_packed;
+      r_del[t] = uint32_t(o0 - base) - ls_packed;
+      r_lo[t] = Lk;
+      r_cur[t] = 0;
+    }
+    r_sp[t] = sp;
+    __syncthreads();
+    for (uint32_t w0 = 0; w0 < S; w0 += CAP) {
+      const uint32_t W = S - w0 < uint32_t(CAP) ? S - w0 : uint32_t(CAP);
+      for (uint32_t x = t; x < W; x += BLOCK) owner[x] = 0;
+      __syncthreads();
+      if (Ls > 0) {
+        if (sp >= w0 && sp < w0 + W) owner[sp - w0] = uint16_t(t);
+        else if (sp < w0 && sp + Ls > w0) owner[0] = uint16_t(t);
+      }
+      __syncthreads();
+      smem_incl_max16<BLOCK, ITEMS>(owner, int(W), tmp32);
+      for (uint32_t x0 = t; x0 < W; x0 += BLOCK * LOAD_U) {
+        Batch<Ld, LOAD_U> bt;
+        uint32_t kr[LOAD_U], off[LOAD_U];
+#pragma unroll
+        for (int u = 0; u < LOAD_U; ++u) {
+          const uint32_t x = x0 + u * BLOCK;
+          bt.valid[u] = x < W;
+          kr[u] = 0;
+          off[u] = 0;
+          if (bt.valid[u]) {
+            kr[u] = owner[x];
+            off[u] = w0 + x - r_sp[kr[u]];
+            const uint32_t n0 = r_n0[kr[u]];
+            bt.part[u] = off[u] < n0 ? 0 : 1;
+            bt.pos[u] = bt.part[u] ? r_s1[kr[u]] + (off[u] - n0) : r_s0[kr[u]] + off[u];
+          }
+        }
+        bt.run(ld);
+#pragma unroll
+        for (int u = 0; u < LOAD_U; ++u) {
+          if (!bt.kept[u]) continue;
+          const uint32_t c = Ld::kAllKept ? off[u] : atomicAdd(&r_cur[kr[u]], 1u);
+          if (c < r_lo[kr[u]]) {
+            const uint32_t lp = r_ls[kr[u]] + c;
+            const uint32_t sg = (r_ls[kr[u]] << 16) | r_lo[kr[u]];
+            b.key[lp] = bt.key[u];
+            sval[lp] = bt.v[u];
+            b.seg[lp] = sg;
+            srow[lp] = uint16_t(kr[u]);
+            atomicAdd(&b.cnt[br_slot(sg, bt.key[u], isr)], 1u);  // histogram
+          } else {
+            dev_fail(st, SP_ERR_INTERNAL, -3);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    br_finish<BLOCK, CAP>(b, E, key_bits, tmp32, st, TileOut<CI, VT>{out_col, out_val, sval, srow, r_del, base});
   }
 }
 

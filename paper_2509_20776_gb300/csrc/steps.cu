@@ -48,7 +48,7 @@ sp_status sort_rows_impl(sp_ctx* ctx, sp_csr* M, cudaStream_t s) {
   const size_t o_long = cv.reserve(size_t(long_cap) * 8);
   const size_t o_huge = cv.reserve(size_t(huge_cap) * 8);
   const size_t o_cnt = cv.reserve(64);
-  size_t po[6];
+  size_t po[kPipeSlots];
   pipe_reserve(cv, m, nnz, sizeof(VT), po);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
