@@ -8,6 +8,7 @@
 // exchange: all rows live in one address space.
 #include "dispatch.h"
 #include "kernels.cuh"
+#include "rowsort.cuh"
 
 namespace sp {
 
@@ -58,29 +59,27 @@ struct PermLen {
   }
 };
 
-// Plain row gather for the identity column map (columns keep their order, no sort).
-template <class RP, class CIt, class VTt, class IX>
-struct PermGather {
+// Phase-1 gather of the permutation: output row r is source row p[r] (its start was
+// recorded by the length scan), every column relabelled through qinv (identity when
+// there is no column permutation).  A column outside [0, n) becomes the key
+// 0xFFFFFFFF, which the sort reports as SP_ERR_INDEX_RANGE.
+template <class CIt, class VTt, class IX>
+struct PermGs {
   using CI = CIt;
   using VT = VTt;
-  const RP* rowptr;
-  const CI* col;
-  const VT* val;
-  const IX* p;
-  long long m, nnz;
-  __device__ void src(long long r, int& which, long long& off) const {
-    which = 0;
-    const long long s = p ? (long long)p[r] : r;
-    off = (s >= 0 && s < m) ? (long long)rowptr[s] : 0;
-  }
-  __device__ void get(int, long long pos, CI& c, VT& v) const {
-    if (pos < 0 || pos >= nnz) {
-      c = CI(0);
-      v = VT(0);
-      return;
-    }
-    c = ld_stream(col + pos);
-    v = ld_stream(val + pos);
+  const CI* c_;
+  const VT* v_;
+  const IX* qinv;           // old column -> new column (null: identity)
+  const long long* sstart;  // source start of output row r
+  long long n;
+  __device__ long long src(long long r) const { return sstart[r]; }
+  __device__ CI col(long long pos) const { return ld_stream(c_ + pos); }
+  __device__ VT val(long long pos) const { return ld_stream(v_ + pos); }
+  __device__ CI map(CI c) const {
+    if (!qinv) return c;
+    const long long cl = (long long)c;
+    if (cl < 0 || cl >= n) return CI(-1);
+    return CI(ld_map(qinv + cl));
   }
 };
 
@@ -96,12 +95,8 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
   const size_t o_scan = cv.reserve(scan_ws_bytes(m));
   const size_t o_ss = cv.reserve(size_t(m) * 8);
-  const long long long_cap = nnz / TILE_CP + 1, huge_cap = nnz / LONG_CAP + 1;
-  const size_t o_long = cv.reserve(size_t(long_cap) * 8);
-  const size_t o_huge = cv.reserve(size_t(huge_cap) * 8);
-  const size_t o_cnt = cv.reserve(64);
-  size_t po[kPipeSlots];
-  pipe_reserve(cv, m, nnz, sizeof(VT), po);
+  size_t ro[kRowsSlots];
+  rows_reserve(cv, m, nnz, sizeof(VT), ro);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
@@ -142,32 +137,12 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   if (nnz == 0 || m == 0) return SP_OK;
   CI* out_col = static_cast<CI*>(B->colidx);
   VT* out_val = static_cast<VT*>(B->values);
-  if (!q) {  // identity column map: rows move whole, no relabel, no sort
-    PermGather<RP, CI, VT, IX> g{static_cast<const RP*>(A->rowptr),
-                                 static_cast<const CI*>(A->colidx),
-                                 static_cast<const VT*>(A->values), p, m, nnz};
-    const long long blocks = (nnz + GATHER_CH - 1) / GATHER_CH;
-    {
-      SP_PHASE(SP_PHASE_GATHER);
-      k_gather_rows<<<unsigned(blocks), GATHER_BLOCK, 0, s>>>(g, vp, m, nnz, out_col, out_val);
-    }
-    SP_CUDA(cudaGetLastError());
-    return SP_OK;
-  }
-  PermLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A->rowptr),
-                                static_cast<const CI*>(A->colidx),
-                                static_cast<const VT*>(A->values), qinv, sstart, vp, n};
-  PipeLists lists;
-  lists.long_rows = cv.at<long long>(o_long);
-  lists.huge_rows = cv.at<long long>(o_huge);
-  lists.n_long = cv.at<unsigned>(o_cnt);
-  lists.n_huge = lists.n_long + 1;
-  lists.long_cap = long_cap;
-  lists.huge_cap = huge_cap;
-  SP_CUDA(cudaMemsetAsync(lists.n_long, 0, 64, s));
-  PipeWs w = pipe_bind(cv, m, nnz, po);
+  // phase 1: gather + relabel; phase 2 (a column permutation only): sort every row
+  const PermGs<CI, VT, IX> g{static_cast<const CI*>(A->colidx), static_cast<const VT*>(A->values), qinv,
+                             sstart, n};
+  const RowsWs w = rows_bind(cv, m, nnz, ro);
   const int kb = ceil_log2_u64(uint64_t(n));
-  return run_pipeline(ctx, s, ld, vp, m, nnz, kb, true, lists, w, out_col, out_val);
+  return run_rows(ctx, s, vp, m, nnz, kb, w, &g, q != nullptr, out_col, out_val);
 }
 
 sp_status alloc_csr(sp_ctx* ctx, sp_csr* B, cudaStream_t s) {

@@ -1,0 +1,662 @@
+// Two-phase Build step (Sec. 3.1, Algorithm 2's fill pass and the per-row sort):
+//   phase 1, k_gather_chunks: every output row gets its source entries, relabelled,
+//     at its final row position but in source order (a load-balanced gather over
+//     fixed chunks of output positions: no shared-memory sort, all loads independent);
+//   phase 2, the rows of the output are sorted in place:
+//     * rows of at most SS_CP entries in tiles (consecutive rows, at most SS_CAP
+//       entries and SS_ROWS rows per tile), k_seg_sort;
+//     * rows of SS_CP < L <= SS_CAP entries alone, k_seg_sort;
+//     * longer rows are first partitioned by key range (k_huge) into runs of at most
+//       SS_CAP entries, which k_seg_sort then sorts.
+// One scan over the output rows (RowsPartition) cuts the tiles and the gather chunks
+// and lists the rows that do not fit a tile.
+#pragma once
+
+#include "pipeline.cuh"
+
+namespace sp {
+
+constexpr int SS_BLOCK = 512;
+constexpr int SS_CAP = 4096;                   // entries per work item
+constexpr int SS_CP = SS_CAP / 2;              // longest row a tile accepts
+constexpr int SS_ROW_W = 4;                    // partition weight of a row
+constexpr int SS_ROWS = SS_CP / SS_ROW_W;      // rows per tile
+constexpr int SS_WORDS = SS_CAP / 32;          // row-start bitmap words
+constexpr int SS_U = SS_CAP / SS_BLOCK;        // entries per thread
+static_assert(SS_ROWS <= SS_BLOCK, "one thread per row of a tile");
+static_assert(SS_CAP <= LONG_CAP, "runs of k_huge fit a work item");
+static_assert(SS_WORDS == 4 * 32, "one warp scans the bitmap, four words per lane");
+
+constexpr int GC_BLOCK = 512;                  // gather: threads per CTA
+constexpr int GC_CH = 4096;                    // gather: output positions per CTA
+constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
+
+// ---- partition ----------------------------------------------------------------------
+// Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= SS_CP).  With
+// c(r) the exclusive prefix of the weights, tile t holds the rows with c(r) in
+// [t*SS_CP, (t+1)*SS_CP): at most SS_ROWS rows and 2*SS_CP entries.  Gather chunk k
+// starts at the row holding output position k*GC_CH.
+__device__ __forceinline__ long long rows_weight(const long long* vp, long long r) {
+  const long long L = vp[r + 1] - vp[r];
+  return SS_ROW_W + (L <= SS_CP ? L : 0);
+}
+
+struct RowsWeight {
+  const long long* vp;
+  __device__ long long operator()(long long r) const { return rows_weight(vp, r); }
+};
+
+struct RowsPartition {
+  const long long* vp;
+  long long nrows;
+  long long ntiles_cap;  // tile_first holds ntiles_cap + 1 entries
+  long long* tile_first;
+  long long* ntiles;
+  long long nchunks;
+  long long* chunk_first;
+  FinalEntry* fin;  // rows sorted alone
+  unsigned* fin_n;
+  long long fin_cap;
+  HugeEntry* huge;  // rows for k_huge
+  unsigned* huge_n;
+  long long huge_cap;
+  int key_bits;
+  DevStatus* st;
+  __device__ void operator()(long long r, long long c) const {
+    if (r == nrows) {  // c = total weight
+      long long nt = c / SS_CP + 1;
+      if (nt > ntiles_cap) {
+        dev_fail(st, SP_ERR_INTERNAL, -14);
+        nt = ntiles_cap;
+      }
+      *ntiles = nt;
+      tile_first[nt] = nrows;
+      return;
+    }
+    if (r == 0) tile_first[0] = 0;
+    const long long o0 = vp[r], o1 = vp[r + 1], L = o1 - o0;
+    const long long e = c + SS_ROW_W + (L <= SS_CP ? L : 0);
+    long long t_lo = c / SS_CP + 1, t_hi = e / SS_CP;
+    if (t_hi > ntiles_cap - 1) t_hi = ntiles_cap - 1;
+    for (long long t = t_lo; t <= t_hi; ++t) tile_first[t] = r + 1;
+    if (L <= 0) return;
+    long long k_hi = (o1 - 1) / GC_CH;
+    if (k_hi > nchunks - 1) k_hi = nchunks - 1;
+    for (long long k = (o0 + GC_CH - 1) / GC_CH; k <= k_hi; ++k) chunk_first[k] = r;
+    if (L > SS_CP) {
+      if (L <= SS_CAP) {
+        const unsigned q = atomicAdd(fin_n, 1u);
+        if (q < fin_cap) fin[q] = FinalEntry{o0, L, BUF_OUT, 0};
+        else dev_fail(st, SP_ERR_INTERNAL, -15);
+      } else {
+        const unsigned q = atomicAdd(huge_n, 1u);
+        if (q < huge_cap) huge[q] = HugeEntry{o0, L, 0u, key_bits, BUF_OUT, 0};
+        else dev_fail(st, SP_ERR_INTERNAL, -16);
+      }
+    }
+  }
+};
+
+// ---- phase 1: gather ----------------------------------------------------------------
+// Each CTA owns GC_CH consecutive output positions, starting at row chunk_first[k].
+// Gs: using CI, VT;
+//     __device__ long long src(long long r) const;     // source start of output row r
+//     __device__ typename Gs::CI col(long long pos) const;  // source column
+//     __device__ typename Gs::CI map(typename Gs::CI c) const;  // new column
+//     __device__ typename Gs::VT val(long long pos) const;
+template <class Gs>
+__global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
+                                                            long long nrows, long long total,
+                                                            const long long* __restrict__ chunk_first,
+                                                            typename Gs::CI* __restrict__ out_col,
+                                                            typename Gs::VT* __restrict__ out_val) {
+  using CI = typename Gs::CI;
+  using VT = typename Gs::VT;
+  constexpr int B = GC_BLOCK, ITEMS = GC_ITEMS;
+  __shared__ uint16_t owner[GC_CH];
+  __shared__ long long r_off[B];
+  __shared__ long long r_o0[B];
+  __shared__ long long r_o1[B];
+  __shared__ uint32_t tmp32[B / 32 + 1];
+  const int t = threadIdx.x;
+  const long long c0 = blockIdx.x * (long long)GC_CH;
+  if (c0 >= total) return;
+  const long long c1 = c0 + GC_CH < total ? c0 + GC_CH : total;
+  for (long long rb = chunk_first[blockIdx.x];; rb += B) {
+    const long long r = rb + t;
+    long long o0 = total, o1 = total;
+    if (r < nrows) {
+      o0 = vp[r];
+      o1 = vp[r + 1];
+    }
+    const bool active = r < nrows && o1 > o0 && o1 > c0 && o0 < c1;
+    if (active) {
+      r_off[t] = gs.src(r);
+      r_o0[t] = o0;
+      r_o1[t] = o1;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) owner[t + j * B] = 0;
+    __syncthreads();
+    if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint16_t(t + 1);
+    __syncthreads();
+    smem_incl_max16<B, ITEMS>(owner, GC_CH, tmp32);
+    // all loads, then all stores (the compiler cannot move stores above later loads)
+    constexpr int H = 8;
+#pragma unroll
+    for (int h = 0; h < ITEMS; h += H) {
+      CI c[H];
+      VT v[H];
+      long long pos[H];
+      bool ok[H];
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        const int x = t + (h + u) * B;
+        const long long g = c0 + x;
+        const int ow = owner[x];
+        ok[u] = false;
+        pos[u] = 0;
+        if (g < c1 && ow > 0) {
+          const int k = ow - 1;
+          const long long o = r_o0[k];
+          // positions past this batch of rows belong to the next batch
+          if (g >= o && g < r_o1[k]) {
+            ok[u] = true;
+            pos[u] = r_off[k] + (g - o);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < H; ++u) c[u] = ok[u] ? gs.col(pos[u]) : CI(0);
+#pragma unroll
+      for (int u = 0; u < H; ++u)
+        if (ok[u]) v[u] = gs.val(pos[u]);
+#pragma unroll
+      for (int u = 0; u < H; ++u)
+        if (ok[u]) c[u] = gs.map(c[u]);
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        if (!ok[u]) continue;
+        const long long g = c0 + t + (h + u) * B;
+        st_stream(out_col + g, c[u]);
+        st_stream(out_val + g, v[u]);
+      }
+    }
+    __syncthreads();
+    // stop once this batch's last row reaches the end of the chunk
+    const long long rl = rb + B - 1;
+    if (rl >= nrows - 1 || vp[rl + 1] >= c1) break;
+  }
+}
+
+// ---- phase 2: in-place sort of output rows ---------------------------------------------
+// Bucket of key k in a row of L entries: nb = 2^(ceil(log2 L) - 1) buckets spaced evenly
+// in an approximate square root of k over the row's key range [0, kmax].  The root is
+// the exponent-halving bit trick on the float of k (exact at even powers of two, up to
+// 6% high in between): monotone in k (every step is), so buckets stay in key order; the
+// scale nb / root(kmax) maps [0, kmax] onto the nb buckets.  The square root keeps
+// buckets balanced both for uniformly relabelled columns and for labels crowded at the
+// low end (degree-descending orderings).
+__device__ __forceinline__ uint32_t ss_nb(uint32_t L) { return L <= 2 ? 1u : 1u << (31 - __clz(L - 1)); }
+__device__ __forceinline__ float ss_root(uint32_t k) {
+  return __uint_as_float((__float_as_uint(__uint2float_rn(k)) >> 1) + 0x1FC00000u);
+}
+// 1 / root(kmax): the scale of a range [0, kmax] is nb * ss_inv_root(kmax)
+__device__ __forceinline__ float ss_inv_root(uint32_t kmax) { return kmax ? 1.0f / ss_root(kmax) : 0.0f; }
+// bucket of `key` given the row's scale and last bucket nb - 1
+__device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_t last) {
+  const uint32_t b = __float2uint_rz(ss_root(key) * scale);
+  return b < last ? b : last;
+}
+
+template <class VT>
+__host__ __device__ constexpr size_t ss_smem_bytes() {
+  return size_t(SS_CAP) * (sizeof(VT) + 4 * 3 + 2 * 3) + size_t(SS_ROWS) * (4 * 2 + 2 * 2) +
+         size_t(SS_WORDS) * 4 * 2;
+}
+
+// In-place exclusive sum of a[0, n), n <= SS_CAP; thread t owns the ceil(n / SS_BLOCK)
+// consecutive entries starting at t * ceil(n / SS_BLOCK).
+__device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
+  const int t = threadIdx.x;
+  const int per = (n + SS_BLOCK - 1) / SS_BLOCK;
+  const int x0 = t * per, x1 = x0 + per < n ? x0 + per : n;
+  uint32_t s = 0;
+  for (int x = x0; x < x1; ++x) s += a[x];
+  uint32_t total;
+  uint32_t run = block_excl_sum<SS_BLOCK>(s, tmp, &total);
+  for (int x = x0; x < x1; ++x) {
+    const uint32_t v = a[x];
+    a[x] = run;
+    run += v;
+  }
+  __syncthreads();
+}
+
+// Work items: tiles [0, *ntiles) of the partition, then runs fin[0, *fin_n) (rows of
+// SS_CP < L <= SS_CAP entries, in the output arrays, and k_huge's runs, in the output
+// or in the temporary arrays).  Every item's entries are loaded into shared memory
+// before any of them is written back, so a run is sorted in place.
+template <class CI, class VT>
+__global__ void __launch_bounds__(SS_BLOCK, 2)
+    k_seg_sort(const long long* __restrict__ vp, const long long* __restrict__ tile_first,
+               const long long* __restrict__ ntiles_p, const FinalEntry* __restrict__ fin,
+               const unsigned* __restrict__ fin_n, long long fin_cap, const uint32_t* __restrict__ tkey_g,
+               const VT* __restrict__ tval_g, CI* __restrict__ out_col, VT* __restrict__ out_val,
+               int key_bits, DevStatus* st) {
+  constexpr int B = SS_BLOCK, CAP = SS_CAP, U = SS_U;
+  extern __shared__ __align__(16) unsigned char smem[];
+  VT* sval = reinterpret_cast<VT*>(smem);
+  uint32_t* skey = reinterpret_cast<uint32_t*>(smem + size_t(CAP) * sizeof(VT));  // packed order
+  uint32_t* tkey = skey + CAP;        // bucket order
+  uint32_t* cnt = tkey + CAP;         // bucket counters
+  uint32_t* rdel = cnt + CAP;         // per row: output offset from base - packed start
+  uint32_t* bits = rdel + 2 * SS_ROWS;  // row starts
+  uint32_t* wpre = bits + SS_WORDS;   // row starts in earlier words
+  uint16_t* slot = reinterpret_cast<uint16_t*>(wpre + SS_WORDS);  // bucket of packed entry
+  uint16_t* tidx = slot + CAP;        // packed entry of each bucket-order position
+  uint16_t* rowk = tidx + CAP;        // row of each packed entry
+  float* rsc = reinterpret_cast<float*>(rdel + SS_ROWS);  // per row: bucket scale
+  uint16_t* rps = rowk + CAP;         // per row: packed start
+  uint16_t* rnm = rps + SS_ROWS;      // per row: last bucket
+  __shared__ uint32_t tmp32[B / 32 + 1];
+  __shared__ uint32_t s_min, s_max;
+  const int t = threadIdx.x;
+  const uint32_t kmax = key_bits >= 32 ? 0xFFFFFFFFu : (1u << key_bits) - 1u;
+  const float isr = ss_inv_root(kmax);
+  const long long ntiles = *ntiles_p;
+  long long nf = *fin_n;
+  if (nf > fin_cap) nf = fin_cap;  // overflow was reported by the producer
+  const long long nitems = ntiles + nf;
+
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    if (t < SS_WORDS) bits[t] = 0;
+    if (t == 0) {
+      s_min = 0xFFFFFFFFu;
+      s_max = 0u;
+    }
+    long long base;
+    int buf = BUF_OUT;
+    uint32_t myL = 0;
+    long long o0 = 0;
+    if (item < ntiles) {
+      const long long r0 = tile_first[item];
+      long long r1 = tile_first[item + 1];
+      base = vp[r0];
+      if (r1 - r0 > SS_ROWS) {  // cannot happen: see RowsPartition
+        if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -17);
+        r1 = r0;
+      }
+      if (t < r1 - r0) {
+        o0 = vp[r0 + t];
+        const long long L = vp[r0 + t + 1] - o0;
+        if (L > 0 && L <= SS_CP) {
+          if (o0 - base > 0xFFFFFFFFll - SS_CAP) dev_fail(st, SP_ERR_OVERFLOW, r0 + t);
+          else myL = uint32_t(L);
+        }
+      }
+    } else {
+      const FinalEntry fe = fin[item - ntiles];
+      base = fe.off;
+      buf = fe.buf;
+      if (fe.len < 0 || fe.len > CAP) {
+        if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -18);
+      } else if (t == 0) {
+        myL = uint32_t(fe.len);
+        o0 = base;
+      }
+    }
+    // packed start (high half) and rank among the item's rows (low half)
+    uint32_t tot;
+    const uint32_t pre = block_excl_sum<B>(myL ? ((myL << 16) | 1u) : 0u, tmp32, &tot);
+    const int E = int(tot >> 16);  // <= 2 * SS_CP by the partition
+    if (E > CAP) {                 // cannot happen: see RowsPartition
+      if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -19);
+      __syncthreads();
+      continue;
+    }
+    if (myL) {
+      const uint32_t k = pre & 0xFFFFu, ps = pre >> 16;
+      const uint32_t nb = ss_nb(myL);
+      rps[k] = uint16_t(ps);
+      rnm[k] = uint16_t(nb - 1);
+      rsc[k] = float(nb) * isr;
+      rdel[k] = uint32_t(o0 - base) - ps;
+      atomicOr(&bits[ps >> 5], 1u << (ps & 31));
+    }
+    for (int x = t; x < E; x += B) cnt[x] = 0;
+    __syncthreads();
+    if (t < 32) {
+      uint32_t c[4], s = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        c[j] = __popc(bits[t * 4 + j]);
+        s += c[j];
+      }
+      uint32_t run = warp_incl_sum(s) - s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        wpre[t * 4 + j] = run;
+        run += c[j];
+      }
+    }
+    __syncthreads();
+    // load: key and value of every packed entry, bucket histogram
+    constexpr int LU = 4;
+    if (item < ntiles) {
+      for (int x0 = t; x0 < E; x0 += B * LU) {
+        uint32_t kk[LU], kr[LU], oo[LU];  // key, row, offset from base
+        VT vv[LU];
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int x = x0 + u * B;
+          kr[u] = 0;
+          oo[u] = 0;
+          if (x < E) {
+            const int w = x >> 5;
+            kr[u] = wpre[w] + __popc(bits[w] & (0xFFFFFFFFu >> (31 - (x & 31)))) - 1u;
+            oo[u] = rdel[kr[u]] + uint32_t(x);
+          }
+        }
+        {  // tiles live in the output arrays
+          const CI* kp = out_col + base;
+          const VT* vq = out_val + base;
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) kk[u] = uint32_t(ld_stream(kp + oo[u]));
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) vv[u] = ld_stream(vq + oo[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int x = x0 + u * B;
+          if (x >= E) continue;
+          uint32_t key = kk[u];
+          if (key > kmax) {  // a column outside [0, ncols)
+            dev_fail(st, SP_ERR_INDEX_RANGE, base + oo[u]);
+            key = kmax;
+          }
+          const uint32_t sl = rps[kr[u]] + ss_bucket(key, rsc[kr[u]], rnm[kr[u]]);
+          skey[x] = key;
+          sval[x] = vv[u];
+          slot[x] = uint16_t(sl);
+          rowk[x] = uint16_t(kr[u]);
+          atomicAdd(&cnt[sl], 1u);
+        }
+      }
+    } else {
+      // a single run (a row sorted alone or a key-range group of a long row): its
+      // buckets span the run's own key range [min, max], found while loading
+      uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+      const CI* kp = out_col + base;
+      const VT* vq = out_val + base;
+      for (int x0 = t; x0 < E; x0 += B * LU) {
+        uint32_t kk[LU];
+        VT vv[LU];
+        if (buf == BUF_TEMP) {
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) kk[u] = ld_stream(tkey_g + base + x0 + u * B);
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) vv[u] = ld_stream(tval_g + base + x0 + u * B);
+        } else {
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) kk[u] = uint32_t(ld_stream(kp + x0 + u * B));
+#pragma unroll
+          for (int u = 0; u < LU; ++u)
+            if (x0 + u * B < E) vv[u] = ld_stream(vq + x0 + u * B);
+        }
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int x = x0 + u * B;
+          if (x >= E) continue;
+          uint32_t key = kk[u];
+          if (key > kmax) {
+            dev_fail(st, SP_ERR_INDEX_RANGE, base + x);
+            key = kmax;
+          }
+          skey[x] = key;
+          sval[x] = vv[u];
+          mn = key < mn ? key : mn;
+          mx = key > mx ? key : mx;
+        }
+      }
+      mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+      mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+      if ((t & 31) == 0) {
+        atomicMin(&s_min, mn);
+        atomicMax(&s_max, mx);
+      }
+      __syncthreads();
+      const uint32_t lo = s_min, w = s_max > s_min ? s_max - s_min : 0u;
+      const uint32_t nb = ss_nb(uint32_t(E)), last = nb - 1;
+      const float sc = float(nb) * ss_inv_root(w);
+      for (int x = t; x < E; x += B) {
+        const uint32_t sl = ss_bucket(skey[x] - lo, sc, last);
+        slot[x] = uint16_t(sl);
+        rowk[x] = 0;
+        atomicAdd(&cnt[sl], 1u);
+      }
+    }
+    __syncthreads();
+    ss_excl_sum(cnt, E, tmp32);
+    // scatter to bucket order; afterwards cnt[s] = end of bucket s, cnt[s-1] its start
+    for (int x = t; x < E; x += B) {
+      const uint32_t p = atomicAdd(&cnt[slot[x]], 1u);
+      tkey[p] = skey[x];
+      tidx[p] = uint16_t(x);
+    }
+    __syncthreads();
+    // rank inside the bucket and write; buckets of more than T_RANK keys are refined
+    CI* const oc = out_col + base;
+    VT* const ov = out_val + base;
+    bool heavy = false;
+    for (int p = t; p < E; p += B) {
+      const uint32_t x = tidx[p], k = tkey[p];
+      const uint32_t s = slot[x];
+      const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
+      if (end - start > uint32_t(T_RANK)) {
+        heavy = true;
+        continue;
+      }
+      uint32_t rank = 0;
+      for (uint32_t q = start; q < end; ++q) rank += tkey[q] < k;
+      const uint32_t g = rdel[rowk[x]] + start + rank;
+      st_stream(oc + g, CI(k));
+      st_stream(ov + g, sval[x]);
+    }
+    if (__syncthreads_or(heavy)) {
+      // skewed keys: refine the heavy buckets (bucket order, own key range); the
+      // segment words live in skey[] and the per-segment words in slot[] from here on
+      SortView r;
+      r.key = tkey;
+      r.seg = skey;
+      r.cnt = cnt;
+      r.lo = reinterpret_cast<uint32_t*>(slot);
+      r.hi = r.lo + CAP / 16;
+      r.base = r.hi + CAP / 16;
+      r.idx = tidx;
+      uint32_t sw[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = t + u * B;
+        sw[u] = 0;
+        if (p < E) {
+          const uint32_t s = slot[tidx[p]];
+          const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
+          if (end - start > uint32_t(T_RANK)) sw[u] = (start << 16) | (end - start);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = t + u * B;
+        if (p < E) skey[p] = sw[u];
+      }
+      __syncthreads();
+      refine_sort<B, U>(r, E, key_bits, tmp32, st, false);
+      for (int p = t; p < E; p += B) {
+        const int fp = final_pos(r, p);
+        if (fp < 0) continue;
+        const uint32_t x = tidx[p];
+        const uint32_t g = rdel[rowk[x]] + uint32_t(fp);
+        st_stream(oc + g, CI(tkey[p]));
+        st_stream(ov + g, sval[x]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---- host side --------------------------------------------------------------------------
+struct RowsWs {
+  long long ntiles_cap = 0, nchunks = 0, fin_cap = 0, huge_cap = 0, nxt_cap = 0;
+  long long* tile_first = nullptr;
+  long long* chunk_first = nullptr;
+  long long* ntiles = nullptr;
+  unsigned* counters = nullptr;  // [0] fin_n [1] huge_n [2] nxt_n [3..4] tickets [5] spare
+  FinalEntry* fin = nullptr;
+  HugeEntry* huge = nullptr;
+  HugeEntry* nxt = nullptr;
+  uint32_t* tkey = nullptr;
+  void* tval = nullptr;
+  char* scan_ws = nullptr;
+};
+
+constexpr int kRowsSlots = 10;
+
+inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
+  w->ntiles_cap = (nnz + SS_ROW_W * nrows) / SS_CP + 1;
+  w->nchunks = (nnz + GC_CH - 1) / GC_CH;
+  w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / LONG_CAP + 16) + nnz / SS_CP + 1;
+  w->huge_cap = nnz / SS_CAP + 1;
+  w->nxt_cap = nnz / LONG_CAP + 1;
+}
+
+inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbytes, size_t* off) {
+  RowsWs w;
+  rows_caps(nrows, nnz, &w);
+  const bool need_temp = nnz > SS_CAP;
+  off[0] = cv.reserve(size_t(w.ntiles_cap + 1) * 8);
+  off[1] = cv.reserve(size_t(w.nchunks + 1) * 8);
+  off[2] = cv.reserve(8);
+  off[3] = cv.reserve(16 * 4);
+  off[4] = cv.reserve(size_t(w.fin_cap) * sizeof(FinalEntry));
+  off[5] = cv.reserve(size_t(w.huge_cap) * sizeof(HugeEntry));
+  off[6] = cv.reserve(size_t(w.nxt_cap) * sizeof(HugeEntry));
+  off[7] = cv.reserve(need_temp ? size_t(nnz) * 4 : 0);
+  off[8] = cv.reserve(need_temp ? size_t(nnz) * vbytes : 0);
+  off[9] = cv.reserve(scan_ws_bytes(nrows));
+}
+
+inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const size_t* off) {
+  RowsWs w;
+  rows_caps(nrows, nnz, &w);
+  w.tile_first = cv.at<long long>(off[0]);
+  w.chunk_first = cv.at<long long>(off[1]);
+  w.ntiles = cv.at<long long>(off[2]);
+  w.counters = cv.at<unsigned>(off[3]);
+  w.fin = cv.at<FinalEntry>(off[4]);
+  w.huge = cv.at<HugeEntry>(off[5]);
+  w.nxt = cv.at<HugeEntry>(off[6]);
+  w.tkey = cv.at<uint32_t>(off[7]);
+  w.tval = cv.at<void>(off[8]);
+  w.scan_ws = cv.at<char>(off[9]);
+  return w;
+}
+
+// Phase-1 functor for callers that only sort (the rows are in place already).
+template <class CIt, class VTt>
+struct NoGather {
+  using CI = CIt;
+  using VT = VTt;
+  __device__ long long src(long long) const { return 0; }
+  __device__ CI col(long long) const { return CI(0); }
+  __device__ CI map(CI c) const { return c; }
+  __device__ VT val(long long) const { return VT(0); }
+};
+
+// A loader for k_huge that only ever processes buffered runs (no source rows).
+template <class CIt, class VTt>
+struct RunsOnly {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr bool kAllKept = true;
+  static constexpr bool kLoadVals = true;
+  __device__ RowSrc row(long long) const { return RowSrc{0, 0, 0, 0}; }
+  __device__ const CI* cols(int) const { return nullptr; }
+  __device__ const VT* vals(int) const { return nullptr; }
+  __device__ bool test(int, long long) const { return false; }
+  __device__ bool map(int, long long, uint32_t&) const { return false; }
+};
+
+// Partition the output rows (row pointer vp, nnz entries), gather them with `gs`
+// (when given) and sort every row in place (when `sort`).
+template <class CI, class VT, class Gs>
+sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long nrows, long long nnz,
+                   int key_bits, const RowsWs& w, const Gs* gs, bool sort, CI* out_col, VT* out_val) {
+  if (nrows == 0 || nnz == 0) return SP_OK;
+  SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
+  const int nsm = ctx->num_sms;
+  unsigned* fin_n = w.counters + 0;
+  unsigned* huge_n = w.counters + 1;
+  unsigned* nxt_n = w.counters + 2;
+  SP_TRY(launch_scan(ctx, s, RowsWeight{vp},
+                     RowsPartition{vp, nrows, w.ntiles_cap, w.tile_first, w.ntiles, w.nchunks, w.chunk_first,
+                                   w.fin, fin_n, w.fin_cap, w.huge, huge_n, w.huge_cap, key_bits,
+                                   ctx->dstatus},
+                     nrows, w.scan_ws, SP_PHASE_PARTITION));
+  if (gs) {
+    if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_gather_chunks<Gs><<<unsigned(w.nchunks), GC_BLOCK, 0, s>>>(*gs, vp, nrows, nnz, w.chunk_first,
+                                                                   out_col, out_val);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (!sort) return SP_OK;
+  VT* tval = static_cast<VT*>(w.tval);
+  if (nnz > SS_CAP) {
+    using RL = RunsOnly<CI, VT>;
+    constexpr size_t hsm = huge_smem_bytes();
+    static bool once_h = (set_smem(k_huge<RL>, hsm), true);
+    (void)once_h;
+    {
+      SP_PHASE(SP_PHASE_HUGE);
+      k_huge<RL><<<nsm, HUGE_BLOCK, hsm, s>>>(RL{}, vp, nullptr, nullptr, w.huge, huge_n, w.huge_cap,
+                                              w.counters + 3, key_bits, w.tkey, tval, out_col, out_val,
+                                              w.fin, fin_n, w.fin_cap, w.nxt, nxt_n, w.nxt_cap,
+                                              ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    // a second round only when a bucket of the first (2^(key_bits - HUGE_NB_LOG) keys)
+    // can hold more than LONG_CAP entries
+    if (key_bits - HUGE_NB_LOG > 12) {
+      static_assert(LONG_CAP == 1 << 12, "second-round test assumes LONG_CAP = 2^12");
+      {
+        SP_PHASE(SP_PHASE_HUGE);
+        k_huge<RL><<<nsm, HUGE_BLOCK, hsm, s>>>(RL{}, vp, nullptr, nullptr, w.nxt, nxt_n, w.nxt_cap,
+                                                w.counters + 4, key_bits, w.tkey, tval, out_col, out_val,
+                                                w.fin, fin_n, w.fin_cap, w.nxt, w.counters + 5, 0, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+    }
+  }
+  constexpr size_t ssm = ss_smem_bytes<VT>();
+  static bool once_s = (set_smem(k_seg_sort<CI, VT>, ssm), true);
+  (void)once_s;
+  {
+    SP_PHASE(SP_PHASE_TILE);
+    k_seg_sort<CI, VT><<<2 * nsm, SS_BLOCK, ssm, s>>>(vp, w.tile_first, w.ntiles, w.fin, fin_n, w.fin_cap,
+                                                      w.tkey, tval, out_col, out_val, key_bits,
+                                                      ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
+}
+
+}  // namespace sp

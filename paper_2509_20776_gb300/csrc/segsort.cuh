@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(HUGE_BLOCK, 1)
         const uint32_t key = sbuf == BUF_TEMP ? tkey[g0 + e] : uint32_t(out_col[g0 + e]);
         const uint32_t bk = (key - lo) >> sh;
         if (key >= lo && bk < uint32_t(nb)) atomicAdd(&hist[bk], 1u);
-        else dev_fail(st, SP_ERR_INTERNAL, -21);
+        else dev_fail(st, SP_ERR_INDEX_RANGE, g0 + e);
       }
     }
     __syncthreads();

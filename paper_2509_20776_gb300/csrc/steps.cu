@@ -2,34 +2,9 @@
 // canonical-form validation, and the release of library-allocated matrices.
 #include "dispatch.h"
 #include "kernels.cuh"
+#include "rowsort.cuh"
 
 namespace sp {
-
-// A row of M sorted in place: the source is the row itself, keys are its columns.
-template <class RP, class CIt, class VTt>
-struct SortLoader {
-  using CI = CIt;
-  using VT = VTt;
-  const RP* rowptr;
-  const CI* col;
-  const VT* val;
-  long long m, n, nnz;
-  __device__ RowSrc row(long long r) const {
-    const long long s = (long long)rowptr[r], e = (long long)rowptr[r + 1];
-    if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
-    return RowSrc{s, 0, e - s, 0};
-  }
-  static constexpr bool kAllKept = true;
-  static constexpr bool kLoadVals = true;
-  __device__ const CI* cols(int) const { return col; }
-  __device__ const VT* vals(int) const { return val; }
-  __device__ bool test(int, long long c) const { return c >= 0 && c < n; }
-  __device__ bool map(int, long long c, uint32_t& key) const {
-    if (c < 0 || c >= n) return false;
-    key = uint32_t(c);
-    return true;
-  }
-};
 
 template <class RP>
 struct RowLenLoad {
@@ -44,12 +19,8 @@ sp_status sort_rows_impl(sp_ctx* ctx, sp_csr* M, cudaStream_t s) {
   const long long m = M->nrows, nnz = M->nnz;
   Carver cv;
   const size_t o_vp = cv.reserve(size_t(m + 1) * 8);
-  const long long long_cap = nnz / TILE_CP + 1, huge_cap = nnz / LONG_CAP + 1;
-  const size_t o_long = cv.reserve(size_t(long_cap) * 8);
-  const size_t o_huge = cv.reserve(size_t(huge_cap) * 8);
-  const size_t o_cnt = cv.reserve(64);
-  size_t po[kPipeSlots];
-  pipe_reserve(cv, m, nnz, sizeof(VT), po);
+  size_t ro[kRowsSlots];
+  rows_reserve(cv, m, nnz, sizeof(VT), ro);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
@@ -64,20 +35,10 @@ sp_status sort_rows_impl(sp_ctx* ctx, sp_csr* M, cudaStream_t s) {
     }
     SP_CUDA(cudaGetLastError());
   }
-  PipeLists lists;
-  lists.long_rows = cv.at<long long>(o_long);
-  lists.huge_rows = cv.at<long long>(o_huge);
-  lists.n_long = cv.at<unsigned>(o_cnt);
-  lists.n_huge = lists.n_long + 1;
-  lists.long_cap = long_cap;
-  lists.huge_cap = huge_cap;
-  SP_CUDA(cudaMemsetAsync(lists.n_long, 0, 64, s));
-  PipeWs w = pipe_bind(cv, m, nnz, po);
-  SortLoader<RP, CI, VT> ld{static_cast<const RP*>(M->rowptr), static_cast<const CI*>(M->colidx),
-                            static_cast<const VT*>(M->values), m, M->ncols, nnz};
+  const RowsWs w = rows_bind(cv, m, nnz, ro);
   const int kb = ceil_log2_u64(uint64_t(M->ncols));
-  return run_pipeline(ctx, s, ld, vp, m, nnz, kb, true, lists, w, static_cast<CI*>(M->colidx),
-                      static_cast<VT*>(M->values));
+  return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, vp, m, nnz, kb, w, nullptr, true,
+                                            static_cast<CI*>(M->colidx), static_cast<VT*>(M->values));
 }
 
 // canonical-form check: one warp per row
