@@ -23,6 +23,8 @@ constexpr int SS_ROW_W = 4;                    // partition weight of a row
 constexpr int SS_ROWS = SS_CP / SS_ROW_W;      // rows per tile
 constexpr int SS_WORDS = SS_CAP / 32;          // row-start bitmap words
 constexpr int SS_U = SS_CAP / SS_BLOCK;        // entries per thread
+constexpr int SS_HEAVY = 128;                  // larger buckets are sorted by a later pass
+constexpr int SS_PASSES = 3;                   // passes over queued heavy buckets
 static_assert(SS_ROWS <= SS_BLOCK, "one thread per row of a tile");
 static_assert(SS_CAP <= LONG_CAP, "runs of k_huge fit a work item");
 static_assert(SS_WORDS == 4 * 32, "one warp scans the bitmap, four words per lane");
@@ -124,14 +126,15 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
   const long long c1 = c0 + GC_CH < total ? c0 + GC_CH : total;
   for (long long rb = chunk_first[blockIdx.x];; rb += B) {
     const long long r = rb + t;
-    long long o0 = total, o1 = total;
-    if (r < nrows) {
+    long long o0 = total, o1 = total, so = 0;
+    if (r < nrows) {  // the source start is loaded alongside, not after, the row pointer
       o0 = vp[r];
       o1 = vp[r + 1];
+      so = gs.src(r);
     }
     const bool active = r < nrows && o1 > o0 && o1 > c0 && o0 < c1;
     if (active) {
-      r_off[t] = gs.src(r);
+      r_off[t] = so;
       r_o0[t] = o0;
       r_o1[t] = o1;
     }
@@ -236,14 +239,18 @@ __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
 // Work items: tiles [0, *ntiles) of the partition, then runs fin[0, *fin_n) (rows of
 // SS_CP < L <= SS_CAP entries, in the output arrays, and k_huge's runs, in the output
 // or in the temporary arrays).  Every item's entries are loaded into shared memory
-// before any of them is written back, so a run is sorted in place.
+// before any of them is written back, so a run is sorted in place.  A bucket of more
+// than SS_HEAVY keys (skewed keys) is written in bucket order and queued in hv[] as a
+// run for a later pass, which buckets it over its own key range; without hv (the last
+// pass) every bucket is ranked directly.
 template <class CI, class VT>
 __global__ void __launch_bounds__(SS_BLOCK, 2)
     k_seg_sort(const long long* __restrict__ vp, const long long* __restrict__ tile_first,
                const long long* __restrict__ ntiles_p, const FinalEntry* __restrict__ fin,
                const unsigned* __restrict__ fin_n, long long fin_cap, const uint32_t* __restrict__ tkey_g,
                const VT* __restrict__ tval_g, CI* __restrict__ out_col, VT* __restrict__ out_val,
-               int key_bits, DevStatus* st) {
+               FinalEntry* __restrict__ hv, unsigned* hv_n, long long hv_cap, int key_bits,
+               DevStatus* st) {
   constexpr int B = SS_BLOCK, CAP = SS_CAP, U = SS_U;
   extern __shared__ __align__(16) unsigned char smem[];
   VT* sval = reinterpret_cast<VT*>(smem);
@@ -450,83 +457,52 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
       tidx[p] = uint16_t(x);
     }
     __syncthreads();
-    // rank inside the bucket and write; buckets of more than T_RANK keys are refined
+    // rank inside the bucket and write (heavy buckets: in bucket order, queued)
     CI* const oc = out_col + base;
     VT* const ov = out_val + base;
-    bool heavy = false;
     for (int p = t; p < E; p += B) {
       const uint32_t x = tidx[p], k = tkey[p];
       const uint32_t s = slot[x];
       const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
-      if (end - start > uint32_t(T_RANK)) {
-        heavy = true;
+      const uint32_t rd = rdel[rowk[x]];
+      if (hv && end - start > uint32_t(SS_HEAVY)) {
+        st_stream(oc + rd + p, CI(k));
+        st_stream(ov + rd + p, sval[x]);
+        if (uint32_t(p) == start) {
+          const unsigned q = atomicAdd(hv_n, 1u);
+          if (q < hv_cap) hv[q] = FinalEntry{base + rd + start, (long long)(end - start), BUF_OUT, 0};
+          else dev_fail(st, SP_ERR_INTERNAL, -22);
+        }
         continue;
       }
       uint32_t rank = 0;
       for (uint32_t q = start; q < end; ++q) rank += tkey[q] < k;
-      const uint32_t g = rdel[rowk[x]] + start + rank;
+      const uint32_t g = rd + start + rank;
       st_stream(oc + g, CI(k));
       st_stream(ov + g, sval[x]);
     }
-    if (__syncthreads_or(heavy)) {
-      // skewed keys: refine the heavy buckets (bucket order, own key range); the
-      // segment words live in skey[] and the per-segment words in slot[] from here on
-      SortView r;
-      r.key = tkey;
-      r.seg = skey;
-      r.cnt = cnt;
-      r.lo = reinterpret_cast<uint32_t*>(slot);
-      r.hi = r.lo + CAP / 16;
-      r.base = r.hi + CAP / 16;
-      r.idx = tidx;
-      uint32_t sw[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int p = t + u * B;
-        sw[u] = 0;
-        if (p < E) {
-          const uint32_t s = slot[tidx[p]];
-          const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
-          if (end - start > uint32_t(T_RANK)) sw[u] = (start << 16) | (end - start);
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int p = t + u * B;
-        if (p < E) skey[p] = sw[u];
-      }
-      __syncthreads();
-      refine_sort<B, U>(r, E, key_bits, tmp32, st, false);
-      for (int p = t; p < E; p += B) {
-        const int fp = final_pos(r, p);
-        if (fp < 0) continue;
-        const uint32_t x = tidx[p];
-        const uint32_t g = rdel[rowk[x]] + uint32_t(fp);
-        st_stream(oc + g, CI(tkey[p]));
-        st_stream(ov + g, sval[x]);
-      }
-      __syncthreads();
-    }
+    __syncthreads();
   }
 }
 
 // ---- host side --------------------------------------------------------------------------
 struct RowsWs {
-  long long ntiles_cap = 0, nchunks = 0, fin_cap = 0, huge_cap = 0, nxt_cap = 0;
+  long long ntiles_cap = 0, nchunks = 0, fin_cap = 0, huge_cap = 0, nxt_cap = 0, hv_cap = 0;
   long long* tile_first = nullptr;
   long long* chunk_first = nullptr;
   long long* ntiles = nullptr;
   unsigned* counters = nullptr;  // [0] fin_n [1] huge_n [2] nxt_n [3..4] tickets [5] spare
+                                 // [6..7] heavy-run counts [8..9] zero (no tiles)
   FinalEntry* fin = nullptr;
   HugeEntry* huge = nullptr;
   HugeEntry* nxt = nullptr;
+  FinalEntry* hv[2] = {nullptr, nullptr};  // heavy buckets queued for the next pass
   uint32_t* tkey = nullptr;
   void* tval = nullptr;
   char* scan_ws = nullptr;
 };
 
-constexpr int kRowsSlots = 10;
+constexpr int kRowsSlots = 12;
 
 inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
   w->ntiles_cap = (nnz + SS_ROW_W * nrows) / SS_CP + 1;
@@ -534,6 +510,7 @@ inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
   w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / LONG_CAP + 16) + nnz / SS_CP + 1;
   w->huge_cap = nnz / SS_CAP + 1;
   w->nxt_cap = nnz / LONG_CAP + 1;
+  w->hv_cap = nnz / (SS_HEAVY + 1) + 1;  // heavy buckets are disjoint runs of > SS_HEAVY
 }
 
 inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbytes, size_t* off) {
@@ -550,6 +527,8 @@ inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbyt
   off[7] = cv.reserve(need_temp ? size_t(nnz) * 4 : 0);
   off[8] = cv.reserve(need_temp ? size_t(nnz) * vbytes : 0);
   off[9] = cv.reserve(scan_ws_bytes(nrows));
+  off[10] = cv.reserve(size_t(w.hv_cap) * sizeof(FinalEntry));
+  off[11] = cv.reserve(size_t(w.hv_cap) * sizeof(FinalEntry));
 }
 
 inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const size_t* off) {
@@ -565,6 +544,8 @@ inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const 
   w.tkey = cv.at<uint32_t>(off[7]);
   w.tval = cv.at<void>(off[8]);
   w.scan_ws = cv.at<char>(off[9]);
+  w.hv[0] = cv.at<FinalEntry>(off[10]);
+  w.hv[1] = cv.at<FinalEntry>(off[11]);
   return w;
 }
 
@@ -652,10 +633,24 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   {
     SP_PHASE(SP_PHASE_TILE);
     k_seg_sort<CI, VT><<<2 * nsm, SS_BLOCK, ssm, s>>>(vp, w.tile_first, w.ntiles, w.fin, fin_n, w.fin_cap,
-                                                      w.tkey, tval, out_col, out_val, key_bits,
-                                                      ctx->dstatus);
+                                                      w.tkey, tval, out_col, out_val, w.hv[0], w.counters + 6,
+                                                      w.hv_cap, key_bits, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
+  // heavy buckets: runs over their own key range; the last pass ranks every bucket
+  const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
+  for (int pass = 0; pass < SS_PASSES; ++pass) {
+    const int a = pass & 1, b = a ^ 1;
+    const bool last = pass == SS_PASSES - 1;
+    SP_CUDA(cudaMemsetAsync(w.counters + 6 + b, 0, 4, s));
+    {
+      SP_PHASE(SP_PHASE_TILE);
+      k_seg_sort<CI, VT><<<2 * nsm, SS_BLOCK, ssm, s>>>(
+          vp, w.tile_first, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
+          last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
   return SP_OK;
 }
 
