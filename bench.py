@@ -159,8 +159,9 @@ TILE_CP, LONG_CAP = 1024, 4096  # row-length limits of the tile and long-row ker
 
 
 def row_classes(rowptr):
-    """Entries / non-empty rows handled by the tile (<= TILE_CP), long and huge
-    (> LONG_CAP) kernels of the permutation (row lengths move with the rows)."""
+    """Entries / non-empty rows of the row sort's three classes: tiles (rows of at most
+    TILE_CP entries), rows sorted alone (at most LONG_CAP) and rows split by key range
+    first (longer); row lengths move with the rows under a permutation."""
     import torch
     L = (rowptr[1:] - rowptr[:-1]).to(torch.int64)
     small = L <= TILE_CP
@@ -173,32 +174,43 @@ def row_classes(rowptr):
 
 
 def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs):
-    """Per-phase algorithmic bytes over measured phase time."""
+    """Roofline of the phase that takes the most device time: its algorithmic bytes per
+    launch (per-entry and per-row byte counts of the kernel, int32 indices and fp32
+    values) over its average CUDA-event duration."""
     e_tile, r_tile = classes["tile"]
-    e_long, r_long = classes["long"]
+    e_long, _ = classes["long"]
     e_huge, _ = classes["huge"]
+    nnz = e_tile + e_long + e_huge
     per_op = {
-        # 16 B/entry (read col+val, write col+val) + 28 B/row (p, rowptr pair, row start)
-        "tile": 16 * e_tile + 28 * r_tile,
-        "long": 16 * e_long + 28 * r_long + 16 * e_huge,
-        "huge": 16 * e_huge,
-        "scan": 28 * m,
-        "map": 8 * n,
+        # gather: read col + val, one map lookup, write col + val; vp and source start per row
+        "gather": 20 * nnz + 16 * m,
+        # in-place sort of tile rows: read and write col + val; row pointer per row
+        "tile": 16 * e_tile + 8 * m,
+        # rows sorted alone and key-range runs of long rows: read and write col + val
+        "long": 16 * (e_long + e_huge),
+        # key-range split of long rows: keys, then keys + values, written to the buffer
+        "huge": 20 * e_huge,
+        # lengths: p, rowptr pair; writes vp and the source start
+        "scan": 36 * m,
+        "map": 12 * n,
         "partition": 8 * m,
     }
     launches_total = ops_per_step * steps
     best = None
     for ph, (ms, cnt) in stats.items():
-        if cnt == 0 or ms <= 0:
+        if cnt == 0 or ms <= 0 or ph not in per_op:
             continue
         if best is None or ms > best[1]:
             best = (ph, ms, cnt)
     ph, ms, cnt = best
-    byts = per_op.get(ph, 0) * launches_total
+    kernel = {"gather": "k_gather_chunks", "tile": "k_seg_sort<SsTile>", "long": "k_seg_sort<SsRun>",
+              "huge": "k_huge", "scan": "k_scan", "map": "k_inverse_map", "partition": "k_scan"}[ph]
+    byts = per_op[ph] * launches_total
     achieved = byts / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": f"k_{ph}", "achieved": round(achieved, 1),
+    return {"bound": "hbm", "kernel": kernel, "phase": ph, "achieved": round(achieved, 1),
             "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
-            "traffic": None, "launches": cnt, "avg_launch_ms": round(ms / cnt, 4),
+            "traffic": None, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
+            "avg_launch_ms": round(ms / cnt, 4),
             "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
 
 
@@ -260,7 +272,8 @@ def run_ours(args, ws, rank, local):
     out_per_step = nnz * len(ops)
     value = out_per_step * args.steps * ws / (ms * 1e-3)
     roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm)
-    alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols  # SURVEY 8(d) permutation formula
+    # whole op: read and write col + val per entry, p and rowptr pair per row, q and qinv
+    alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols
     op_frac = alg_bytes_op * len(ops) * args.steps / (ms * 1e-3) / 1e9 / hbm
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
@@ -374,7 +387,8 @@ def bench_extract(ctx, args, dev, hbm, ws):
     ctx.set_option(SP_OPT_TIMING, 0)
     phases = {k: round(v[0] / (steps + 1), 3) for k, v in ctx.phase_stats(reset=True).items() if v[1]}
     ms = max_over_ranks(ms, ws)
-    # nnz_sel*sc + nnz_out*(sv+sc+sv) + |I|(s_i+2 sr) + |J| s_i + n s_i + |J| s_i + |I| sr
+    # read the columns of the selected rows, read the kept values, write col + val;
+    # I, rowptr pairs and J per selected index, the column maps and the output row pointer
     L = (A.rowptr[1:] - A.rowptr[:-1])
     nnz_sel = int(L[I.long()].sum())
     ab = nnz_sel * 4 + nnz_out * 12 + (n // 2) * (4 + 16) + (n // 2) * 4 + n * 4 + (n // 2) * 4 + (n // 2) * 8

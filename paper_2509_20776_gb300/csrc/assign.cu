@@ -8,12 +8,14 @@
 //     gives the merged canonical row.
 // Identify: rowmap (row -> position in I, -1 elsewhere) and a bitmap of J; counting:
 // per row of I, len_A - |A[I[i],:] ∩ J| + len_B(i); two exclusive scans give the row
-// pointer of the rebuilt rows and of A'.  Fill: the rebuilt rows are produced by the
-// shared gather / relabel / sort pipeline into a staging buffer, then one load-balanced
-// pass assembles A' from A's untouched rows and the staged rows.
+// pointer of the rebuilt rows and of A'.  Fill: the rebuilt rows are gathered into a
+// staging buffer (kept entries of both parts, relabelled) and sorted there in place;
+// one load-balanced gather then assembles A' from A's untouched rows and the staged
+// rows.
 #include "dispatch.h"
 #include "kernels.cuh"
 #include "plan.h"
+#include "rowsort.cuh"
 
 namespace sp {
 
@@ -83,11 +85,13 @@ struct AssignLen {
   }
 };
 
-// source of row r of A': A itself (which 0) or the staged rebuilt row (which 1)
+// Assembly gather of A': row r comes from A itself or, for a row of I, from the staged
+// rebuilt row; staged positions carry bit 62 (positions stay far below 2^62).
 template <class RP, class CIt, class VTt, class IX>
-struct AssignGather {
+struct AssignGs {
   using CI = CIt;
   using VT = VTt;
+  static constexpr long long kStaged = 1ll << 62;
   const RP* rpA;
   const CI* colA;
   const VT* valA;
@@ -96,35 +100,25 @@ struct AssignGather {
   const CI* tcol;
   const VT* tval;
   long long nnzA, ntemp;
-  __device__ void src(long long r, int& which, long long& off) const {
+  __device__ long long src(long long r) const {
     const long long i = (long long)rowmap[r];
-    if (i >= 0) {
-      which = 1;
-      off = vt[i];
-    } else {
-      which = 0;
-      off = (long long)rpA[r];
-    }
+    return i >= 0 ? (vt[i] | kStaged) : (long long)rpA[r];
   }
-  __device__ void get(int which, long long pos, CI& c, VT& v) const {
-    if (which) {
-      if (pos < 0 || pos >= ntemp) {
-        c = CI(0);
-        v = VT(0);
-        return;
-      }
-      c = ld_stream(tcol + pos);
-      v = ld_stream(tval + pos);
-    } else {
-      if (pos < 0 || pos >= nnzA) {
-        c = CI(0);
-        v = VT(0);
-        return;
-      }
-      c = ld_stream(colA + pos);
-      v = ld_stream(valA + pos);
+  __device__ CI col(long long pos) const {
+    if (pos & kStaged) {
+      const long long q = pos & ~kStaged;
+      return q < ntemp ? ld_stream(tcol + q) : CI(0);
     }
+    return (pos >= 0 && pos < nnzA) ? ld_stream(colA + pos) : CI(0);
   }
+  __device__ VT val(long long pos) const {
+    if (pos & kStaged) {
+      const long long q = pos & ~kStaged;
+      return q < ntemp ? ld_stream(tval + q) : VT(0);
+    }
+    return (pos >= 0 && pos < nnzA) ? ld_stream(valA + pos) : VT(0);
+  }
+  __device__ CI map(CI c) const { return c; }
 };
 
 template <class RP, class CI, class IX>
@@ -142,8 +136,6 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_rb = cv.reserve(size_t(nI + 1) * 8);
   pl->list_cap = nI + 1;
   const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
-  const size_t o_lr = cv.reserve(size_t(pl->list_cap) * 8);
-  const size_t o_hr = cv.reserve(size_t(pl->list_cap) * 8);
   const size_t o_cn = cv.reserve(64);
   const size_t o_s1 = cv.reserve(scan_ws_bytes(nI));
   const size_t o_s2 = cv.reserve(scan_ws_bytes(m));
@@ -157,8 +149,6 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   pl->vp_out = cv.at<long long>(o_vo);
   pl->rpB = cv.at<long long>(o_rb);
   pl->cl_rows = cv.at<long long>(o_cl);
-  pl->long_rows = cv.at<long long>(o_lr);
-  pl->huge_rows = cv.at<long long>(o_hr);
   pl->counters = cv.at<unsigned>(o_cn);
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
@@ -186,8 +176,7 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
                                           static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
                                           static_cast<const CI*>(B.colidx), nullptr, I, J, jbits,
                                           m, n, A.nnz, nJ, B.nnz};
-    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->long_rows, pl->counters + 1,
-                  pl->list_cap, pl->huge_rows, pl->counters + 2, pl->list_cap};
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
     {
       SP_PHASE(SP_PHASE_COUNT);
       k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
@@ -222,22 +211,18 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   Carver cv;
   const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
   const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
-  size_t po[kPipeSlots];
-  pipe_reserve(cv, nI, nt, sizeof(VT), po);
+  const size_t o_tk = cv.reserve(16);
+  size_t r1[kRowsSlots], r2[kRowsSlots];
+  rows_reserve(cv, nI, nt, sizeof(VT), r1);
+  rows_reserve(cv, m, nnz_out, sizeof(VT), r2, false);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
   CI* tcol = cv.at<CI>(o_tc);
   VT* tval = cv.at<VT>(o_tv);
+  const int nsm = ctx->num_sms;
   if (nt > 0) {
-    PipeWs w = pipe_bind(cv, nI, nt, po);
-    PipeLists lists;
-    lists.long_rows = pl->long_rows;
-    lists.n_long = pl->counters + 1;
-    lists.long_cap = pl->list_cap;
-    lists.huge_rows = pl->huge_rows;
-    lists.n_huge = pl->counters + 2;
-    lists.huge_cap = pl->list_cap;
+    // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
     AssignLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
                                     static_cast<const CI*>(A.colidx),
                                     static_cast<const VT*>(A.values), pl->rpB,
@@ -246,21 +231,30 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
                                     static_cast<const IX*>(pl->J),
                                     static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols,
                                     A.nnz, pl->nJ, B.nnz};
+    unsigned* ticket = cv.at<unsigned>(o_tk);
+    SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, tcol,
+                                       tval, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    const RowsWs w1 = rows_bind(cv, nI, nt, r1);
     const int kb = ceil_log2_u64(uint64_t(A.ncols));
-    SP_TRY(run_pipeline(ctx, s, ld, pl->vp, nI, nt, kb, false, lists, w, tcol, tval));
+    SP_TRY((run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nt, kb, w1, nullptr, true, tcol, tval)));
   }
-  AssignGather<RP, CI, VT, IX> g{static_cast<const RP*>(A.rowptr),
-                                 static_cast<const CI*>(A.colidx),
-                                 static_cast<const VT*>(A.values),
-                                 static_cast<const IX*>(pl->rowmap), pl->vp, tcol, tval, A.nnz, nt};
-  const long long blocks = (nnz_out + GATHER_CH - 1) / GATHER_CH;
-  {
-    SP_PHASE(SP_PHASE_GATHER);
-    k_gather_rows<<<unsigned(blocks), GATHER_BLOCK, 0, s>>>(
-        g, pl->vp_out, m, nnz_out, static_cast<CI*>(Ap->colidx), static_cast<VT*>(Ap->values));
-  }
-  SP_CUDA(cudaGetLastError());
-  return SP_OK;
+  // assembly: untouched rows from A, rows of I from the staging buffer
+  const AssignGs<RP, CI, VT, IX> g{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
+                                   static_cast<const VT*>(A.values), static_cast<const IX*>(pl->rowmap),
+                                   pl->vp, tcol, tval, A.nnz, nt};
+  const RowsWs w2 = rows_bind(cv, m, nnz_out, r2, false);
+  return run_rows(ctx, s, pl->vp_out, m, nnz_out, 0, w2, &g, false, static_cast<CI*>(Ap->colidx),
+                  static_cast<VT*>(Ap->values));
 }
 
 }  // namespace sp
@@ -278,7 +272,7 @@ extern "C" sp_status sp_assign_count(sp_ctx* ctx, const sp_csr* A, const void* I
   if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
   if (mode != SP_ASSIGN_REPLACE && mode != SP_ASSIGN_SELECT2ND && mode != SP_ASSIGN_PLUS)
     return SP_ERR_INVALID_ARG;
-  if (mode != SP_ASSIGN_REPLACE) return SP_ERR_INVALID_ARG;  // see DESIGN: REPLACE only so far
+  if (mode != SP_ASSIGN_REPLACE) return SP_ERR_INVALID_ARG;  // only REPLACE is implemented
   if (nI < 0 || nJ < 0 || nI > A->nrows || nJ > A->ncols) return SP_ERR_SHAPE;
   if ((nI > 0 && !I) || (nJ > 0 && !J)) return SP_ERR_INVALID_ARG;
   if (B->nrows != nI || B->ncols != nJ) return SP_ERR_SHAPE;

@@ -9,6 +9,7 @@
 #include "dispatch.h"
 #include "kernels.cuh"
 #include "plan.h"
+#include "rowsort.cuh"
 
 namespace sp {
 
@@ -98,8 +99,6 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_vp = cv.reserve(size_t(nI + 1) * 8);
   pl->list_cap = nI + 1;
   const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
-  const size_t o_lr = cv.reserve(size_t(pl->list_cap) * 8);
-  const size_t o_hr = cv.reserve(size_t(pl->list_cap) * 8);
   const size_t o_cn = cv.reserve(64);
   const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
@@ -110,8 +109,6 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   pl->jbits = jbits;
   pl->vp = cv.at<long long>(o_vp);
   pl->cl_rows = cv.at<long long>(o_cl);
-  pl->long_rows = cv.at<long long>(o_lr);
-  pl->huge_rows = cv.at<long long>(o_hr);
   pl->counters = cv.at<unsigned>(o_cn);
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
@@ -140,8 +137,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     ExtractLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
                                            static_cast<const CI*>(A.colidx), nullptr, I, jinv,
                                            jbits, m, n, nnz};
-    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->long_rows, pl->counters + 1,
-                  pl->list_cap, pl->huge_rows, pl->counters + 2, pl->list_cap};
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
     {
       SP_PHASE(SP_PHASE_COUNT);
       k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
@@ -168,27 +164,38 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   SP_TRY(store_rowptr(ctx, s, pl->vp, nI + 1, B->rowptr_type, B->rowptr));
   if (nnz_out == 0) return SP_OK;
   Carver cv;
-  size_t po[kPipeSlots];
-  pipe_reserve(cv, nI, nnz_out, sizeof(VT), po);
+  size_t ro[kRowsSlots];
+  rows_reserve(cv, nI, nnz_out, sizeof(VT), ro);
+  const size_t o_tk = cv.reserve(16);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
-  PipeWs w = pipe_bind(cv, nI, nnz_out, po);
-  PipeLists lists;
-  lists.long_rows = pl->long_rows;
-  lists.n_long = pl->counters + 1;
-  lists.long_cap = pl->list_cap;
-  lists.huge_rows = pl->huge_rows;
-  lists.n_huge = pl->counters + 2;
-  lists.huge_cap = pl->list_cap;
   ExtractLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
                                    static_cast<const CI*>(A.colidx),
                                    static_cast<const VT*>(A.values), static_cast<const IX*>(pl->I),
                                    static_cast<const IX*>(pl->jmap),
                                    static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz};
+  CI* oc = static_cast<CI*>(B->colidx);
+  VT* ov = static_cast<VT*>(B->values);
+  // fill: kept entries, relabelled through jinv, into their output rows
+  unsigned* ticket = cv.at<unsigned>(o_tk);
+  SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
+  const int nsm = ctx->num_sms;
+  {
+    SP_PHASE(SP_PHASE_GATHER);
+    k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, oc, ov, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  {
+    SP_PHASE(SP_PHASE_GATHER);
+    k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, oc, ov,
+                                     ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  // sort every row in place
+  const RowsWs w = rows_bind(cv, nI, nnz_out, ro);
   const int kb = ceil_log2_u64(uint64_t(pl->nJ));
-  return run_pipeline(ctx, s, ld, pl->vp, nI, nnz_out, kb, false, lists, w,
-                      static_cast<CI*>(B->colidx), static_cast<VT*>(B->values));
+  return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nnz_out, kb, w, nullptr, true, oc, ov);
 }
 
 sp_status plan_release(sp_ctx* ctx, sp_plan* pl) {

@@ -1,9 +1,10 @@
-// Index maps, per-row counting passes, the tile partition and the load-balanced row
-// gather.  Every kernel that dereferences an index taken from user data checks it
-// first: a bad index is reported through the device error record and never read.
+// Index maps and the per-row count and fill passes.  Every kernel that dereferences an
+// index taken from user data checks it first: a bad index is reported through the
+// device error record and never read.
 #pragma once
 
-#include "pipeline.cuh"
+#include "loaders.cuh"
+#include "scan.cuh"
 
 namespace sp {
 
@@ -82,18 +83,12 @@ __global__ void k_narrow(const long long* __restrict__ in, long long n, T* __res
 }
 
 // ---- counting passes (Alg. 5 first pass, restated as a ballot/popc per warp) ------
-// A row is "source-long" when its source holds more than TILE_CP entries: it is
-// counted by k_count_long (one CTA per row) and listed for k_long / k_huge.
+// A row is "source-long" when its source holds more than SRC_LONG entries: it is
+// counted and filled by one CTA (k_count_long, k_fill_long) instead of a warp.
 struct CountLists {
   long long* cl_rows;  // source-long rows waiting for k_count_long
   unsigned* n_cl;
   long long cl_cap;
-  long long* long_rows;
-  unsigned* n_long;
-  long long long_cap;
-  long long* huge_rows;
-  unsigned* n_huge;
-  long long huge_cap;
 };
 
 __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long cap, long long r,
@@ -106,8 +101,8 @@ __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long
 // Count kernels take a loader (see segsort.cuh) and count the entries its map keeps.
 // Short rows: one warp handles COUNT_RB rows per step, reading the first 32 entries of
 // all of them in one batch (ballot + popc per row); the rest of longer rows follows
-// in batches of LOAD_U x 32.  Source-long rows (> TILE_CP entries) are listed for
-// k_count_long (one CTA per row) and later handled by k_long / k_huge.
+// in batches of LOAD_U x 32.  Source-long rows (> SRC_LONG entries) are listed for
+// k_count_long (one CTA per row).
 constexpr int COUNT_RB = 4;
 
 template <class Ct>
@@ -127,7 +122,7 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
       const long long i = i0 + u;
       rs[u] = i < nlisted ? ct.row(i) : RowSrc{0, 0, 0, 0};
       Ls[u] = rs[u].n0 + rs[u].n1;
-      lng[u] = Ls[u] > TILE_CP;
+      lng[u] = Ls[u] > SRC_LONG;
       bt.valid[u] = !lng[u] && lane < Ls[u];
       if (bt.valid[u]) bt.at(u, rs[u], lane);
     }
@@ -198,121 +193,129 @@ __global__ void __launch_bounds__(1024) k_count_long(Ct ct, long long* __restric
     if (t < 32) {
       long long v = t < int(blockDim.x >> 5) ? red[t] : 0;
       v = warp_sum(v);
-      if (t == 0) {
-        counts[i] = v;
-        if (v <= LONG_CAP) push_row(cl.long_rows, cl.n_long, cl.long_cap, i, st);
-        else push_row(cl.huge_rows, cl.n_huge, cl.huge_cap, i, st);
-      }
+      if (t == 0) counts[i] = v;
     }
     __syncthreads();
   }
 }
 
-// ---- load-balanced row gather -------------------------------------------------------
-// out[vp[r] + k] = source element (which, off(r) + k) for k < vp[r+1]-vp[r]; each CTA
-// owns GATHER_CH consecutive output positions, so long and short rows cost the same.
-// Gs: __device__ void src(long long r, int& which, long long& off) const;
-//     __device__ void get(int which, long long pos, CI& c, VT& v) const;
-constexpr int GATHER_BLOCK = 512, GATHER_CH = 8192;
-
-template <class Gs>
-__global__ void __launch_bounds__(GATHER_BLOCK) k_gather_rows(Gs gs, const long long* __restrict__ vp,
-                                                              long long nrows, long long total,
-                                                              typename Gs::CI* __restrict__ out_col,
-                                                              typename Gs::VT* __restrict__ out_val) {
-  using CI = typename Gs::CI;
-  using VT = typename Gs::VT;
-  constexpr int B = GATHER_BLOCK, ITEMS = GATHER_CH / B;
-  __shared__ uint32_t owner[GATHER_CH];
-  __shared__ long long r_off[B];
-  __shared__ long long r_o0[B];
-  __shared__ long long r_o1[B];
-  __shared__ int r_which[B];
-  __shared__ uint32_t tmp32[B / 32 + 1];
-  __shared__ long long s_first;
-  const int t = threadIdx.x;
-  const long long c0 = blockIdx.x * (long long)GATHER_CH;
-  if (c0 >= total) return;
-  const long long c1 = c0 + GATHER_CH < total ? c0 + GATHER_CH : total;
-  if (t == 0) {  // last row with vp[r] <= c0
-    long long lo = 0, hi = nrows;
-    while (hi - lo > 1) {
-      const long long mid = (lo + hi) >> 1;
-      if (vp[mid] <= c0) lo = mid;
-      else hi = mid;
-    }
-    s_first = lo;
+// ---- fill passes (Alg. 5 second pass) --------------------------------------------------
+// The kept entries of listed row i, relabelled, are written to [vp[i], vp[i+1]) of
+// (out_col, out_val) in no particular order (the row sort orders them): a warp ballot
+// over 32 entries gives each kept entry its slot.  Short rows as in k_count_warp;
+// source-long rows (cl_rows) one CTA each, the CTA's warps taking slots from a shared
+// cursor.  A slot past the row's end (counts that do not match the fill) is reported
+// and not written.
+template <class Ld>
+__device__ __forceinline__ void fill_put(const Ld&, typename Ld::CI* out_col, typename Ld::VT* out_val,
+                                         long long pos, long long end, uint32_t key,
+                                         const typename Ld::VT& v, DevStatus* st) {
+  if (pos < end) {
+    st_stream(out_col + pos, typename Ld::CI(key));
+    st_stream(out_val + pos, v);
+  } else {
+    dev_fail(st, SP_ERR_INTERNAL, -23);
   }
-  __syncthreads();
-  for (long long rb = s_first;; rb += B) {
-    const long long r = rb + t;
-    long long o0 = total, o1 = total;
-    if (r < nrows) {
-      o0 = vp[r];
-      o1 = vp[r + 1];
-    }
-    const bool active = r < nrows && o1 > o0 && o1 > c0 && o0 < c1;
-    if (active) {
-      int which;
-      long long off;
-      gs.src(r, which, off);
-      r_which[t] = which;
-      r_off[t] = off;
-      r_o0[t] = o0;
-      r_o1[t] = o1;
-    }
-    for (int j = 0; j < ITEMS; ++j) owner[t + j * B] = 0xFFFFFFFFu;
-    __syncthreads();
-    if (active) {
-      const long long p = o0 > c0 ? o0 : c0;
-      owner[p - c0] = uint32_t(t);
-    }
-    __syncthreads();
-    // inclusive max-scan where "unset" (0xFFFFFFFF) is treated as -inf
+}
+
+constexpr int FILL_RB = 2;  // rows per warp step of the fill (fewer than counting: values)
+
+template <class Ld>
+__global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, const long long* __restrict__ vp,
+                            typename Ld::CI* __restrict__ out_col, typename Ld::VT* __restrict__ out_val,
+                            DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i0 = w0 * FILL_RB; i0 < nlisted; i0 += nw * FILL_RB) {
+    RowSrc rs[FILL_RB];
+    long long Ls[FILL_RB], o[FILL_RB], oe[FILL_RB];
+    bool lng[FILL_RB];
+    Batch<Ld, FILL_RB> bt;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t * ITEMS + j;
-      if (owner[x] == 0xFFFFFFFFu) owner[x] = 0;
-      else owner[x] += 1;
+    for (int u = 0; u < FILL_RB; ++u) {
+      const long long i = i0 + u;
+      rs[u] = i < nlisted ? ld.row(i) : RowSrc{0, 0, 0, 0};
+      o[u] = i < nlisted ? vp[i] : 0;
+      oe[u] = i < nlisted ? vp[i + 1] : 0;
+      Ls[u] = rs[u].n0 + rs[u].n1;
+      lng[u] = Ls[u] > SRC_LONG;
+      bt.valid[u] = !lng[u] && lane < Ls[u];
+      if (bt.valid[u]) bt.at(u, rs[u], lane);
     }
-    __syncthreads();
-    smem_incl_max<B, ITEMS>(owner, GATHER_CH, tmp32);
-    // all loads first, then all stores: the stores may not be moved above later loads
-    // (the compiler cannot rule out aliasing), so interleaving would serialise them
-    constexpr int H = 8;
+    bt.run(ld);
 #pragma unroll
-    for (int h = 0; h < ITEMS; h += H) {
-      CI c[H];
-      VT v[H];
-      bool ok[H];
+    for (int u = 0; u < FILL_RB; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, bt.kept[u]);
+      if (bt.kept[u]) fill_put(ld, out_col, out_val, o[u] + __popc(m & lt), oe[u], bt.key[u], bt.v[u], st);
+      o[u] += __popc(m);
+    }
 #pragma unroll
-      for (int u = 0; u < H; ++u) {
-        const int x = t + (h + u) * B;
-        const long long g = c0 + x;
-        const uint32_t ow = owner[x];
-        ok[u] = false;
-        if (g < c1 && ow > 0) {
-          const int k = int(ow) - 1;
-          const long long o = r_o0[k];
-          // positions beyond the chunk's rows belong to the next chunk of rows
-          if (g >= o && g < r_o1[k]) {
-            ok[u] = true;
-            gs.get(r_which[k], r_off[k] + (g - o), c[u], v[u]);
-          }
+    for (int u = 0; u < FILL_RB; ++u) {
+      if (lng[u] || Ls[u] <= 32) continue;
+      for (long long e0 = 32; e0 < Ls[u]; e0 += 32 * LOAD_U) {
+        Batch<Ld, LOAD_U> b2;
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const long long e = e0 + v * 32 + lane;
+          b2.valid[v] = e < Ls[u];
+          if (b2.valid[v]) b2.at(v, rs[u], e);
+        }
+        b2.run(ld);
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const unsigned m = __ballot_sync(0xffffffffu, b2.kept[v]);
+          if (b2.kept[v]) fill_put(ld, out_col, out_val, o[u] + __popc(m & lt), oe[u], b2.key[v], b2.v[v], st);
+          o[u] += __popc(m);
         }
       }
+    }
+  }
+}
+
+template <class Ld>
+__global__ void __launch_bounds__(1024) k_fill_long(Ld ld, const long long* __restrict__ cl_rows,
+                                                    const unsigned* __restrict__ n_cl, long long cl_cap,
+                                                    const long long* __restrict__ vp, unsigned* ticket,
+                                                    typename Ld::CI* __restrict__ out_col,
+                                                    typename Ld::VT* __restrict__ out_val, DevStatus* st) {
+  __shared__ unsigned s_item;
+  __shared__ unsigned long long s_cur;
+  const int t = threadIdx.x, lane = t & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned count = *n_cl;
+  if (count > cl_cap) count = unsigned(cl_cap);
+  for (;;) {
+    if (t == 0) {
+      s_item = atomicAdd(ticket, 1u);
+      s_cur = 0;
+    }
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= count) break;
+    const long long i = cl_rows[item];
+    const RowSrc rs = ld.row(i);
+    const long long Ls = rs.n0 + rs.n1, o = vp[i], oe = vp[i + 1];
+    for (long long e0 = 0; e0 < Ls; e0 += (long long)blockDim.x * LOAD_U) {
+      Batch<Ld, LOAD_U> bt;
 #pragma unroll
-      for (int u = 0; u < H; ++u) {
-        if (!ok[u]) continue;
-        const long long g = c0 + t + (h + u) * B;
-        st_stream(out_col + g, c[u]);
-        st_stream(out_val + g, v[u]);
+      for (int u = 0; u < LOAD_U; ++u) {
+        const long long e = e0 + (long long)u * blockDim.x + t;
+        bt.valid[u] = e < Ls;
+        if (bt.valid[u]) bt.at(u, rs, e);
+      }
+      bt.run(ld);
+#pragma unroll
+      for (int u = 0; u < LOAD_U; ++u) {
+        const unsigned m = __ballot_sync(0xffffffffu, bt.kept[u]);
+        unsigned long long b = 0;
+        if (lane == 0 && m) b = atomicAdd(&s_cur, (unsigned long long)__popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (bt.kept[u]) fill_put(ld, out_col, out_val, o + (long long)b + __popc(m & lt), oe, bt.key[u], bt.v[u], st);
       }
     }
     __syncthreads();
-    // stop once the chunk's last row reaches the end of this CTA's positions
-    const long long rl = rb + B - 1;
-    if (rl >= nrows - 1 || vp[rl + 1] >= c1) break;
   }
 }
 

@@ -1,0 +1,85 @@
+// Source-row loaders of the count and fill passes.
+//
+// A loader describes where listed row i takes its entries from and which survive:
+//   struct Loader {
+//     using CI = ...;  using VT = ...;           // column index / value word types
+//     static constexpr bool kAllKept;            // no source entry is ever dropped
+//     static constexpr bool kLoadVals;           // the pass needs the values
+//     RowSrc row(int64 i) const;                 // source runs of listed row i
+//     const CI* cols(int part) const;            // column / value arrays of run `part`
+//     const VT* vals(int part) const;
+//     bool test(int part, int64 c) const;        // does an entry of column c survive
+//     bool map(int part, int64 c, uint32& key) const;
+//         // new column of a surviving entry with column c (false: dropped)
+//   };
+// Source entries are read in batches (struct Batch): every thread first issues the
+// column loads of U entries, then their map lookups, then their value loads, so that
+// U independent chains of dependent loads are in flight per thread.
+#pragma once
+
+#include "common.cuh"
+
+namespace sp {
+
+struct RowSrc {
+  long long s0, s1;  // start of run 0 / run 1 in the source arrays
+  long long n0, n1;  // lengths (n1 = 0 for single-run sources)
+};
+
+// U source entries read together (see the file comment).
+template <class Ld, int U>
+struct Batch {
+  long long pos[U];
+  int part[U];
+  bool valid[U];
+  bool kept[U];
+  uint32_t key[U];
+  typename Ld::VT v[U];
+  __device__ __forceinline__ void run(const Ld& ld) {
+    using CI = typename Ld::CI;
+    CI c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = valid[u] ? ld_stream(ld.cols(part[u]) + pos[u]) : CI(0);
+    if constexpr (Ld::kLoadVals && Ld::kAllKept) {
+      // nothing is dropped: the value loads need not wait for the map lookups
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (valid[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) kept[u] = valid[u] && ld.map(part[u], (long long)c[u], key[u]);
+    if constexpr (Ld::kLoadVals && !Ld::kAllKept) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (kept[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
+    }
+  }
+  // entry e of a row's source runs
+  __device__ __forceinline__ void at(int u, const RowSrc& rs, long long e) {
+    part[u] = e < rs.n0 ? 0 : 1;
+    pos[u] = part[u] ? rs.s1 + (e - rs.n0) : rs.s0 + e;
+  }
+};
+
+constexpr int LOAD_U = 4;  // entries per thread per batch
+
+// A loader view for counting passes: membership only (no key, no value loads).
+template <class Ld>
+struct CountOnly {
+  using CI = typename Ld::CI;
+  struct Nothing {};
+  using VT = Nothing;
+  static constexpr bool kLoadVals = false;
+  static constexpr bool kAllKept = false;
+  Ld ld;
+  __device__ __forceinline__ const CI* cols(int part) const { return ld.cols(part); }
+  __device__ __forceinline__ bool map(int part, long long c, uint32_t&) const {
+    return ld.test(part, c);
+  }
+};
+
+// Rows whose source holds more than SRC_LONG entries are "source-long": the count and
+// fill passes give each of them a whole CTA instead of a warp.
+constexpr int SRC_LONG = 1024;
+
+}  // namespace sp

@@ -24,10 +24,8 @@ struct sp_plan {
   long long* vp_out = nullptr; // assignment: row pointer of A'
   long long* rpB = nullptr;    // assignment: B's row pointer widened to int64
   long long* cl_rows = nullptr;
-  long long* long_rows = nullptr;
-  long long* huge_rows = nullptr;
   long long list_cap = 0;
-  unsigned* counters = nullptr;  // [0] n_cl [1] n_long [2] n_huge [3] count ticket
+  unsigned* counters = nullptr;  // [0] n_cl [3] count ticket
   long long* h_tail = nullptr;   // pinned host: totals read back by the count call
 };
 

@@ -3,44 +3,69 @@
 //     at its final row position but in source order (a load-balanced gather over
 //     fixed chunks of output positions: no shared-memory sort, all loads independent);
 //   phase 2, the rows of the output are sorted in place:
-//     * rows of at most SS_CP entries in tiles (consecutive rows, at most SS_CAP
-//       entries and SS_ROWS rows per tile), k_seg_sort;
-//     * rows of SS_CP < L <= SS_CAP entries alone, k_seg_sort;
-//     * longer rows are first partitioned by key range (k_huge) into runs of at most
-//       SS_CAP entries, which k_seg_sort then sorts.
+//     * rows of at most SS_TILE_MAX entries in tiles (consecutive rows, at most
+//       2 * SS_TILE_MAX entries per tile), k_seg_sort<SsTile>;
+//     * rows of SS_TILE_MAX < L <= SS_RUN_MAX entries alone, k_seg_sort<SsRun>;
+//     * longer rows are first partitioned by key range (k_split) into runs of at most
+//       SS_RUN_MAX entries, which k_seg_sort<SsRun> then sorts.
 // One scan over the output rows (RowsPartition) cuts the tiles and the gather chunks
 // and lists the rows that do not fit a tile.
 #pragma once
 
-#include "pipeline.cuh"
+#include "scan.cuh"
 
 namespace sp {
 
-constexpr int SS_BLOCK = 512;
-constexpr int SS_CAP = 4096;                   // entries per work item
-constexpr int SS_CP = SS_CAP / 2;              // longest row a tile accepts
 constexpr int SS_ROW_W = 4;                    // partition weight of a row
-constexpr int SS_ROWS = SS_CP / SS_ROW_W;      // rows per tile
-constexpr int SS_WORDS = SS_CAP / 32;          // row-start bitmap words
-constexpr int SS_U = SS_CAP / SS_BLOCK;        // entries per thread
 constexpr int SS_HEAVY = 128;                  // larger buckets are sorted by a later pass
 constexpr int SS_PASSES = 3;                   // passes over queued heavy buckets
-static_assert(SS_ROWS <= SS_BLOCK, "one thread per row of a tile");
-static_assert(SS_CAP <= LONG_CAP, "runs of k_huge fit a work item");
-static_assert(SS_WORDS == 4 * 32, "one warp scans the bitmap, four words per lane");
+
+// A sort configuration: BLOCK threads sort items of at most CAP entries; a tile holds
+// the rows whose partition coordinate starts in a window of CP = CAP / 2, so at most
+// ROWS = CP / SS_ROW_W rows (one thread each) of at most CP entries.
+template <int BLOCK_, int CAP_>
+struct SsCfg {
+  static constexpr int B = BLOCK_, CAP = CAP_, CP = CAP_ / 2, ROWS = CP / SS_ROW_W;
+  static constexpr int WORDS = CAP_ / 32;  // row-start bitmap words
+  static_assert(ROWS <= B, "one thread per row of a tile");
+  static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
+};
+using SsTile = SsCfg<256, 2048>;  // tiles of rows of at most 1024 entries, 4 CTAs per SM
+using SsRun = SsCfg<512, 4096>;   // single runs of at most 4096 entries, 2 CTAs per SM
+constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts
+constexpr int SS_RUN_MAX = SsRun::CAP;   // longest row sorted alone
+
+// Runs handed from one kernel to the next: in the output arrays or in the temporary
+// arrays (keys as uint32, values) at the same offsets.
+enum BufId : int { BUF_TEMP = 0, BUF_OUT = 1 };
+
+struct FinalEntry {  // a run of at most SS_RUN_MAX entries left to sort in place
+  long long off;
+  long long len;
+  int buf;
+  int pad;
+};
+struct HugeEntry {  // a run longer than SS_RUN_MAX, keys in [lo, lo + 2^wb)
+  long long off;
+  long long len;
+  unsigned lo;
+  int wb;
+  int buf;
+  int pad;
+};
 
 constexpr int GC_BLOCK = 512;                  // gather: threads per CTA
 constexpr int GC_CH = 4096;                    // gather: output positions per CTA
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
 
 // ---- partition ----------------------------------------------------------------------
-// Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= SS_CP).  With
-// c(r) the exclusive prefix of the weights, tile t holds the rows with c(r) in
-// [t*SS_CP, (t+1)*SS_CP): at most SS_ROWS rows and 2*SS_CP entries.  Gather chunk k
-// starts at the row holding output position k*GC_CH.
+// Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= SS_TILE_MAX).
+// With c(r) the exclusive prefix of the weights, tile t holds the rows with c(r) in
+// [t*SS_TILE_MAX, (t+1)*SS_TILE_MAX): at most SsTile::ROWS rows and 2*SS_TILE_MAX
+// entries.  Gather chunk k starts at the row holding output position k*GC_CH.
 __device__ __forceinline__ long long rows_weight(const long long* vp, long long r) {
   const long long L = vp[r + 1] - vp[r];
-  return SS_ROW_W + (L <= SS_CP ? L : 0);
+  return SS_ROW_W + (L <= SS_TILE_MAX ? L : 0);
 }
 
 struct RowsWeight {
@@ -59,14 +84,15 @@ struct RowsPartition {
   FinalEntry* fin;  // rows sorted alone
   unsigned* fin_n;
   long long fin_cap;
-  HugeEntry* huge;  // rows for k_huge
+  HugeEntry* huge;  // rows for k_split
   unsigned* huge_n;
   long long huge_cap;
   int key_bits;
+  int classify;  // list the rows that do not fit a tile (only when the rows are sorted)
   DevStatus* st;
   __device__ void operator()(long long r, long long c) const {
     if (r == nrows) {  // c = total weight
-      long long nt = c / SS_CP + 1;
+      long long nt = c / SS_TILE_MAX + 1;
       if (nt > ntiles_cap) {
         dev_fail(st, SP_ERR_INTERNAL, -14);
         nt = ntiles_cap;
@@ -77,16 +103,16 @@ struct RowsPartition {
     }
     if (r == 0) tile_first[0] = 0;
     const long long o0 = vp[r], o1 = vp[r + 1], L = o1 - o0;
-    const long long e = c + SS_ROW_W + (L <= SS_CP ? L : 0);
-    long long t_lo = c / SS_CP + 1, t_hi = e / SS_CP;
+    const long long e = c + SS_ROW_W + (L <= SS_TILE_MAX ? L : 0);
+    long long t_lo = c / SS_TILE_MAX + 1, t_hi = e / SS_TILE_MAX;
     if (t_hi > ntiles_cap - 1) t_hi = ntiles_cap - 1;
     for (long long t = t_lo; t <= t_hi; ++t) tile_first[t] = r + 1;
     if (L <= 0) return;
     long long k_hi = (o1 - 1) / GC_CH;
     if (k_hi > nchunks - 1) k_hi = nchunks - 1;
     for (long long k = (o0 + GC_CH - 1) / GC_CH; k <= k_hi; ++k) chunk_first[k] = r;
-    if (L > SS_CP) {
-      if (L <= SS_CAP) {
+    if (classify && L > SS_TILE_MAX) {
+      if (L <= SS_RUN_MAX) {
         const unsigned q = atomicAdd(fin_n, 1u);
         if (q < fin_cap) fin[q] = FinalEntry{o0, L, BUF_OUT, 0};
         else dev_fail(st, SP_ERR_INTERNAL, -15);
@@ -192,6 +218,179 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
   }
 }
 
+// ---- key-range split of long runs ------------------------------------------------------
+// A run of more than SS_RUN_MAX entries with keys in [lo, lo + 2^wb) is cut into
+// SPLIT_NB buckets of 2^(wb - SPLIT_NB_LOG) consecutive keys: pass 1 counts the bucket
+// sizes, one scan gives their offsets, pass 2 scatters the run bucket by bucket into the
+// other buffer (output <-> temporary) at the same offsets.  Consecutive small buckets
+// whose starts fall in one GROUP_CAP window form one run for k_seg_sort; a bucket of
+// more than GROUP_CAP entries is a run of its own, or (more than SS_RUN_MAX entries,
+// only when a bucket spans more than SS_RUN_MAX keys) a run for the next split round.
+constexpr int SPLIT_BLOCK = 1024;
+constexpr int SPLIT_NB_LOG = 14;
+constexpr int SPLIT_NB = 1 << SPLIT_NB_LOG;
+constexpr int SPLIT_U = 4;                 // entries per thread per batch
+constexpr int GROUP_CAP = SS_RUN_MAX / 2;  // small buckets grouped up to this start window
+constexpr size_t split_smem_bytes() { return size_t(SPLIT_NB) * 4 * 2; }
+
+template <class CI, class VT>
+__global__ void __launch_bounds__(SPLIT_BLOCK, 1)
+    k_split(const HugeEntry* __restrict__ runs, const unsigned* __restrict__ nruns_p, long long runs_cap,
+            unsigned* ticket, uint32_t* __restrict__ tkey, VT* __restrict__ tval, CI* __restrict__ out_col,
+            VT* __restrict__ out_val, FinalEntry* __restrict__ fin, unsigned* fin_n, long long fin_cap,
+            HugeEntry* __restrict__ nxt, unsigned* nxt_n, long long nxt_cap, DevStatus* st) {
+  constexpr int B = SPLIT_BLOCK, ITEMS = SPLIT_NB / B, U = SPLIT_U;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* aux = hist + SPLIT_NB;
+  __shared__ uint32_t tmp32[B / 32 + 1];
+  __shared__ unsigned s_item;
+  const int t = threadIdx.x;
+  unsigned count = *nruns_p;
+  if (count > runs_cap) count = unsigned(runs_cap);
+  for (;;) {
+    if (t == 0) s_item = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= count) break;
+    const HugeEntry he = runs[item];
+    const long long g0 = he.off, L = he.len;
+    const unsigned lo = he.lo;
+    const int wb = he.wb, sbuf = he.buf;
+    const int dbuf = sbuf == BUF_TEMP ? BUF_OUT : BUF_TEMP;
+    const int nbl = wb < SPLIT_NB_LOG ? wb : SPLIT_NB_LOG;
+    const int nb = 1 << nbl;
+    const int sh = wb - nbl;
+    for (int x = t; x < SPLIT_NB; x += B) hist[x] = 0;
+    __syncthreads();
+    const uint32_t* skp = tkey + g0;
+    const CI* sop = out_col + g0;
+    // pass 1: bucket sizes
+    for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
+      uint32_t k[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * B;
+        if (e < L) k[u] = sbuf == BUF_TEMP ? ld_stream(skp + e) : uint32_t(ld_stream(sop + e));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * B;
+        if (e >= L) continue;
+        const uint32_t bk = (k[u] - lo) >> sh;
+        if (k[u] >= lo && bk < uint32_t(nb)) atomicAdd(&hist[bk], 1u);
+        else dev_fail(st, SP_ERR_INDEX_RANGE, g0 + e);  // a column outside [0, ncols)
+      }
+    }
+    __syncthreads();
+    const uint32_t total = smem_excl_sum<B, ITEMS>(hist, SPLIT_NB, tmp32);
+    if (total != uint32_t(L)) {
+      if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -5);
+      continue;
+    }
+    // previous non-empty bucket (inclusive max-scan of b+1 over non-empty buckets)
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int x = t * ITEMS + j;
+      const uint32_t c = (x + 1 < nb ? hist[x + 1] : uint32_t(L)) - hist[x];
+      aux[x] = (x < nb && c > 0) ? uint32_t(x + 1) : 0u;
+    }
+    __syncthreads();
+    smem_incl_max<B, ITEMS>(aux, SPLIT_NB, tmp32);
+    // heads of groups: small non-empty buckets that start a new group of consecutive
+    // small buckets (group = buckets whose start lies in one GROUP_CAP window, cut at
+    // every big bucket); big buckets stand alone.
+    bool head[ITEMS], big[ITEMS];
+    uint32_t cc[ITEMS], sb[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int x = t * ITEMS + j;
+      sb[j] = hist[x];
+      cc[j] = x < nb ? (x + 1 < nb ? hist[x + 1] : uint32_t(L)) - sb[j] : 0u;
+      big[j] = cc[j] > uint32_t(GROUP_CAP);
+      head[j] = false;
+      if (cc[j] > 0 && !big[j]) {
+        const uint32_t pv = x > 0 ? aux[x - 1] : 0u;  // previous non-empty bucket + 1
+        if (pv == 0) {
+          head[j] = true;
+        } else {
+          const int y = int(pv) - 1;
+          const uint32_t cy = (y + 1 < nb ? hist[y + 1] : uint32_t(L)) - hist[y];
+          head[j] = cy > uint32_t(GROUP_CAP) || (hist[y] / GROUP_CAP) != (sb[j] / GROUP_CAP);
+        }
+      }
+    }
+    __syncthreads();
+    // next boundary start after each bucket: suffix min over boundary starts, computed
+    // as a prefix max over the reversed array of (L - start)
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int x = t * ITEMS + j;
+      const bool bnd = head[j] || big[j];
+      aux[SPLIT_NB - 1 - x] = bnd ? uint32_t(L) - sb[j] : 0u;
+    }
+    __syncthreads();
+    smem_incl_max<B, ITEMS>(aux, SPLIT_NB, tmp32);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int x = t * ITEMS + j;
+      if (x >= nb || cc[j] == 0) continue;
+      if (big[j]) {
+        if (cc[j] <= uint32_t(SS_RUN_MAX)) {
+          const unsigned q = atomicAdd(fin_n, 1u);
+          if (q < fin_cap) fin[q] = FinalEntry{g0 + sb[j], cc[j], dbuf, 0};
+          else dev_fail(st, SP_ERR_INTERNAL, -6);
+        } else {
+          const unsigned q = atomicAdd(nxt_n, 1u);
+          if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb[j], cc[j], lo + (uint32_t(x) << sh), sh, dbuf, 0};
+          else dev_fail(st, SP_ERR_INTERNAL, -7);
+        }
+      } else if (head[j]) {
+        // reversed index of x+1 holds max over buckets >= x+1 of (L - start) -> min start
+        const uint32_t nx = (x + 1 < SPLIT_NB) ? aux[SPLIT_NB - 1 - (x + 1)] : 0u;
+        const uint32_t end = nx ? uint32_t(L) - nx : uint32_t(L);
+        const unsigned q = atomicAdd(fin_n, 1u);
+        if (q < fin_cap) fin[q] = FinalEntry{g0 + sb[j], (long long)(end - sb[j]), dbuf, 0};
+        else dev_fail(st, SP_ERR_INTERNAL, -6);
+      }
+    }
+    __syncthreads();
+    // pass 2: scatter bucket by bucket (hist now serves as the bucket cursors)
+    const VT* svp = sbuf == BUF_TEMP ? tval + g0 : out_val + g0;
+    for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
+      uint32_t k[U];
+      VT v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * B;
+        if (e < L) k[u] = sbuf == BUF_TEMP ? ld_stream(skp + e) : uint32_t(ld_stream(sop + e));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * B;
+        if (e < L) v[u] = ld_stream(svp + e);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long e = e0 + (long long)u * B;
+        if (e >= L) continue;
+        const uint32_t bk = (k[u] - lo) >> sh;
+        if (k[u] < lo || bk >= uint32_t(nb)) continue;
+        const uint32_t q = atomicAdd(&hist[bk], 1u);
+        if (q >= uint32_t(L)) continue;
+        if (dbuf == BUF_TEMP) {
+          st_stream(tkey + g0 + q, k[u]);
+          st_stream(tval + g0 + q, v[u]);
+        } else {
+          st_stream(out_col + g0 + q, CI(k[u]));
+          st_stream(out_val + g0 + q, v[u]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---- phase 2: in-place sort of output rows ---------------------------------------------
 // Bucket of key k in a row of L entries: nb = 2^(ceil(log2 L) - 1) buckets spaced evenly
 // in an approximate square root of k over the row's key range [0, kmax].  The root is
@@ -212,22 +411,23 @@ __device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_
   return b < last ? b : last;
 }
 
-template <class VT>
+template <class Cfg, class VT>
 __host__ __device__ constexpr size_t ss_smem_bytes() {
-  return size_t(SS_CAP) * (sizeof(VT) + 4 * 3 + 2 * 3) + size_t(SS_ROWS) * (4 * 2 + 2 * 2) +
-         size_t(SS_WORDS) * 4 * 2;
+  return size_t(Cfg::CAP) * (sizeof(VT) + 4 * 3 + 2 * 3) + size_t(Cfg::ROWS) * (4 * 2 + 2 * 2) +
+         size_t(Cfg::WORDS) * 4 * 2;
 }
 
-// In-place exclusive sum of a[0, n), n <= SS_CAP; thread t owns the ceil(n / SS_BLOCK)
-// consecutive entries starting at t * ceil(n / SS_BLOCK).
+// In-place exclusive sum of a[0, n); thread t owns the ceil(n / B) consecutive entries
+// starting at t * ceil(n / B).
+template <int B>
 __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
   const int t = threadIdx.x;
-  const int per = (n + SS_BLOCK - 1) / SS_BLOCK;
+  const int per = (n + B - 1) / B;
   const int x0 = t * per, x1 = x0 + per < n ? x0 + per : n;
   uint32_t s = 0;
   for (int x = x0; x < x1; ++x) s += a[x];
   uint32_t total;
-  uint32_t run = block_excl_sum<SS_BLOCK>(s, tmp, &total);
+  uint32_t run = block_excl_sum<B>(s, tmp, &total);
   for (int x = x0; x < x1; ++x) {
     const uint32_t v = a[x];
     a[x] = run;
@@ -237,35 +437,35 @@ __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
 }
 
 // Work items: tiles [0, *ntiles) of the partition, then runs fin[0, *fin_n) (rows of
-// SS_CP < L <= SS_CAP entries, in the output arrays, and k_huge's runs, in the output
-// or in the temporary arrays).  Every item's entries are loaded into shared memory
+// SS_TILE_MAX < L <= SS_RUN_MAX entries, in the output arrays, and k_split's runs, in
+// the output or in the temporary arrays).  Every item's entries are loaded into shared memory
 // before any of them is written back, so a run is sorted in place.  A bucket of more
 // than SS_HEAVY keys (skewed keys) is written in bucket order and queued in hv[] as a
 // run for a later pass, which buckets it over its own key range; without hv (the last
 // pass) every bucket is ranked directly.
-template <class CI, class VT>
-__global__ void __launch_bounds__(SS_BLOCK, 2)
+template <class Cfg, class CI, class VT>
+__global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
     k_seg_sort(const long long* __restrict__ vp, const long long* __restrict__ tile_first,
                const long long* __restrict__ ntiles_p, const FinalEntry* __restrict__ fin,
                const unsigned* __restrict__ fin_n, long long fin_cap, const uint32_t* __restrict__ tkey_g,
                const VT* __restrict__ tval_g, CI* __restrict__ out_col, VT* __restrict__ out_val,
                FinalEntry* __restrict__ hv, unsigned* hv_n, long long hv_cap, int key_bits,
                DevStatus* st) {
-  constexpr int B = SS_BLOCK, CAP = SS_CAP, U = SS_U;
+  constexpr int B = Cfg::B, CAP = Cfg::CAP, ROWS = Cfg::ROWS, WORDS = Cfg::WORDS;
   extern __shared__ __align__(16) unsigned char smem[];
   VT* sval = reinterpret_cast<VT*>(smem);
   uint32_t* skey = reinterpret_cast<uint32_t*>(smem + size_t(CAP) * sizeof(VT));  // packed order
   uint32_t* tkey = skey + CAP;        // bucket order
   uint32_t* cnt = tkey + CAP;         // bucket counters
   uint32_t* rdel = cnt + CAP;         // per row: output offset from base - packed start
-  uint32_t* bits = rdel + 2 * SS_ROWS;  // row starts
-  uint32_t* wpre = bits + SS_WORDS;   // row starts in earlier words
-  uint16_t* slot = reinterpret_cast<uint16_t*>(wpre + SS_WORDS);  // bucket of packed entry
+  uint32_t* bits = rdel + 2 * ROWS;   // row starts
+  uint32_t* wpre = bits + WORDS;      // row starts in earlier words
+  uint16_t* slot = reinterpret_cast<uint16_t*>(wpre + WORDS);  // bucket of packed entry
   uint16_t* tidx = slot + CAP;        // packed entry of each bucket-order position
   uint16_t* rowk = tidx + CAP;        // row of each packed entry
-  float* rsc = reinterpret_cast<float*>(rdel + SS_ROWS);  // per row: bucket scale
+  float* rsc = reinterpret_cast<float*>(rdel + ROWS);  // per row: bucket scale
   uint16_t* rps = rowk + CAP;         // per row: packed start
-  uint16_t* rnm = rps + SS_ROWS;      // per row: last bucket
+  uint16_t* rnm = rps + ROWS;         // per row: last bucket
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ uint32_t s_min, s_max;
   const int t = threadIdx.x;
@@ -277,7 +477,7 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
   const long long nitems = ntiles + nf;
 
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-    if (t < SS_WORDS) bits[t] = 0;
+    for (int w = t; w < WORDS; w += B) bits[w] = 0;
     if (t == 0) {
       s_min = 0xFFFFFFFFu;
       s_max = 0u;
@@ -290,15 +490,15 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
       const long long r0 = tile_first[item];
       long long r1 = tile_first[item + 1];
       base = vp[r0];
-      if (r1 - r0 > SS_ROWS) {  // cannot happen: see RowsPartition
+      if (r1 - r0 > ROWS) {  // cannot happen: see RowsPartition
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -17);
         r1 = r0;
       }
       if (t < r1 - r0) {
         o0 = vp[r0 + t];
         const long long L = vp[r0 + t + 1] - o0;
-        if (L > 0 && L <= SS_CP) {
-          if (o0 - base > 0xFFFFFFFFll - SS_CAP) dev_fail(st, SP_ERR_OVERFLOW, r0 + t);
+        if (L > 0 && L <= Cfg::CP) {
+          if (o0 - base > 0xFFFFFFFFll - CAP) dev_fail(st, SP_ERR_OVERFLOW, r0 + t);
           else myL = uint32_t(L);
         }
       }
@@ -316,7 +516,7 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
     // packed start (high half) and rank among the item's rows (low half)
     uint32_t tot;
     const uint32_t pre = block_excl_sum<B>(myL ? ((myL << 16) | 1u) : 0u, tmp32, &tot);
-    const int E = int(tot >> 16);  // <= 2 * SS_CP by the partition
+    const int E = int(tot >> 16);  // <= 2 * Cfg::CP by the partition
     if (E > CAP) {                 // cannot happen: see RowsPartition
       if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -19);
       __syncthreads();
@@ -334,16 +534,17 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
     for (int x = t; x < E; x += B) cnt[x] = 0;
     __syncthreads();
     if (t < 32) {
-      uint32_t c[4], s = 0;
+      constexpr int WL = WORDS / 32;  // words per lane
+      uint32_t c[WL], s = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        c[j] = __popc(bits[t * 4 + j]);
+      for (int j = 0; j < WL; ++j) {
+        c[j] = __popc(bits[t * WL + j]);
         s += c[j];
       }
       uint32_t run = warp_incl_sum(s) - s;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        wpre[t * 4 + j] = run;
+      for (int j = 0; j < WL; ++j) {
+        wpre[t * WL + j] = run;
         run += c[j];
       }
     }
@@ -449,7 +650,7 @@ __global__ void __launch_bounds__(SS_BLOCK, 2)
       }
     }
     __syncthreads();
-    ss_excl_sum(cnt, E, tmp32);
+    ss_excl_sum<B>(cnt, E, tmp32);
     // scatter to bucket order; afterwards cnt[s] = end of bucket s, cnt[s-1] its start
     for (int x = t; x < E; x += B) {
       const uint32_t p = atomicAdd(&cnt[slot[x]], 1u);
@@ -505,18 +706,21 @@ struct RowsWs {
 constexpr int kRowsSlots = 12;
 
 inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
-  w->ntiles_cap = (nnz + SS_ROW_W * nrows) / SS_CP + 1;
+  w->ntiles_cap = (nnz + SS_ROW_W * nrows) / SS_TILE_MAX + 1;
   w->nchunks = (nnz + GC_CH - 1) / GC_CH;
-  w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / LONG_CAP + 16) + nnz / SS_CP + 1;
-  w->huge_cap = nnz / SS_CAP + 1;
-  w->nxt_cap = nnz / LONG_CAP + 1;
+  w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / SS_RUN_MAX + 16) + nnz / SS_TILE_MAX + 1;
+  w->huge_cap = nnz / SS_RUN_MAX + 1;
+  w->nxt_cap = nnz / SS_RUN_MAX + 1;
   w->hv_cap = nnz / (SS_HEAVY + 1) + 1;  // heavy buckets are disjoint runs of > SS_HEAVY
 }
 
-inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbytes, size_t* off) {
+// Workspace of run_rows; `sort` = false reserves only what the gather needs.
+inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbytes, size_t* off,
+                         bool sort = true) {
   RowsWs w;
   rows_caps(nrows, nnz, &w);
-  const bool need_temp = nnz > SS_CAP;
+  if (!sort) w.fin_cap = w.huge_cap = w.nxt_cap = w.hv_cap = 0;
+  const bool need_temp = sort && nnz > SS_RUN_MAX;
   off[0] = cv.reserve(size_t(w.ntiles_cap + 1) * 8);
   off[1] = cv.reserve(size_t(w.nchunks + 1) * 8);
   off[2] = cv.reserve(8);
@@ -531,9 +735,11 @@ inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbyt
   off[11] = cv.reserve(size_t(w.hv_cap) * sizeof(FinalEntry));
 }
 
-inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const size_t* off) {
+inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const size_t* off,
+                        bool sort = true) {
   RowsWs w;
   rows_caps(nrows, nnz, &w);
+  if (!sort) w.fin_cap = w.huge_cap = w.nxt_cap = w.hv_cap = 0;
   w.tile_first = cv.at<long long>(off[0]);
   w.chunk_first = cv.at<long long>(off[1]);
   w.ntiles = cv.at<long long>(off[2]);
@@ -560,20 +766,6 @@ struct NoGather {
   __device__ VT val(long long) const { return VT(0); }
 };
 
-// A loader for k_huge that only ever processes buffered runs (no source rows).
-template <class CIt, class VTt>
-struct RunsOnly {
-  using CI = CIt;
-  using VT = VTt;
-  static constexpr bool kAllKept = true;
-  static constexpr bool kLoadVals = true;
-  __device__ RowSrc row(long long) const { return RowSrc{0, 0, 0, 0}; }
-  __device__ const CI* cols(int) const { return nullptr; }
-  __device__ const VT* vals(int) const { return nullptr; }
-  __device__ bool test(int, long long) const { return false; }
-  __device__ bool map(int, long long, uint32_t&) const { return false; }
-};
-
 // Partition the output rows (row pointer vp, nnz entries), gather them with `gs`
 // (when given) and sort every row in place (when `sort`).
 template <class CI, class VT, class Gs>
@@ -588,7 +780,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   SP_TRY(launch_scan(ctx, s, RowsWeight{vp},
                      RowsPartition{vp, nrows, w.ntiles_cap, w.tile_first, w.ntiles, w.nchunks, w.chunk_first,
                                    w.fin, fin_n, w.fin_cap, w.huge, huge_n, w.huge_cap, key_bits,
-                                   ctx->dstatus},
+                                   sort ? 1 : 0, ctx->dstatus},
                      nrows, w.scan_ws, SP_PHASE_PARTITION));
   if (gs) {
     if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
@@ -601,51 +793,57 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   }
   if (!sort) return SP_OK;
   VT* tval = static_cast<VT*>(w.tval);
-  if (nnz > SS_CAP) {
-    using RL = RunsOnly<CI, VT>;
-    constexpr size_t hsm = huge_smem_bytes();
-    static bool once_h = (set_smem(k_huge<RL>, hsm), true);
+  if (nnz > SS_RUN_MAX) {
+    constexpr size_t hsm = split_smem_bytes();
+    static bool once_h = (set_smem(k_split<CI, VT>, hsm), true);
     (void)once_h;
     {
       SP_PHASE(SP_PHASE_HUGE);
-      k_huge<RL><<<nsm, HUGE_BLOCK, hsm, s>>>(RL{}, vp, nullptr, nullptr, w.huge, huge_n, w.huge_cap,
-                                              w.counters + 3, key_bits, w.tkey, tval, out_col, out_val,
-                                              w.fin, fin_n, w.fin_cap, w.nxt, nxt_n, w.nxt_cap,
-                                              ctx->dstatus);
+      k_split<CI, VT><<<nsm, SPLIT_BLOCK, hsm, s>>>(w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval,
+                                                    out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt, nxt_n,
+                                                    w.nxt_cap, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
-    // a second round only when a bucket of the first (2^(key_bits - HUGE_NB_LOG) keys)
-    // can hold more than LONG_CAP entries
-    if (key_bits - HUGE_NB_LOG > 12) {
-      static_assert(LONG_CAP == 1 << 12, "second-round test assumes LONG_CAP = 2^12");
+    // a second round only when a bucket of the first (2^(key_bits - SPLIT_NB_LOG) keys)
+    // can hold more than SS_RUN_MAX entries
+    if ((1ll << (key_bits > SPLIT_NB_LOG ? key_bits - SPLIT_NB_LOG : 0)) > SS_RUN_MAX) {
       {
         SP_PHASE(SP_PHASE_HUGE);
-        k_huge<RL><<<nsm, HUGE_BLOCK, hsm, s>>>(RL{}, vp, nullptr, nullptr, w.nxt, nxt_n, w.nxt_cap,
-                                                w.counters + 4, key_bits, w.tkey, tval, out_col, out_val,
-                                                w.fin, fin_n, w.fin_cap, w.nxt, w.counters + 5, 0, ctx->dstatus);
+        k_split<CI, VT><<<nsm, SPLIT_BLOCK, hsm, s>>>(w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval,
+                                                      out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt,
+                                                      w.counters + 5, 0, ctx->dstatus);
       }
       SP_CUDA(cudaGetLastError());
     }
   }
-  constexpr size_t ssm = ss_smem_bytes<VT>();
-  static bool once_s = (set_smem(k_seg_sort<CI, VT>, ssm), true);
+  // tiles (4 CTAs per SM), then the runs, then the heavy buckets queued by either
+  const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
+  const unsigned* no_runs = w.counters + 8;
+  constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), rsm = ss_smem_bytes<SsRun, VT>();
+  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
   (void)once_s;
   {
     SP_PHASE(SP_PHASE_TILE);
-    k_seg_sort<CI, VT><<<2 * nsm, SS_BLOCK, ssm, s>>>(vp, w.tile_first, w.ntiles, w.fin, fin_n, w.fin_cap,
-                                                      w.tkey, tval, out_col, out_val, w.hv[0], w.counters + 6,
-                                                      w.hv_cap, key_bits, ctx->dstatus);
+    k_seg_sort<SsTile, CI, VT><<<4 * nsm, SsTile::B, tsm, s>>>(
+        vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0], w.counters + 6,
+        w.hv_cap, key_bits, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  {
+    SP_PHASE(SP_PHASE_LONG);
+    k_seg_sort<SsRun, CI, VT><<<2 * nsm, SsRun::B, rsm, s>>>(
+        vp, w.tile_first, no_tiles, w.fin, fin_n, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
+        w.counters + 6, w.hv_cap, key_bits, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   // heavy buckets: runs over their own key range; the last pass ranks every bucket
-  const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   for (int pass = 0; pass < SS_PASSES; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     const bool last = pass == SS_PASSES - 1;
     SP_CUDA(cudaMemsetAsync(w.counters + 6 + b, 0, 4, s));
     {
-      SP_PHASE(SP_PHASE_TILE);
-      k_seg_sort<CI, VT><<<2 * nsm, SS_BLOCK, ssm, s>>>(
+      SP_PHASE(SP_PHASE_LONG);
+      k_seg_sort<SsRun, CI, VT><<<2 * nsm, SsRun::B, rsm, s>>>(
           vp, w.tile_first, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
           last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, ctx->dstatus);
     }

@@ -11,7 +11,7 @@
 #include <mutex>
 
 #include "dispatch.h"
-#include "pipeline.cuh"
+#include "scan.cuh"
 
 namespace sp {
 
