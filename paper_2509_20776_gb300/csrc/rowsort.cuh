@@ -125,6 +125,67 @@ struct RowsPartition {
   }
 };
 
+// ---- conflict-free block scans over shared arrays ------------------------------------------
+// Each warp owns a contiguous segment of n / (B / 32) entries and walks it 32 entries at a
+// time (lane l reads word base + l: no bank conflicts), carrying its running value; the
+// warps' segment totals are combined by one warp.  n must be a multiple of B.
+template <int B>
+__device__ uint32_t smem_excl_sum_w(uint32_t* a, int n, uint32_t* tmp) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, seg = n / NW;
+  uint32_t* s = a + w * seg;
+  uint32_t tot = 0;
+  for (int x = lane; x < seg; x += 32) tot += s[x];
+  tot = warp_sum(tot);
+  if (lane == 0) tmp[w] = tot;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = lane < NW ? tmp[lane] : 0u;
+    const uint32_t inc = warp_incl_sum(v);
+    if (lane < NW) tmp[lane] = inc - v;
+    if (lane == NW - 1) tmp[NW] = inc;
+  }
+  __syncthreads();
+  uint32_t carry = tmp[w];
+  for (int x = lane; x < seg; x += 32) {
+    const uint32_t v = s[x];
+    const uint32_t inc = warp_incl_sum(v);
+    s[x] = carry + inc - v;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  const uint32_t total = tmp[NW];
+  __syncthreads();
+  return total;
+}
+
+template <int B>
+__device__ void smem_incl_max_w(uint32_t* a, int n, uint32_t* tmp) {
+  constexpr int NW = B / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, seg = n / NW;
+  uint32_t* s = a + w * seg;
+  uint32_t mx = 0;
+  for (int x = lane; x < seg; x += 32) mx = s[x] > mx ? s[x] : mx;
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) tmp[w] = mx;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = lane < NW ? tmp[lane] : 0u;
+    uint32_t inc = warp_incl_max(v);
+    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) ex = 0u;
+    if (lane < NW) tmp[lane] = ex;
+  }
+  __syncthreads();
+  uint32_t carry = tmp[w];
+  for (int x = lane; x < seg; x += 32) {
+    const uint32_t inc = warp_incl_max(s[x]);
+    const uint32_t r = inc > carry ? inc : carry;
+    s[x] = r;
+    carry = __shfl_sync(0xffffffffu, r, 31);
+  }
+  __syncthreads();
+}
+
 // ---- phase 1: gather ----------------------------------------------------------------
 // Each CTA owns GC_CH consecutive output positions, starting at row chunk_first[k].
 // Gs: using CI, VT;
@@ -141,7 +202,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
   using CI = typename Gs::CI;
   using VT = typename Gs::VT;
   constexpr int B = GC_BLOCK, ITEMS = GC_ITEMS;
-  __shared__ uint16_t owner[GC_CH];
+  __shared__ uint32_t owner[GC_CH];
   __shared__ long long r_off[B];
   __shared__ long long r_o0[B];
   __shared__ long long r_o1[B];
@@ -167,9 +228,9 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) owner[t + j * B] = 0;
     __syncthreads();
-    if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint16_t(t + 1);
+    if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint32_t(t + 1);
     __syncthreads();
-    smem_incl_max16<B, ITEMS>(owner, GC_CH, tmp32);
+    smem_incl_max_w<B>(owner, GC_CH, tmp32);
     // all loads, then all stores (the compiler cannot move stores above later loads)
     constexpr int H = 8;
 #pragma unroll
@@ -182,7 +243,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
       for (int u = 0; u < H; ++u) {
         const int x = t + (h + u) * B;
         const long long g = c0 + x;
-        const int ow = owner[x];
+        const int ow = int(owner[x]);
         ok[u] = false;
         pos[u] = 0;
         if (g < c1 && ow > 0) {
@@ -231,7 +292,7 @@ constexpr int SPLIT_NB_LOG = 14;
 constexpr int SPLIT_NB = 1 << SPLIT_NB_LOG;
 constexpr int SPLIT_U = 4;                 // entries per thread per batch
 constexpr int GROUP_CAP = SS_RUN_MAX / 2;  // small buckets grouped up to this start window
-constexpr size_t split_smem_bytes() { return size_t(SPLIT_NB) * 4 * 2; }
+constexpr size_t split_smem_bytes() { return size_t(SPLIT_NB) * 4 * 3; }
 
 template <class CI, class VT>
 __global__ void __launch_bounds__(SPLIT_BLOCK, 1)
@@ -239,10 +300,11 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 1)
             unsigned* ticket, uint32_t* __restrict__ tkey, VT* __restrict__ tval, CI* __restrict__ out_col,
             VT* __restrict__ out_val, FinalEntry* __restrict__ fin, unsigned* fin_n, long long fin_cap,
             HugeEntry* __restrict__ nxt, unsigned* nxt_n, long long nxt_cap, DevStatus* st) {
-  constexpr int B = SPLIT_BLOCK, ITEMS = SPLIT_NB / B, U = SPLIT_U;
+  constexpr int B = SPLIT_BLOCK, U = SPLIT_U;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* aux = hist + SPLIT_NB;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);  // bucket sizes, then starts, then cursors
+  uint32_t* prv = hist + SPLIT_NB;   // 1 + last non-empty bucket at or before x (0: none)
+  uint32_t* nxb = prv + SPLIT_NB;    // reversed: L - start of the first group boundary >= x
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ unsigned s_item;
   const int t = threadIdx.x;
@@ -283,74 +345,63 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 1)
       }
     }
     __syncthreads();
-    const uint32_t total = smem_excl_sum<B, ITEMS>(hist, SPLIT_NB, tmp32);
+    const uint32_t total = smem_excl_sum_w<B>(hist, SPLIT_NB, tmp32);
     if (total != uint32_t(L)) {
       if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -5);
       continue;
     }
-    // previous non-empty bucket (inclusive max-scan of b+1 over non-empty buckets)
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t * ITEMS + j;
-      const uint32_t c = (x + 1 < nb ? hist[x + 1] : uint32_t(L)) - hist[x];
-      aux[x] = (x < nb && c > 0) ? uint32_t(x + 1) : 0u;
-    }
+    // bucket x holds [hist[x], end(x)); bucket order is key order
+    auto bend = [&](int x) { return x + 1 < nb ? hist[x + 1] : uint32_t(L); };
+    // previous non-empty bucket (inclusive max-scan of x+1 over non-empty buckets)
+    for (int x = t; x < SPLIT_NB; x += B) prv[x] = (x < nb && bend(x) > hist[x]) ? uint32_t(x + 1) : 0u;
     __syncthreads();
-    smem_incl_max<B, ITEMS>(aux, SPLIT_NB, tmp32);
-    // heads of groups: small non-empty buckets that start a new group of consecutive
-    // small buckets (group = buckets whose start lies in one GROUP_CAP window, cut at
-    // every big bucket); big buckets stand alone.
-    bool head[ITEMS], big[ITEMS];
-    uint32_t cc[ITEMS], sb[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t * ITEMS + j;
-      sb[j] = hist[x];
-      cc[j] = x < nb ? (x + 1 < nb ? hist[x + 1] : uint32_t(L)) - sb[j] : 0u;
-      big[j] = cc[j] > uint32_t(GROUP_CAP);
-      head[j] = false;
-      if (cc[j] > 0 && !big[j]) {
-        const uint32_t pv = x > 0 ? aux[x - 1] : 0u;  // previous non-empty bucket + 1
+    smem_incl_max_w<B>(prv, SPLIT_NB, tmp32);
+    // Groups: a bucket of more than GROUP_CAP entries ("big") stands alone; a small
+    // non-empty bucket starts a new group ("head") unless the previous non-empty
+    // bucket is small and starts in the same GROUP_CAP window.
+    auto kind = [&](int x, bool& big, bool& head) {
+      const uint32_t sb = hist[x], cc = x < nb ? bend(x) - sb : 0u;
+      big = cc > uint32_t(GROUP_CAP);
+      head = false;
+      if (cc > 0 && !big) {
+        const uint32_t pv = x > 0 ? prv[x - 1] : 0u;
         if (pv == 0) {
-          head[j] = true;
+          head = true;
         } else {
           const int y = int(pv) - 1;
-          const uint32_t cy = (y + 1 < nb ? hist[y + 1] : uint32_t(L)) - hist[y];
-          head[j] = cy > uint32_t(GROUP_CAP) || (hist[y] / GROUP_CAP) != (sb[j] / GROUP_CAP);
+          head = bend(y) - hist[y] > uint32_t(GROUP_CAP) || (hist[y] / GROUP_CAP) != (sb / GROUP_CAP);
         }
       }
+    };
+    // next group boundary after each bucket: suffix min of boundary starts, as a prefix
+    // max over the reversed array of (L - start)
+    for (int x = t; x < SPLIT_NB; x += B) {
+      bool big, head;
+      kind(x, big, head);
+      nxb[SPLIT_NB - 1 - x] = (big || head) ? uint32_t(L) - hist[x] : 0u;
     }
     __syncthreads();
-    // next boundary start after each bucket: suffix min over boundary starts, computed
-    // as a prefix max over the reversed array of (L - start)
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t * ITEMS + j;
-      const bool bnd = head[j] || big[j];
-      aux[SPLIT_NB - 1 - x] = bnd ? uint32_t(L) - sb[j] : 0u;
-    }
-    __syncthreads();
-    smem_incl_max<B, ITEMS>(aux, SPLIT_NB, tmp32);
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const int x = t * ITEMS + j;
-      if (x >= nb || cc[j] == 0) continue;
-      if (big[j]) {
-        if (cc[j] <= uint32_t(SS_RUN_MAX)) {
+    smem_incl_max_w<B>(nxb, SPLIT_NB, tmp32);
+    for (int x = t; x < nb; x += B) {
+      bool big, head;
+      kind(x, big, head);
+      const uint32_t sb = hist[x], cc = bend(x) - sb;
+      if (big) {
+        if (cc <= uint32_t(SS_RUN_MAX)) {
           const unsigned q = atomicAdd(fin_n, 1u);
-          if (q < fin_cap) fin[q] = FinalEntry{g0 + sb[j], cc[j], dbuf, 0};
+          if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, cc, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -6);
         } else {
           const unsigned q = atomicAdd(nxt_n, 1u);
-          if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb[j], cc[j], lo + (uint32_t(x) << sh), sh, dbuf, 0};
+          if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb, cc, lo + (uint32_t(x) << sh), sh, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -7);
         }
-      } else if (head[j]) {
+      } else if (head) {
         // reversed index of x+1 holds max over buckets >= x+1 of (L - start) -> min start
-        const uint32_t nx = (x + 1 < SPLIT_NB) ? aux[SPLIT_NB - 1 - (x + 1)] : 0u;
+        const uint32_t nx = (x + 1 < SPLIT_NB) ? nxb[SPLIT_NB - 1 - (x + 1)] : 0u;
         const uint32_t end = nx ? uint32_t(L) - nx : uint32_t(L);
         const unsigned q = atomicAdd(fin_n, 1u);
-        if (q < fin_cap) fin[q] = FinalEntry{g0 + sb[j], (long long)(end - sb[j]), dbuf, 0};
+        if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, (long long)(end - sb), dbuf, 0};
         else dev_fail(st, SP_ERR_INTERNAL, -6);
       }
     }
@@ -418,7 +469,8 @@ __host__ __device__ constexpr size_t ss_smem_bytes() {
 }
 
 // In-place exclusive sum of a[0, n); thread t owns the ceil(n / B) consecutive entries
-// starting at t * ceil(n / B).
+// starting at t * ceil(n / B) (few per thread for the item sizes here, so the blocked
+// layout's bank conflicts cost less than a second pass would).
 template <int B>
 __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
   const int t = threadIdx.x;
