@@ -187,7 +187,7 @@ __device__ void smem_incl_max_w(uint32_t* a, int n, uint32_t* tmp) {
 }
 
 // ---- phase 1: gather ----------------------------------------------------------------
-// Each CTA owns GC_CH consecutive output positions, starting at row chunk_first[k].
+// Chunk k is GC_CH consecutive output positions, starting inside row chunk_first[k].
 // Gs: using CI, VT;
 //     __device__ long long src(long long r) const;     // source start of output row r
 //     __device__ typename Gs::CI col(long long pos) const;  // source column
@@ -197,6 +197,7 @@ template <class Gs>
 __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
                                                             long long nrows, long long total,
                                                             const long long* __restrict__ chunk_first,
+                                                            long long nchunks,
                                                             typename Gs::CI* __restrict__ out_col,
                                                             typename Gs::VT* __restrict__ out_val) {
   using CI = typename Gs::CI;
@@ -207,35 +208,54 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
   __shared__ long long r_o0[B];
   __shared__ long long r_o1[B];
   __shared__ uint32_t tmp32[B / 32 + 1];
+  __shared__ long long s_last;  // output end of the batch's last row
   const int t = threadIdx.x;
-  const long long c0 = blockIdx.x * (long long)GC_CH;
-  if (c0 >= total) return;
-  const long long c1 = c0 + GC_CH < total ? c0 + GC_CH : total;
-  for (long long rb = chunk_first[blockIdx.x];; rb += B) {
-    const long long r = rb + t;
-    long long o0 = total, o1 = total, so = 0;
-    if (r < nrows) {  // the source start is loaded alongside, not after, the row pointer
-      o0 = vp[r];
-      o1 = vp[r + 1];
-      so = gs.src(r);
+  // row r's output range [o0, o1) and source start
+  auto setup = [&](long long r, long long& a, long long& b, long long& s) {
+    a = total;
+    b = total;
+    s = 0;
+    if (r < nrows) {
+      a = vp[r];
+      b = vp[r + 1];
+      s = gs.src(r);
     }
-    const bool active = r < nrows && o1 > o0 && o1 > c0 && o0 < c1;
+  };
+  // persistent: chunks blockIdx.x, + gridDim.x, ...; a batch is B consecutive rows.  The
+  // next batch's row setup is loaded while this batch's entries are in flight.
+  long long c = blockIdx.x;
+  if (c >= nchunks) return;
+  long long rb = chunk_first[c];
+  long long o0, o1, so;
+  setup(rb + t, o0, o1, so);
+  for (;;) {
+    const long long c0 = c * (long long)GC_CH, c1 = c0 + GC_CH < total ? c0 + GC_CH : total;
+    const long long cn = c + gridDim.x;
+    const long long rb_next_chunk = cn < nchunks ? chunk_first[cn] : 0;
+    const bool active = rb + t < nrows && o1 > o0 && o1 > c0 && o0 < c1;
     if (active) {
       r_off[t] = so;
       r_o0[t] = o0;
       r_o1[t] = o1;
     }
+    if (t == B - 1) s_last = o1;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) owner[t + j * B] = 0;
     __syncthreads();
     if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint32_t(t + 1);
     __syncthreads();
     smem_incl_max_w<B>(owner, GC_CH, tmp32);
+    // the chunk ends with this batch once its last row reaches the end of the chunk
+    const bool last_batch = rb + B - 1 >= nrows - 1 || s_last >= c1;
+    const bool more = !last_batch || cn < nchunks;
+    const long long rb_next = last_batch ? rb_next_chunk : rb + B;
+    long long n0 = 0, n1 = 0, ns = 0;
+    if (more) setup(rb_next + t, n0, n1, ns);
     // all loads, then all stores (the compiler cannot move stores above later loads)
     constexpr int H = 8;
 #pragma unroll
     for (int h = 0; h < ITEMS; h += H) {
-      CI c[H];
+      CI cv[H];
       VT v[H];
       long long pos[H];
       bool ok[H];
@@ -257,25 +277,28 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
         }
       }
 #pragma unroll
-      for (int u = 0; u < H; ++u) c[u] = ok[u] ? gs.col(pos[u]) : CI(0);
+      for (int u = 0; u < H; ++u) cv[u] = ok[u] ? gs.col(pos[u]) : CI(0);
 #pragma unroll
       for (int u = 0; u < H; ++u)
         if (ok[u]) v[u] = gs.val(pos[u]);
 #pragma unroll
       for (int u = 0; u < H; ++u)
-        if (ok[u]) c[u] = gs.map(c[u]);
+        if (ok[u]) cv[u] = gs.map(cv[u]);
 #pragma unroll
       for (int u = 0; u < H; ++u) {
         if (!ok[u]) continue;
         const long long g = c0 + t + (h + u) * B;
-        st_stream(out_col + g, c[u]);
+        st_stream(out_col + g, cv[u]);
         st_stream(out_val + g, v[u]);
       }
     }
     __syncthreads();
-    // stop once this batch's last row reaches the end of the chunk
-    const long long rl = rb + B - 1;
-    if (rl >= nrows - 1 || vp[rl + 1] >= c1) break;
+    if (!more) break;
+    if (last_batch) c = cn;
+    rb = rb_next;
+    o0 = n0;
+    o1 = n1;
+    so = ns;
   }
 }
 
@@ -838,8 +861,9 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
     {
       SP_PHASE(SP_PHASE_GATHER);
-      k_gather_chunks<Gs><<<unsigned(w.nchunks), GC_BLOCK, 0, s>>>(*gs, vp, nrows, nnz, w.chunk_first,
-                                                                   out_col, out_val);
+      const long long g = w.nchunks < 2ll * nsm ? w.nchunks : 2ll * nsm;  // persistent, 2 per SM
+      k_gather_chunks<Gs><<<unsigned(g), GC_BLOCK, 0, s>>>(*gs, vp, nrows, nnz, w.chunk_first, w.nchunks,
+                                                           out_col, out_val);
     }
     SP_CUDA(cudaGetLastError());
   }
