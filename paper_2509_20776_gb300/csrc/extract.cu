@@ -46,6 +46,57 @@ struct ExtractLoader {
   }
 };
 
+// Consecutive J = [j0, j1): the kept entries of a (sorted) row form one segment, found by
+// binary search, and keep their order (the paper's binary-search idea of Alg. 5 applied
+// to a whole range).  The row length functor of the scan records the segment start.
+template <class CI>
+__device__ __forceinline__ long long lower_bound_col(const CI* col, long long lo, long long hi, long long v) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if ((long long)col[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class RP, class CI, class IX>
+struct ExtractRangeLen {
+  const RP* rowptr;
+  const CI* col;
+  const IX* I;
+  long long m, nnz, j0, j1;
+  long long* sstart;
+  DevStatus* st;
+  __device__ long long operator()(long long i) const {
+    const long long r = (long long)I[i];
+    long long s = 0, e = 0;
+    if (r < 0 || r >= m) {
+      dev_fail(st, SP_ERR_INDEX_RANGE, i);
+    } else {
+      s = (long long)rowptr[r];
+      e = (long long)rowptr[r + 1];
+      if (s < 0 || e < s || e > nnz) s = e = 0;
+    }
+    const long long lo = lower_bound_col(col, s, e, j0), hi = lower_bound_col(col, lo, e, j1);
+    sstart[i] = lo;
+    return hi - lo;
+  }
+};
+
+template <class CIt, class VTt>
+struct ExtractRangeGs {
+  using CI = CIt;
+  using VT = VTt;
+  const CI* c_;
+  const VT* v_;
+  const long long* sstart;
+  long long j0;
+  __device__ long long src(long long i) const { return sstart[i]; }
+  __device__ CI col(long long pos) const { return ld_stream(c_ + pos); }
+  __device__ VT val(long long pos) const { return ld_stream(v_ + pos); }
+  __device__ CI map(CI c) const { return CI((long long)c - j0); }
+};
+
 // copy an int64 row pointer into a typed output row pointer
 sp_status store_rowptr(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n1,
                        sp_itype t, void* out) {
@@ -101,8 +152,11 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
   const size_t o_cn = cv.reserve(64);
   const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
+  const size_t o_ss = cv.reserve(size_t(nI) * 8);
+  const size_t o_fl = cv.reserve(16);
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
+  pl->sstart = cv.at<long long>(o_ss);
   IX* jinv = cv.at<IX>(o_jinv);
   uint32_t* jbits = cv.at<uint32_t>(o_jb);
   pl->jmap = jinv;
@@ -111,6 +165,36 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   pl->cl_rows = cv.at<long long>(o_cl);
   pl->counters = cv.at<unsigned>(o_cn);
   const int nsm = ctx->num_sms;
+  // the shape of J picks the path: consecutive J needs neither maps nor membership tests
+  int* flags = cv.at<int>(o_fl);
+  SP_CUDA(cudaMemsetAsync(flags, 0, 16, s));
+  if (nJ > 1) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_index_shape<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, flags);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 1, flags, 8, cudaMemcpyDeviceToHost, s));
+  if (nJ > 0) SP_CUDA(cudaMemcpyAsync(pl->h_tail + 2, J, sizeof(IX), cudaMemcpyDeviceToHost, s));
+  SP_TRY(ctx_collect(ctx, s));
+  int fl[2];
+  std::memcpy(fl, pl->h_tail + 1, 8);
+  pl->j_shape = nJ == 0 ? 0 : (fl[1] == 0 ? 2 : (fl[0] == 0 ? 1 : 0));
+  if (pl->j_shape == 2) {
+    IX first;
+    std::memcpy(&first, pl->h_tail + 2, sizeof(IX));
+    pl->j0 = (long long)first;
+    if (pl->j0 < 0 || pl->j0 + nJ > n) return SP_ERR_INDEX_RANGE;
+    ExtractRangeLen<RP, CI, IX> len{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), I,
+                                    m, nnz, pl->j0, pl->j0 + nJ, pl->sstart, ctx->dstatus};
+    SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI,
+                       cv.at<char>(o_scan)));
+    SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+    SP_TRY(ctx_collect(ctx, s));
+    pl->nnz_out = pl->h_tail[0];
+    return SP_OK;
+  }
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
   SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
   SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
@@ -163,9 +247,23 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   const long long nI = pl->nI, nnz_out = pl->nnz_out;
   SP_TRY(store_rowptr(ctx, s, pl->vp, nI + 1, B->rowptr_type, B->rowptr));
   if (nnz_out == 0) return SP_OK;
+  CI* oc = static_cast<CI*>(B->colidx);
+  VT* ov = static_cast<VT*>(B->values);
   Carver cv;
   size_t ro[kRowsSlots];
-  rows_reserve(cv, nI, nnz_out, sizeof(VT), ro);
+  if (pl->j_shape == 2) {
+    // consecutive J: copy every row's kept segment, columns shifted by j0; already sorted
+    rows_reserve(cv, nI, nnz_out, sizeof(VT), ro, false);
+    char* base;
+    SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+    cv.bind(base);
+    const ExtractRangeGs<CI, VT> g{static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
+                                   pl->sstart, pl->j0};
+    const RowsWs w = rows_bind(cv, nI, nnz_out, ro, false);
+    return run_rows(ctx, s, pl->vp, nI, nnz_out, 0, w, &g, false, oc, ov);
+  }
+  const bool sorted = pl->j_shape == 1;  // ascending J: the fill keeps rows in order
+  rows_reserve(cv, nI, nnz_out, sizeof(VT), ro, !sorted);
   const size_t o_tk = cv.reserve(16);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
@@ -175,9 +273,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
                                    static_cast<const VT*>(A.values), static_cast<const IX*>(pl->I),
                                    static_cast<const IX*>(pl->jmap),
                                    static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz};
-  CI* oc = static_cast<CI*>(B->colidx);
-  VT* ov = static_cast<VT*>(B->values);
-  // fill: kept entries, relabelled through jinv, into their output rows
+  // fill: kept entries, relabelled through jinv, into their output rows in source order
   unsigned* ticket = cv.at<unsigned>(o_tk);
   SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
   const int nsm = ctx->num_sms;
@@ -192,6 +288,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
                                      ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
+  if (sorted) return SP_OK;
   // sort every row in place
   const RowsWs w = rows_bind(cv, nI, nnz_out, ro);
   const int kb = ceil_log2_u64(uint64_t(pl->nJ));

@@ -56,6 +56,18 @@ __global__ void k_range_check(const IX* __restrict__ idx, long long len, long lo
   }
 }
 
+// Shape of an index vector: flags[0] = 1 unless strictly ascending, flags[1] = 1 unless
+// consecutive (idx[k+1] = idx[k] + 1 for all k); the flags are zeroed before the launch.
+template <class IX>
+__global__ void k_index_shape(const IX* __restrict__ idx, long long len, int* flags) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k + 1 < len;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long a = (long long)idx[k], b = (long long)idx[k + 1];
+    if (b <= a) flags[0] = 1;
+    if (b != a + 1) flags[1] = 1;
+  }
+}
+
 constexpr long long J_KEY_LIMIT = 1ll << 32;  // new column ids must fit 32-bit sort keys
 
 template <int kDummy = 0>
@@ -201,10 +213,11 @@ __global__ void __launch_bounds__(1024) k_count_long(Ct ct, long long* __restric
 
 // ---- fill passes (Alg. 5 second pass) --------------------------------------------------
 // The kept entries of listed row i, relabelled, are written to [vp[i], vp[i+1]) of
-// (out_col, out_val) in no particular order (the row sort orders them): a warp ballot
-// over 32 entries gives each kept entry its slot.  Short rows as in k_count_warp;
-// source-long rows (cl_rows) one CTA each, the CTA's warps taking slots from a shared
-// cursor.  A slot past the row's end (counts that do not match the fill) is reported
+// (out_col, out_val) in source order (the row sort then orders them by new column): a warp ballot
+// over 32 entries gives each kept entry its slot.  Short rows as in k_count_warp (FILL_RB
+// rows per warp step); source-long rows (cl_rows) one CTA each.  Both keep the source
+// order within a row, so a monotone relabelling needs no sort afterwards.  A slot past
+// the row's end (counts that do not match the fill) is reported
 // and not written.
 template <class Ld>
 __device__ __forceinline__ void fill_put(const Ld&, typename Ld::CI* out_col, typename Ld::VT* out_val,
@@ -280,16 +293,18 @@ __global__ void __launch_bounds__(1024) k_fill_long(Ld ld, const long long* __re
                                                     const long long* __restrict__ vp, unsigned* ticket,
                                                     typename Ld::CI* __restrict__ out_col,
                                                     typename Ld::VT* __restrict__ out_val, DevStatus* st) {
+  constexpr int NW = 1024 / 32;
   __shared__ unsigned s_item;
-  __shared__ unsigned long long s_cur;
-  const int t = threadIdx.x, lane = t & 31;
+  __shared__ unsigned s_wc[NW], s_wx[NW], s_tot;
+  __shared__ long long s_base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const unsigned lt = (1u << lane) - 1u;
   unsigned count = *n_cl;
   if (count > cl_cap) count = unsigned(cl_cap);
   for (;;) {
     if (t == 0) {
       s_item = atomicAdd(ticket, 1u);
-      s_cur = 0;
+      s_base = 0;
     }
     __syncthreads();
     const unsigned item = s_item;
@@ -306,13 +321,23 @@ __global__ void __launch_bounds__(1024) k_fill_long(Ld ld, const long long* __re
         if (bt.valid[u]) bt.at(u, rs, e);
       }
       bt.run(ld);
+      // slots in source order: warp counts, scanned across the block, slice by slice
 #pragma unroll
       for (int u = 0; u < LOAD_U; ++u) {
         const unsigned m = __ballot_sync(0xffffffffu, bt.kept[u]);
-        unsigned long long b = 0;
-        if (lane == 0 && m) b = atomicAdd(&s_cur, (unsigned long long)__popc(m));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (bt.kept[u]) fill_put(ld, out_col, out_val, o + (long long)b + __popc(m & lt), oe, bt.key[u], bt.v[u], st);
+        if (lane == 0) s_wc[w] = __popc(m);
+        __syncthreads();
+        if (w == 0) {
+          const unsigned v = s_wc[lane];
+          const unsigned inc = warp_incl_sum(v);
+          s_wx[lane] = inc - v;
+          if (lane == NW - 1) s_tot = inc;
+        }
+        __syncthreads();
+        if (bt.kept[u])
+          fill_put(ld, out_col, out_val, o + s_base + s_wx[w] + __popc(m & lt), oe, bt.key[u], bt.v[u], st);
+        __syncthreads();
+        if (t == 0) s_base += s_tot;
       }
     }
     __syncthreads();

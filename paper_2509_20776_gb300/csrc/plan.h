@@ -24,6 +24,11 @@ struct sp_plan {
   long long* vp_out = nullptr; // assignment: row pointer of A'
   long long* rpB = nullptr;    // assignment: B's row pointer widened to int64
   long long* cl_rows = nullptr;
+  // extraction: shape of J (0 general, 1 ascending, 2 consecutive), its first index, and
+  // for consecutive J the start of every selected row's kept segment
+  int j_shape = 0;
+  long long j0 = 0;
+  long long* sstart = nullptr;
   long long list_cap = 0;
   unsigned* counters = nullptr;  // [0] n_cl [3] count ticket
   long long* h_tail = nullptr;   // pinned host: totals read back by the count call

@@ -208,6 +208,37 @@ def test_extract_hubs(ctx):
     assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
 
 
+@pytest.mark.parametrize("shape", ["ascending", "consecutive", "consecutive_edge"])
+def test_extract_ordered_j(ctx, shape):
+    """Ascending J (rows come out of the fill in order, no sort) and consecutive J (binary
+    search of each row's kept segment, affine relabel); R-MAT hubs give source rows far
+    beyond one warp's share, and I repeats rows."""
+    A = special_values(rmat(15))
+    n = A.nrows
+    g = torch.Generator().manual_seed(31)
+    I = torch.randint(0, n, (n // 2,), generator=g).to(torch.int32)
+    if shape == "ascending":
+        J = torch.sort(synth.random_subset(n, n // 3, 9, 2)).values
+    elif shape == "consecutive":
+        J = torch.arange(n // 5, n // 5 + n // 3, dtype=torch.int32)
+    else:  # the range touches column 0 and the last column
+        J = torch.arange(0, n, dtype=torch.int32)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), f"extract {shape}")
+    kc = ctx.sp_kept_counts(to_dev(A), I.cuda(), J.cuda())
+    assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
+
+
+def test_extract_consecutive_j_out_of_range(ctx):
+    from paper_2509_20776_gb300 import SpError
+    A = to_dev(er(100, 4, seed=1))
+    J = torch.arange(90, 110, dtype=torch.int32).cuda()
+    I = torch.arange(0, 10, dtype=torch.int32).cuda()
+    with pytest.raises(SpError):
+        ctx.sp_extract(A, I, J)
+    ctx.sync()
+
+
 def test_extract_long_sources_short_outputs(ctx):
     """Hub rows whose sources exceed the tile limit but keep few entries sit between
     ordinary rows of a tile (the tile must leave their output positions alone)."""
