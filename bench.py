@@ -394,10 +394,30 @@ def bench_extract(ctx, args, dev, hbm, ws):
     ab = nnz_sel * 4 + nnz_out * 12 + (n // 2) * (4 + 16) + (n // 2) * 4 + n * 4 + (n // 2) * 4 + (n // 2) * 8
     frac = ab * steps / (ms * 1e-3) / 1e9 / hbm
     value = nnz_out * steps * ws / (ms * 1e-3)
-    return {"workload": "ER n=2^26, 32 draws/row; A(I,J), random distinct |I|=|J|=2^25",
-            "nnz_in": A.nnz, "nnz_out": nnz_out, "value": round(value, 1), "unit": UNIT,
-            "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
-            "alg_bytes_per_op": ab, "phase_ms_per_op": phases}
+    res = {"workload": "ER n=2^26, 32 draws/row; A(I,J), random distinct |I|=|J|=2^25",
+           "nnz_in": A.nnz, "nnz_out": nnz_out, "value": round(value, 1), "unit": UNIT,
+           "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
+           "alg_bytes_per_op": ab, "phase_ms_per_op": phases}
+    # the contiguous block A(0:n/4, n/4:n/2): each row's kept entries are one segment
+    Ic = torch.arange(0, n // 4, dtype=torch.int32, device=dev)
+    Jc = torch.arange(n // 4, n // 2, dtype=torch.int32, device=dev)
+    B = ctx.sp_extract(Ad, Ic, Jc)
+    nnz_c = B.nnz
+    del B
+
+    def step_c():
+        ctx.sp_extract(Ad, Ic, Jc, sync=False)
+
+    ms_c = max_over_ranks(time_steps(step_c, steps, 1, ws), ws)
+    # kept segment read (col + val) and written, I and the rowptr pairs, output row pointer
+    ab_c = nnz_c * 16 + (n // 4) * (4 + 16 + 8)
+    res["contiguous_block"] = {
+        "workload": "same A; A(0:n/4, n/4:n/2)", "nnz_out": nnz_c,
+        "value": round(nnz_c * steps * ws / (ms_c * 1e-3), 1), "unit": UNIT,
+        "ms_per_op": round(ms_c / steps, 3),
+        "op_roofline_frac": round(ab_c * steps / (ms_c * 1e-3) / 1e9 / hbm, 4),
+        "alg_bytes_per_op": ab_c}
+    return res
 
 
 def bench_assign(ctx, args, dev, hbm, ws):

@@ -69,7 +69,8 @@ typedef enum sp_assign_mode {
                               A'(I,J) == B exactly */
   SP_ASSIGN_SELECT2ND = 1, /* A (+) P B Q^T with select-second: A's entries inside the
                               region that B does not store survive; B wins ties */
-  SP_ASSIGN_PLUS = 2       /* A (+) P B Q^T with arithmetic add (one IEEE add) */
+  SP_ASSIGN_PLUS = 2       /* A (+) P B Q^T with arithmetic add: where both store an
+                              entry, one IEEE round-to-nearest add a + b in the value type */
 } sp_assign_mode;
 
 /* A CSR matrix descriptor (host struct, device arrays).

@@ -52,6 +52,7 @@ struct AssignLoader {
   }
   static constexpr bool kAllKept = false;
   static constexpr bool kLoadVals = true;
+  static constexpr bool kRowCtx = false;
   __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
   __device__ const CI* cols(int part) const { return part ? colB : colA; }
   __device__ const VT* vals(int part) const { return part ? valB : valA; }
@@ -67,6 +68,105 @@ struct AssignLoader {
     if (c < 0 || c >= nJ) return false;  // B's column b lands in column J[b]
     key = uint32_t(ld_map(J + c));
     return true;
+  }
+};
+
+// Rebuilt row I[i] under the union modes (A (+) P B Q^T, Algorithm 4 with a chosen add):
+//   SELECT2ND: A's entries survive unless B's row i stores the same column (B wins);
+//   PLUS: A's entries all survive, those that meet a B entry carry a + b (one IEEE add),
+//   and B's entries survive unless they met an A entry.
+// "Meets" is decided by a binary search in the other matrix's sorted row: for A's entry
+// at column c in J, B's row i is searched for jinv[c]; for B's entry at column b, A's
+// row I[i] is searched for J[b].  Keys stay unique, so the row sort applies unchanged.
+template <class RP, class CIt, class VTt, class IX>
+struct AssignMergeLoader {
+  using CI = CIt;
+  using VT = VTt;
+  const RP* rpA;
+  const CI* colA;
+  const VT* valA;
+  const long long* rpB;
+  const CI* colB;
+  const VT* valB;
+  const IX* I;
+  const IX* J;
+  const IX* jinv;  // column of A -> position in J, -1 elsewhere
+  const uint32_t* jbits;
+  long long m, n, nnzA, nJ, nnzB;
+  int plus;  // 0: SELECT2ND, 1: PLUS
+  static constexpr bool kAllKept = false;
+  static constexpr bool kLoadVals = true;
+  static constexpr bool kRowCtx = true;
+  __device__ RowSrc row(long long i) const {
+    const long long r = (long long)I[i];
+    RowSrc rs{0, 0, 0, 0};
+    if (r >= 0 && r < m) {
+      const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+      if (s >= 0 && e >= s && e <= nnzA) {
+        rs.s0 = s;
+        rs.n0 = e - s;
+      }
+    }
+    const long long s = rpB[i], e = rpB[i + 1];
+    if (s >= 0 && e >= s && e <= nnzB) {
+      rs.s1 = s;
+      rs.n1 = e - s;
+    }
+    return rs;
+  }
+  __device__ const CI* cols(int part) const { return part ? colB : colA; }
+  __device__ const VT* vals(int part) const { return part ? valB : valA; }
+  __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
+  // position of column b in B's row i, or -1
+  __device__ long long find_b(long long i, long long b) const {
+    const long long s = rpB[i], e = rpB[i + 1];
+    if (s < 0 || e < s || e > nnzB) return -1;
+    const long long q = lower_bound_col(colB, s, e, b);
+    return (q < e && (long long)colB[q] == b) ? q : -1;
+  }
+  // does A's row I[i] store column c
+  __device__ bool in_a(long long i, long long c) const {
+    const long long r = (long long)I[i];
+    if (r < 0 || r >= m) return false;
+    const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+    if (s < 0 || e < s || e > nnzA) return false;
+    const long long q = lower_bound_col(colA, s, e, c);
+    return q < e && (long long)colA[q] == c;
+  }
+  __device__ bool map_ctx(int part, long long c, uint32_t& key, long long i, long long& aux) const {
+    aux = -1;
+    if (part == 0) {
+      if (c < 0 || c >= n) return false;
+      key = uint32_t(c);
+      if (!in_j(c)) return true;
+      const long long q = find_b(i, (long long)ld_map(jinv + c));
+      if (plus) {
+        aux = q;  // the B entry added onto this one
+        return true;
+      }
+      return q < 0;
+    }
+    if (c < 0 || c >= nJ) return false;
+    const long long col = (long long)ld_map(J + c);
+    key = uint32_t(col);
+    return !plus || !in_a(i, col);
+  }
+  __device__ bool test_ctx(int part, long long c, long long i) const {
+    uint32_t key;
+    long long aux;
+    return map_ctx(part, c, key, i, aux);
+  }
+  // values are moved as 4- or 8-byte words; PLUS adds them as the IEEE floats they hold
+  // (round to nearest, no contraction)
+  __device__ VT value_ctx(int part, long long pos, long long aux) const {
+    const VT v = ld_stream(vals(part) + pos);
+    if (aux < 0) return v;
+    const VT w = ld_stream(valB + aux);
+    if constexpr (sizeof(VT) == 4) {
+      return VT(__float_as_uint(__fadd_rn(__uint_as_float(uint32_t(v)), __uint_as_float(uint32_t(w)))));
+    } else {
+      return VT(__double_as_longlong(__dadd_rn(__longlong_as_double((long long)v), __longlong_as_double((long long)w))));
+    }
   }
 };
 
@@ -139,6 +239,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_cn = cv.reserve(64);
   const size_t o_s1 = cv.reserve(scan_ws_bytes(nI));
   const size_t o_s2 = cv.reserve(scan_ws_bytes(m));
+  const bool merge = pl->mode != SP_ASSIGN_REPLACE;
+  const size_t o_ji = cv.reserve(merge ? size_t(n) * sizeof(IX) : 0);
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
   IX* rowmap = cv.at<IX>(o_rm);
@@ -170,23 +272,44 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     }
     SP_CUDA(cudaGetLastError());
   }
+  IX* jinv = merge ? cv.at<IX>(o_ji) : nullptr;
+  pl->jinv = jinv;
+  if (merge && nJ > 0) {
+    SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_inverse_map<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jinv, ctx->dstatus,
+                                                                    SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
   SP_TRY(widen_rowptr(ctx, s, B.rowptr, B.rowptr_type, nI + 1, pl->rpB));
   if (nI > 0) {
-    AssignLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
-                                          static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
-                                          static_cast<const CI*>(B.colidx), nullptr, I, J, jbits,
-                                          m, n, A.nnz, nJ, B.nnz};
     CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
-    {
-      SP_PHASE(SP_PHASE_COUNT);
-      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+    auto count = [&](const auto& ct) -> sp_status {
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        k_count_long<<<nsm, 1024, 0, s>>>(ct, pl->vp, cl, pl->counters + 3, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      return SP_OK;
+    };
+    if (merge) {
+      SP_TRY(count(AssignMergeLoader<RP, CI, uint32_t, IX>{
+          static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
+          static_cast<const CI*>(B.colidx), nullptr, I, J, jinv, jbits, m, n, A.nnz, nJ, B.nnz,
+          pl->mode == SP_ASSIGN_PLUS ? 1 : 0}));
+    } else {
+      SP_TRY(count(AssignLoader<RP, CI, uint32_t, IX>{static_cast<const RP*>(A.rowptr),
+                                                      static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
+                                                      static_cast<const CI*>(B.colidx), nullptr, I, J,
+                                                      jbits, m, n, A.nnz, nJ, B.nnz}));
     }
-    SP_CUDA(cudaGetLastError());
-    {
-      SP_PHASE(SP_PHASE_COUNT);
-      k_count_long<<<nsm, 1024, 0, s>>>(ct, pl->vp, cl, pl->counters + 3, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
   }
   SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
                      StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_s1)));
@@ -223,27 +346,39 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   const int nsm = ctx->num_sms;
   if (nt > 0) {
     // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
-    AssignLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
-                                    static_cast<const CI*>(A.colidx),
-                                    static_cast<const VT*>(A.values), pl->rpB,
-                                    static_cast<const CI*>(B.colidx),
-                                    static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
-                                    static_cast<const IX*>(pl->J),
-                                    static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols,
-                                    A.nnz, pl->nJ, B.nnz};
     unsigned* ticket = cv.at<unsigned>(o_tk);
     SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
-    {
-      SP_PHASE(SP_PHASE_GATHER);
-      k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
+    auto fill = [&](const auto& ld) -> sp_status {
+      {
+        SP_PHASE(SP_PHASE_GATHER);
+        k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      {
+        SP_PHASE(SP_PHASE_GATHER);
+        k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, tcol,
+                                         tval, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      return SP_OK;
+    };
+    if (pl->mode != SP_ASSIGN_REPLACE) {
+      SP_TRY(fill(AssignMergeLoader<RP, CI, VT, IX>{
+          static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
+          pl->rpB, static_cast<const CI*>(B.colidx), static_cast<const VT*>(B.values),
+          static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->J), static_cast<const IX*>(pl->jinv),
+          static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz,
+          pl->mode == SP_ASSIGN_PLUS ? 1 : 0}));
+    } else {
+      SP_TRY(fill(AssignLoader<RP, CI, VT, IX>{static_cast<const RP*>(A.rowptr),
+                                               static_cast<const CI*>(A.colidx),
+                                               static_cast<const VT*>(A.values), pl->rpB,
+                                               static_cast<const CI*>(B.colidx),
+                                               static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
+                                               static_cast<const IX*>(pl->J),
+                                               static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols,
+                                               A.nnz, pl->nJ, B.nnz}));
     }
-    SP_CUDA(cudaGetLastError());
-    {
-      SP_PHASE(SP_PHASE_GATHER);
-      k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, tcol,
-                                       tval, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
     const RowsWs w1 = rows_bind(cv, nI, nt, r1);
     const int kb = ceil_log2_u64(uint64_t(A.ncols));
     SP_TRY((run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nt, kb, w1, nullptr, true, tcol, tval)));
@@ -272,7 +407,6 @@ extern "C" sp_status sp_assign_count(sp_ctx* ctx, const sp_csr* A, const void* I
   if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
   if (mode != SP_ASSIGN_REPLACE && mode != SP_ASSIGN_SELECT2ND && mode != SP_ASSIGN_PLUS)
     return SP_ERR_INVALID_ARG;
-  if (mode != SP_ASSIGN_REPLACE) return SP_ERR_INVALID_ARG;  // only REPLACE is implemented
   if (nI < 0 || nJ < 0 || nI > A->nrows || nJ > A->ncols) return SP_ERR_SHAPE;
   if ((nI > 0 && !I) || (nJ > 0 && !J)) return SP_ERR_INVALID_ARG;
   if (B->nrows != nI || B->ncols != nJ) return SP_ERR_SHAPE;

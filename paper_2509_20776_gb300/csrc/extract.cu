@@ -33,6 +33,7 @@ struct ExtractLoader {
   }
   static constexpr bool kAllKept = false;
   static constexpr bool kLoadVals = true;
+  static constexpr bool kRowCtx = false;
   __device__ const CI* cols(int) const { return col; }
   __device__ const VT* vals(int) const { return val; }
   __device__ bool test(int, long long c) const {
@@ -49,16 +50,6 @@ struct ExtractLoader {
 // Consecutive J = [j0, j1): the kept entries of a (sorted) row form one segment, found by
 // binary search, and keep their order (the paper's binary-search idea of Alg. 5 applied
 // to a whole range).  The row length functor of the scan records the segment start.
-template <class CI>
-__device__ __forceinline__ long long lower_bound_col(const CI* col, long long lo, long long hi, long long v) {
-  while (lo < hi) {
-    const long long mid = (lo + hi) >> 1;
-    if ((long long)col[mid] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 template <class RP, class CI, class IX>
 struct ExtractRangeLen {
   const RP* rowptr;

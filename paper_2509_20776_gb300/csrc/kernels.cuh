@@ -136,6 +136,7 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
       Ls[u] = rs[u].n0 + rs[u].n1;
       lng[u] = Ls[u] > SRC_LONG;
       bt.valid[u] = !lng[u] && lane < Ls[u];
+      bt.set_row(u, i);
       if (bt.valid[u]) bt.at(u, rs[u], lane);
     }
     bt.run(ko);
@@ -150,6 +151,7 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
         for (int v = 0; v < LOAD_U; ++v) {
           const long long e = e0 + v * 32 + lane;
           b2.valid[v] = e < Ls[u];
+          b2.set_row(v, i0 + u);
           if (b2.valid[v]) b2.at(v, rs[u], e);
         }
         b2.run(ko);
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(1024) k_count_long(Ct ct, long long* __restric
       for (int u = 0; u < LOAD_U; ++u) {
         const long long e = e0 + (long long)u * blockDim.x + t;
         bt.valid[u] = e < Ls;
+        bt.set_row(u, i);
         if (bt.valid[u]) bt.at(u, rs, e);
       }
       bt.run(ko);
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, 
       Ls[u] = rs[u].n0 + rs[u].n1;
       lng[u] = Ls[u] > SRC_LONG;
       bt.valid[u] = !lng[u] && lane < Ls[u];
+      bt.set_row(u, i);
       if (bt.valid[u]) bt.at(u, rs[u], lane);
     }
     bt.run(ld);
@@ -273,6 +277,7 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, 
         for (int v = 0; v < LOAD_U; ++v) {
           const long long e = e0 + v * 32 + lane;
           b2.valid[v] = e < Ls[u];
+          b2.set_row(v, i0 + u);
           if (b2.valid[v]) b2.at(v, rs[u], e);
         }
         b2.run(ld);
@@ -318,6 +323,7 @@ __global__ void __launch_bounds__(1024) k_fill_long(Ld ld, const long long* __re
       for (int u = 0; u < LOAD_U; ++u) {
         const long long e = e0 + (long long)u * blockDim.x + t;
         bt.valid[u] = e < Ls;
+        bt.set_row(u, i);
         if (bt.valid[u]) bt.at(u, rs, e);
       }
       bt.run(ld);

@@ -11,6 +11,10 @@
 //     bool test(int part, int64 c) const;        // does an entry of column c survive
 //     bool map(int part, int64 c, uint32& key) const;
 //         // new column of a surviving entry with column c (false: dropped)
+//     static constexpr bool kRowCtx;             // survival depends on the row as well:
+//     bool test_ctx(int part, int64 c, int64 i) const;            // instead of test,
+//     bool map_ctx(int part, int64 c, uint32& key, int64 i, int64& aux) const;  // map,
+//     VT value_ctx(int part, int64 pos, int64 aux) const;          // and the value load
 //   };
 // Source entries are read in batches (struct Batch): every thread first issues the
 // column loads of U entries, then their map lookups, then their value loads, so that
@@ -26,32 +30,60 @@ struct RowSrc {
   long long n0, n1;  // lengths (n1 = 0 for single-run sources)
 };
 
+// First position in col[lo, hi) (ascending) whose column is not below v.
+template <class CI>
+__device__ __forceinline__ long long lower_bound_col(const CI* col, long long lo, long long hi, long long v) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if ((long long)col[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // U source entries read together (see the file comment).
 template <class Ld, int U>
 struct Batch {
+  static constexpr int UR = Ld::kRowCtx ? U : 1;
   long long pos[U];
   int part[U];
   bool valid[U];
   bool kept[U];
   uint32_t key[U];
   typename Ld::VT v[U];
+  long long row[UR];  // listed row of each entry (row-context loaders only)
+  __device__ __forceinline__ void set_row(int u, long long i) {
+    if constexpr (Ld::kRowCtx) row[u] = i;
+  }
   __device__ __forceinline__ void run(const Ld& ld) {
     using CI = typename Ld::CI;
     CI c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) c[u] = valid[u] ? ld_stream(ld.cols(part[u]) + pos[u]) : CI(0);
-    if constexpr (Ld::kLoadVals && Ld::kAllKept) {
-      // nothing is dropped: the value loads need not wait for the map lookups
+    if constexpr (Ld::kRowCtx) {
+      long long aux[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (valid[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
-    }
+        kept[u] = valid[u] && ld.map_ctx(part[u], (long long)c[u], key[u], row[u], aux[u]);
+      if constexpr (Ld::kLoadVals) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) kept[u] = valid[u] && ld.map(part[u], (long long)c[u], key[u]);
-    if constexpr (Ld::kLoadVals && !Ld::kAllKept) {
+        for (int u = 0; u < U; ++u)
+          if (kept[u]) v[u] = ld.value_ctx(part[u], pos[u], aux[u]);
+      }
+    } else {
+      if constexpr (Ld::kLoadVals && Ld::kAllKept) {
+        // nothing is dropped: the value loads need not wait for the map lookups
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (kept[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
+        for (int u = 0; u < U; ++u)
+          if (valid[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) kept[u] = valid[u] && ld.map(part[u], (long long)c[u], key[u]);
+      if constexpr (Ld::kLoadVals && !Ld::kAllKept) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (kept[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
+      }
     }
   }
   // entry e of a row's source runs
@@ -71,11 +103,16 @@ struct CountOnly {
   using VT = Nothing;
   static constexpr bool kLoadVals = false;
   static constexpr bool kAllKept = false;
+  static constexpr bool kRowCtx = Ld::kRowCtx;
   Ld ld;
   __device__ __forceinline__ const CI* cols(int part) const { return ld.cols(part); }
   __device__ __forceinline__ bool map(int part, long long c, uint32_t&) const {
     return ld.test(part, c);
   }
+  __device__ __forceinline__ bool map_ctx(int part, long long c, uint32_t&, long long i, long long&) const {
+    return ld.test_ctx(part, c, i);
+  }
+  __device__ __forceinline__ VT value_ctx(int, long long, long long) const { return VT{}; }
 };
 
 // Rows whose source holds more than SRC_LONG entries are "source-long": the count and

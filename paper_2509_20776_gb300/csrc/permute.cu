@@ -12,32 +12,6 @@
 
 namespace sp {
 
-template <class RP, class CIt, class VTt, class IX>
-struct PermLoader {
-  using CI = CIt;
-  using VT = VTt;
-  const RP* rowptr;
-  const CI* col;
-  const VT* val;
-  const IX* qinv;          // old column -> new column (null: identity)
-  const long long* sstart;  // source start of output row r (written by the scan)
-  const long long* vp;      // output row pointer (row r has vp[r+1]-vp[r] entries)
-  long long n;
-  __device__ RowSrc row(long long r) const {
-    return RowSrc{sstart[r], 0, vp[r + 1] - vp[r], 0};
-  }
-  static constexpr bool kAllKept = true;
-  static constexpr bool kLoadVals = true;
-  __device__ const CI* cols(int) const { return col; }
-  __device__ const VT* vals(int) const { return val; }
-  __device__ bool test(int, long long c) const { return c >= 0 && c < n; }
-  __device__ bool map(int, long long c, uint32_t& key) const {
-    if (c < 0 || c >= n) return false;  // not canonical (sp_csr_validate reports it)
-    key = qinv ? uint32_t(ld_map(qinv + c)) : uint32_t(c);
-    return true;
-  }
-};
-
 // Scan input for the permutation: len(A[p[i], :]); records the source start of every
 // output row on the way, so the fill kernels need no second lookup through p.
 template <class RP, class IX>

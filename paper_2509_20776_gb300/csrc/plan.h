@@ -20,6 +20,7 @@ struct sp_plan {
   void* jmap = nullptr;        // extraction: jinv (nJ positions); assignment: J bitmap
   void* rowmap = nullptr;      // assignment: rowmap (m entries of idx type)
   void* jbits = nullptr;       // extraction: membership bitmap of J
+  void* jinv = nullptr;        // assignment (union modes): column -> position in J
   long long* vp = nullptr;     // extraction: row pointer of B; assignment: of rows I (temp)
   long long* vp_out = nullptr; // assignment: row pointer of A'
   long long* rpB = nullptr;    // assignment: B's row pointer widened to int64

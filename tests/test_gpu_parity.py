@@ -279,6 +279,38 @@ def test_assign_hubs_and_roundtrip(ctx):
     assert_same(E, to_oracle(Bm), "extract after assign")
 
 
+def _union_b(A, I, J, seed, kind):
+    """B of |I| x |J|: every entry of A(I, J) with a fresh value, plus random others, so
+    the union modes meet both B entries that hit A and B entries that do not."""
+    E = oracle.extract(to_oracle(A), I.numpy(), J.numpy())
+    er_, ec, _ = E.triplets()
+    rng = np.random.default_rng(seed)
+    nI, nJ = len(I), len(J)
+    rr = rng.integers(0, nI, size=nI * 6)
+    rc = rng.integers(0, nJ, size=nI * 6)
+    rows = np.concatenate([er_, rr])
+    cols = np.concatenate([ec, rc])
+    key = np.unique(rows * nJ + cols)
+    rows, cols = key // nJ, key % nJ
+    dt = np.float32 if kind == "f32" else np.float64
+    vals = rng.uniform(-1, 1, size=key.size).astype(dt)
+    return oracle.build_csr(nI, nJ, rows, cols, vals)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+def test_assign_union_modes(ctx, mode, kind):
+    """SELECT2ND (1) and PLUS (2): A (+) P B Q^T; hub rows of A give source-long rows."""
+    A = rmat(14, sym=False, kind="f32u01" if kind == "f32" else "f64um11")
+    n = A.nrows
+    I = torch.cat([torch.arange(4, dtype=torch.int32), synth.random_subset(n - 4, 1500, 4, 1) + 4])
+    J = synth.random_subset(n, n // 2, 4, 2)
+    Bo = _union_b(A, I, J, 5, kind)
+    Bd = from_oracle(Bo, rowptr_dtype=torch.int32, colidx_dtype=A.colidx.dtype)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), Bd, mode=mode)
+    assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), Bo, mode), f"assign mode {mode}")
+
+
 def test_assign_contiguous(ctx):
     A = er(3000, 8, seed=8, kind="f32u01", rp=torch.int64)
     Bm = synth.er_csr(300, 400, 6, seed=9)
