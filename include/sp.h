@@ -217,6 +217,23 @@ SP_API sp_status sp_assign(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t 
                     int64_t nJ, sp_itype idx_type, const sp_csr* B, sp_assign_mode mode,
                     sp_csr* Aprime, sp_stream_t stream);
 
+/* Fused assignment + permutation (Sec. 6.3: incremental updates of a randomly permuted
+ * matrix; the fused HipAssign + HipPerm of the experiments):
+ *   out = P (A (+) B') Q^T, i.e. out[i, j] = A'[p[i], q[j]] with A' = sp_assign(A, I, J, B,
+ *   mode), computed without forming A'.
+ *   sp_assign_permute_fill takes a plan from sp_assign_count (which fixes I, J, B, mode
+ *   and the output nnz) and writes out; the plan stays valid.  p: nrows entries, q: ncols
+ *   entries (permutations of the plan's idx_type, or NULL for the identity; q == p gives
+ *   P A' P^T).  out: rowptr_type chosen by the caller, arrays caller-allocated (nnz from
+ *   the count) or all NULL (library-allocated).  sp_assign_permute = count + fill and
+ *   synchronises once.  Errors: those of sp_assign and sp_permute. */
+SP_API sp_status sp_assign_permute_fill(sp_ctx* ctx, sp_plan* plan, const void* p, const void* q,
+                                        sp_csr* out, sp_stream_t stream);
+SP_API sp_status sp_assign_permute(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                   const void* J, int64_t nJ, sp_itype idx_type, const sp_csr* B,
+                                   sp_assign_mode mode, const void* p, const void* q, sp_csr* out,
+                                   sp_stream_t stream);
+
 /* Release a plan (stream-ordered on the stream of its last call).  NULL is a no-op. */
 SP_API sp_status sp_plan_destroy(sp_ctx* ctx, sp_plan* plan);
 

@@ -63,6 +63,9 @@ SIGNATURES = {
                                ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp]),
     "sp_assign_fill": (_int, [_vp, _vp, _PCSR, _vp]),
     "sp_assign": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _int, _PCSR, _vp]),
+    "sp_assign_permute_fill": (_int, [_vp, _vp, _vp, _vp, _PCSR, _vp]),
+    "sp_assign_permute": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _int, _vp, _vp, _PCSR,
+                                 _vp]),
     "sp_plan_destroy": (_int, [_vp, _vp]),
     "sp_csr_free": (_int, [_vp, _PCSR]),
     "sp_inverse_map": (_int, [_vp, _vp, _i64, _i64, _int, _vp, _int, _vp]),
@@ -258,6 +261,31 @@ class Context:
         if sync:
             self.sync(stream)
         return Ap
+
+    def sp_assign_permute(self, A: CSR, I: torch.Tensor, J: torch.Tensor, B: CSR, p=None, q=None,
+                          mode: int = SP_ASSIGN_REPLACE, rowptr_dtype=None, stream=None,
+                          sync: bool = True) -> CSR:
+        """out = P (A with A(I, J) (+) B) Q^T without forming the assigned matrix
+        (p/q None = identity; q is p = symmetric)."""
+        idx_t = _itype(I.dtype)
+        plan = ctypes.c_void_p()
+        nnz = ctypes.c_int64()
+        st = _stream(stream)
+        self._check(self.lib.sp_assign_count(self.handle, ctypes.byref(A.desc()), _ptr(I),
+                                             I.numel(), _ptr(J), J.numel(), idx_t,
+                                             ctypes.byref(B.desc()), mode, ctypes.byref(plan),
+                                             ctypes.byref(nnz), st), "sp_assign_count")
+        try:
+            out = self._alloc(A.nrows, A.ncols, nnz.value, rowptr_dtype or A.rowptr.dtype, A)
+            d = out.desc()
+            self._check(self.lib.sp_assign_permute_fill(self.handle, plan, _ptr(p), _ptr(q),
+                                                        ctypes.byref(d), st),
+                        "sp_assign_permute_fill")
+        finally:
+            self.lib.sp_plan_destroy(self.handle, plan)
+        if sync:
+            self.sync(stream)
+        return out
 
     def _alloc(self, nrows, ncols, nnz, rowptr_dtype, like: CSR) -> CSR:
         dev = like.colidx.device

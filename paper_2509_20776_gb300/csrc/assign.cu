@@ -324,6 +324,45 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   return SP_OK;
 }
 
+// The rebuilt rows of I (kept entries of both parts, relabelled) into the staging buffer
+// at the rebuilt-row pointer pl->vp, in source order.  `ticket` holds 16 bytes.
+template <class RP, class CI, class VT, class IX>
+sp_status assign_stage(sp_ctx* ctx, sp_plan* pl, CI* tcol, VT* tval, unsigned* ticket, cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const sp_csr& B = pl->B;
+  const long long nI = pl->nI;
+  const int nsm = ctx->num_sms;
+  SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
+  auto fill = [&](const auto& ld) -> sp_status {
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, tcol,
+                                       tval, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+  };
+  if (pl->mode != SP_ASSIGN_REPLACE) {
+    return fill(AssignMergeLoader<RP, CI, VT, IX>{
+        static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
+        pl->rpB, static_cast<const CI*>(B.colidx), static_cast<const VT*>(B.values),
+        static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->J), static_cast<const IX*>(pl->jinv),
+        static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz,
+        pl->mode == SP_ASSIGN_PLUS ? 1 : 0});
+  }
+  return fill(AssignLoader<RP, CI, VT, IX>{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
+                                           static_cast<const VT*>(A.values), pl->rpB,
+                                           static_cast<const CI*>(B.colidx), static_cast<const VT*>(B.values),
+                                           static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->J),
+                                           static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols, A.nnz,
+                                           pl->nJ, B.nnz});
+}
+
 template <class RP, class CI, class VT, class IX>
 sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s) {
   const sp_csr& A = pl->A;
@@ -346,39 +385,7 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   const int nsm = ctx->num_sms;
   if (nt > 0) {
     // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
-    unsigned* ticket = cv.at<unsigned>(o_tk);
-    SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
-    auto fill = [&](const auto& ld) -> sp_status {
-      {
-        SP_PHASE(SP_PHASE_GATHER);
-        k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
-      }
-      SP_CUDA(cudaGetLastError());
-      {
-        SP_PHASE(SP_PHASE_GATHER);
-        k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, tcol,
-                                         tval, ctx->dstatus);
-      }
-      SP_CUDA(cudaGetLastError());
-      return SP_OK;
-    };
-    if (pl->mode != SP_ASSIGN_REPLACE) {
-      SP_TRY(fill(AssignMergeLoader<RP, CI, VT, IX>{
-          static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
-          pl->rpB, static_cast<const CI*>(B.colidx), static_cast<const VT*>(B.values),
-          static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->J), static_cast<const IX*>(pl->jinv),
-          static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz,
-          pl->mode == SP_ASSIGN_PLUS ? 1 : 0}));
-    } else {
-      SP_TRY(fill(AssignLoader<RP, CI, VT, IX>{static_cast<const RP*>(A.rowptr),
-                                               static_cast<const CI*>(A.colidx),
-                                               static_cast<const VT*>(A.values), pl->rpB,
-                                               static_cast<const CI*>(B.colidx),
-                                               static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
-                                               static_cast<const IX*>(pl->J),
-                                               static_cast<const uint32_t*>(pl->jmap), A.nrows, A.ncols,
-                                               A.nnz, pl->nJ, B.nnz}));
-    }
+    SP_TRY((assign_stage<RP, CI, VT, IX>(ctx, pl, tcol, tval, cv.at<unsigned>(o_tk), s)));
     const RowsWs w1 = rows_bind(cv, nI, nt, r1);
     const int kb = ceil_log2_u64(uint64_t(A.ncols));
     SP_TRY((run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nt, kb, w1, nullptr, true, tcol, tval)));
@@ -390,6 +397,133 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   const RowsWs w2 = rows_bind(cv, m, nnz_out, r2, false);
   return run_rows(ctx, s, pl->vp_out, m, nnz_out, 0, w2, &g, false, static_cast<CI*>(Ap->colidx),
                   static_cast<VT*>(Ap->values));
+}
+
+
+// ---- fused assignment + permutation (the paper's incremental-update use, Sec. 6.3) ----
+// out = P (A (+) P_I B Q_J^T) Q^T: output row i is row p[i] of A' = A with the
+// assignment applied, columns relabelled through qinv, sorted.  Row p[i] of A' is A's
+// own row (p[i] outside I) or the staged rebuilt row; one gather reads either, so A' is
+// never assembled.
+template <class RP, class IX>
+struct FusedLen {
+  const IX* p;
+  const long long* vpa;  // row pointer of A'
+  const IX* rowmap;      // row of A -> position in I, -1 elsewhere
+  const long long* vt;   // row pointer of the staged rebuilt rows
+  const RP* rpA;
+  long long m;
+  long long* sstart;     // source start of output row i (staged: bit 62 set)
+  __device__ long long operator()(long long i) const {
+    const long long r = p ? (long long)p[i] : i;
+    if (r < 0 || r >= m) {
+      sstart[i] = 0;
+      return 0;  // reported by the permutation check
+    }
+    const long long k = (long long)rowmap[r];
+    sstart[i] = k >= 0 ? (vt[k] | (1ll << 62)) : (long long)rpA[r];
+    return vpa[r + 1] - vpa[r];
+  }
+};
+
+template <class CIt, class VTt, class IX>
+struct FusedGs {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr long long kStaged = 1ll << 62;
+  const CI* colA;
+  const VT* valA;
+  const CI* tcol;
+  const VT* tval;
+  const IX* qinv;  // null: identity
+  const long long* sstart;
+  long long nnzA, ntemp, n;
+  __device__ long long src(long long i) const { return sstart[i]; }
+  __device__ CI col(long long pos) const {
+    if (pos & kStaged) {
+      const long long q = pos & ~kStaged;
+      return q < ntemp ? ld_stream(tcol + q) : CI(0);
+    }
+    return (pos >= 0 && pos < nnzA) ? ld_stream(colA + pos) : CI(0);
+  }
+  __device__ VT val(long long pos) const {
+    if (pos & kStaged) {
+      const long long q = pos & ~kStaged;
+      return q < ntemp ? ld_stream(tval + q) : VT(0);
+    }
+    return (pos >= 0 && pos < nnzA) ? ld_stream(valA + pos) : VT(0);
+  }
+  __device__ CI map(CI c) const {
+    if (!qinv) return c;
+    const long long cl = (long long)c;
+    if (cl < 0 || cl >= n) return CI(-1);  // reported as SP_ERR_INDEX_RANGE by the sort
+    return CI(ld_map(qinv + cl));
+  }
+};
+
+template <class RP, class CI, class VT, class IX>
+sp_status assign_permute_impl(sp_ctx* ctx, sp_plan* pl, const IX* p, const IX* q, sp_csr* out,
+                              cudaStream_t s) {
+  const sp_csr& A = pl->A;
+  const long long m = A.nrows, n = A.ncols, nt = pl->nnz_temp, nnz_out = pl->nnz_out;
+  const bool sym = p && q && (const void*)p == (const void*)q && m == n;
+  const bool out64 = out->rowptr_type == SP_I64;
+  Carver cv;
+  const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
+  const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
+  const size_t o_tk = cv.reserve(16);
+  const size_t o_qinv = cv.reserve(q ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_pbits = cv.reserve((p && !sym) ? size_t((m + 31) / 32) * 4 : 0);
+  const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
+  const size_t o_ss = cv.reserve(size_t(m) * 8);
+  const size_t o_scan = cv.reserve(scan_ws_bytes(m));
+  size_t ro[kRowsSlots];
+  rows_reserve(cv, m, nnz_out, sizeof(VT), ro);
+  char* base;
+  SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+  cv.bind(base);
+  const int nsm = ctx->num_sms;
+  IX* qinv = q ? cv.at<IX>(o_qinv) : nullptr;
+  if (q) {
+    SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(n) * sizeof(IX), s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_inverse_map<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, ctx->dstatus,
+                                                                   SP_ERR_NOT_PERMUTATION);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (p && !sym) {
+    uint32_t* bits = cv.at<uint32_t>(o_pbits);
+    SP_CUDA(cudaMemsetAsync(bits, 0, size_t((m + 31) / 32) * 4, s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(m, 256, nsm * 8), 256, 0, s>>>(p, m, m, bits, ctx->dstatus,
+                                                                SP_ERR_NOT_PERMUTATION);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  CI* tcol = cv.at<CI>(o_tc);
+  VT* tval = cv.at<VT>(o_tv);
+  if (nt > 0) SP_TRY((assign_stage<RP, CI, VT, IX>(ctx, pl, tcol, tval, cv.at<unsigned>(o_tk), s)));
+  // output row lengths (rows of A' moved by p) and their sources
+  long long* vp = out64 ? static_cast<long long*>(out->rowptr) : cv.at<long long>(o_vp);
+  long long* sstart = cv.at<long long>(o_ss);
+  const FusedLen<RP, IX> len{p, pl->vp_out, static_cast<const IX*>(pl->rowmap), pl->vp,
+                             static_cast<const RP*>(A.rowptr), m, sstart};
+  if (out64) {
+    SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{vp, nullptr, ctx->dstatus}, m, cv.at<char>(o_scan)));
+  } else {
+    SP_TRY(launch_scan(ctx, s, len, StoreDual<int32_t>{vp, static_cast<int32_t*>(out->rowptr), ctx->dstatus}, m,
+                       cv.at<char>(o_scan)));
+  }
+  if (nnz_out == 0) return SP_OK;
+  const FusedGs<CI, VT, IX> g{static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values), tcol, tval,
+                              qinv, sstart, A.nnz, nt, n};
+  const RowsWs w = rows_bind(cv, m, nnz_out, ro);
+  const int kb = ceil_log2_u64(uint64_t(n));
+  return run_rows(ctx, s, vp, m, nnz_out, kb, w, &g, true, static_cast<CI*>(out->colidx),
+                  static_cast<VT*>(out->values));
 }
 
 }  // namespace sp
@@ -484,6 +618,50 @@ extern "C" sp_status sp_assign(sp_ctx* ctx, const sp_csr* A, const void* I, int6
   int64_t nnz = 0;
   SP_TRY(sp_assign_count(ctx, A, I, nI, J, nJ, idx_type, B, mode, &pl, &nnz, stream));
   sp_status st = sp_assign_fill(ctx, pl, Aprime, stream);
+  plan_release(ctx, pl);
+  return st;
+}
+
+extern "C" sp_status sp_assign_permute_fill(sp_ctx* ctx, sp_plan* pl, const void* p, const void* q,
+                                            sp_csr* out, sp_stream_t stream) {
+  if (!ctx || !pl || !out || pl->op != 1) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type != SP_I32 && out->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  pl->stream = s;
+  const sp_csr& A = pl->A;
+  out->nrows = A.nrows;
+  out->ncols = A.ncols;
+  out->nnz = pl->nnz_out;
+  out->colidx_type = A.colidx_type;
+  out->value_type = A.value_type;
+  SP_TRY(alloc_csr(ctx, out, s));
+  return dispatch_i(A.rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(A.colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(A.value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(pl->idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return assign_permute_impl<RP, CI, VT, IX>(ctx, pl, static_cast<const IX*>(p),
+                                                     static_cast<const IX*>(q), out, s);
+        });
+      });
+    });
+  });
+}
+
+extern "C" sp_status sp_assign_permute(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
+                                       const void* J, int64_t nJ, sp_itype idx_type, const sp_csr* B,
+                                       sp_assign_mode mode, const void* p, const void* q, sp_csr* out,
+                                       sp_stream_t stream) {
+  if (!out) return SP_ERR_INVALID_ARG;
+  sp_plan* pl = nullptr;
+  int64_t nnz = 0;
+  SP_TRY(sp_assign_count(ctx, A, I, nI, J, nJ, idx_type, B, mode, &pl, &nnz, stream));
+  const sp_status st = sp_assign_permute_fill(ctx, pl, p, q, out, stream);
   plan_release(ctx, pl);
   return st;
 }

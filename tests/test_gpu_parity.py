@@ -311,6 +311,26 @@ def test_assign_union_modes(ctx, mode, kind):
     assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), Bo, mode), f"assign mode {mode}")
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("perm", ["sym", "pq", "rows_only"])
+def test_assign_permute_fused(ctx, mode, perm):
+    """out = P (A (+) B') Q^T in one pass equals the oracle's assign followed by permute."""
+    A = rmat(14, sym=False)
+    n = A.nrows
+    I = torch.cat([torch.arange(4, dtype=torch.int32), synth.random_subset(n - 4, 1500, 6, 1) + 4])
+    J = synth.random_subset(n, n // 2, 6, 2)
+    Bo = _union_b(A, I, J, 7, "f32")
+    Bd = from_oracle(Bo, rowptr_dtype=torch.int32, colidx_dtype=A.colidx.dtype)
+    p = synth.random_permutation(n, 6, 0)
+    q = p if perm == "sym" else (synth.random_permutation(n, 6, 1) if perm == "pq" else None)
+    pd = p.cuda()
+    qd = pd if perm == "sym" else (q.cuda() if q is not None else None)  # same tensor: P A' P^T
+    got = ctx.sp_assign_permute(to_dev(A), I.cuda(), J.cuda(), Bd, pd, qd, mode=mode)
+    Ao = oracle.assign(to_oracle(A), I.numpy(), J.numpy(), Bo, mode)
+    want = oracle.permute(Ao, p.numpy(), None if q is None else q.numpy())
+    assert_same(got, want, f"fused mode {mode} {perm}")
+
+
 def test_assign_contiguous(ctx):
     A = er(3000, 8, seed=8, kind="f32u01", rp=torch.int64)
     Bm = synth.er_csr(300, 400, 6, seed=9)
