@@ -458,11 +458,33 @@ def bench_assign(ctx, args, dev, hbm, ws):
     ab = A.nnz * 8 + nnz_out * 8 + 2 * (m + 1) * 8 + Bm.nnz * 8 + (k + 1) * 8 + k * 4 + k * 4 + m * 4 + A.ncols // 8
     frac = ab * steps / (ms * 1e-3) / 1e9 / hbm
     value = nnz_out * steps * ws / (ms * 1e-3)
-    return {"workload": "R-MAT scale 26 ef 24; A(I,J)=B, B ER 2^22 x 2^22 8/row, random I,J",
-            "nnz_in": A.nnz, "nnz_B": Bm.nnz, "nnz_out": nnz_out, "value": round(value, 1),
-            "unit": UNIT, "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
-            "alg_bytes_per_op": ab, "extract_after_assign_equals_B": roundtrip,
-            "phase_ms_per_op": phases}
+    res = {"workload": "R-MAT scale 26 ef 24; A(I,J)=B, B ER 2^22 x 2^22 8/row, random I,J",
+           "nnz_in": A.nnz, "nnz_B": Bm.nnz, "nnz_out": nnz_out, "value": round(value, 1),
+           "unit": UNIT, "ms_per_op": round(ms / steps, 3), "op_roofline_frac": round(frac, 4),
+           "alg_bytes_per_op": ab, "extract_after_assign_equals_B": roundtrip,
+           "phase_ms_per_op": phases}
+    # the incremental-update use: the assigned matrix under a random symmetric
+    # permutation, fused (one pass) against assign followed by permute
+    p = synth.random_permutation(m, 4, 3, device=dev)
+    out = ctx.sp_assign_permute(Ad, I, J, Bd, p, p)
+    ok = out.nnz == nnz_out
+    del out
+
+    def step_fused():
+        ctx.sp_assign_permute(Ad, I, J, Bd, p, p, sync=False)
+
+    def step_separate():
+        Ap2 = ctx.sp_assign(Ad, I, J, Bd, sync=False)
+        ctx.sp_permute(Ap2, p, p, sync=False)
+
+    ms_f = max_over_ranks(time_steps(step_fused, steps, 1, ws), ws)
+    ms_s = max_over_ranks(time_steps(step_separate, steps, 1, ws), ws)
+    res["assign_permute"] = {
+        "workload": "same A, I, J, B; out = P (A(I,J)=B) P^T, random p", "nnz_out": nnz_out,
+        "value": round(nnz_out * steps * ws / (ms_f * 1e-3), 1), "unit": UNIT,
+        "ms_per_op": round(ms_f / steps, 3), "ms_per_op_assign_then_permute": round(ms_s / steps, 3),
+        "nnz_matches_assign": ok}
+    return res
 
 
 # ---------------------------------------------------------------------------------------

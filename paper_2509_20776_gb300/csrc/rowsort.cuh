@@ -23,15 +23,16 @@ constexpr int SS_PASSES = 3;                   // passes over queued heavy bucke
 // A sort configuration: BLOCK threads sort items of at most CAP entries; a tile holds
 // the rows whose partition coordinate starts in a window of CP = CAP / 2, so at most
 // ROWS = CP / SS_ROW_W rows (one thread each) of at most CP entries.
-template <int BLOCK_, int CAP_>
+template <int BLOCK_, int CAP_, bool TILES_>
 struct SsCfg {
   static constexpr int B = BLOCK_, CAP = CAP_, CP = CAP_ / 2, ROWS = CP / SS_ROW_W;
   static constexpr int WORDS = CAP_ / 32;  // row-start bitmap words
+  static constexpr bool kTiles = TILES_;   // items are tiles (else: single runs)
   static_assert(ROWS <= B, "one thread per row of a tile");
   static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
 };
-using SsTile = SsCfg<256, 2048>;  // tiles of rows of at most 1024 entries, 4 CTAs per SM
-using SsRun = SsCfg<512, 4096>;   // single runs of at most 4096 entries, 2 CTAs per SM
+using SsTile = SsCfg<256, 2048, true>;   // tiles of rows of at most 1024 entries, 4 CTAs per SM
+using SsRun = SsCfg<512, 4096, false>;   // single runs of at most 4096 entries, 2 CTAs per SM
 constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts
 constexpr int SS_RUN_MAX = SsRun::CAP;   // longest row sorted alone
 
@@ -310,15 +311,15 @@ __global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long
 // whose starts fall in one GROUP_CAP window form one run for k_seg_sort; a bucket of
 // more than GROUP_CAP entries is a run of its own, or (more than SS_RUN_MAX entries,
 // only when a bucket spans more than SS_RUN_MAX keys) a run for the next split round.
-constexpr int SPLIT_BLOCK = 1024;
-constexpr int SPLIT_NB_LOG = 14;
+constexpr int SPLIT_BLOCK = 512;   // two CTAs (two long rows) per SM
+constexpr int SPLIT_NB_LOG = 13;
 constexpr int SPLIT_NB = 1 << SPLIT_NB_LOG;
 constexpr int SPLIT_U = 4;                 // entries per thread per batch
 constexpr int GROUP_CAP = SS_RUN_MAX / 2;  // small buckets grouped up to this start window
 constexpr size_t split_smem_bytes() { return size_t(SPLIT_NB) * 4 * 3; }
 
 template <class CI, class VT>
-__global__ void __launch_bounds__(SPLIT_BLOCK, 1)
+__global__ void __launch_bounds__(SPLIT_BLOCK, 2)
     k_split(const HugeEntry* __restrict__ runs, const unsigned* __restrict__ nruns_p, long long runs_cap,
             unsigned* ticket, uint32_t* __restrict__ tkey, VT* __restrict__ tval, CI* __restrict__ out_col,
             VT* __restrict__ out_val, FinalEntry* __restrict__ fin, unsigned* fin_n, long long fin_cap,
@@ -546,22 +547,27 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
   const int t = threadIdx.x;
   const uint32_t kmax = key_bits >= 32 ? 0xFFFFFFFFu : (1u << key_bits) - 1u;
   const float isr = ss_inv_root(kmax);
-  const long long ntiles = *ntiles_p;
-  long long nf = *fin_n;
-  if (nf > fin_cap) nf = fin_cap;  // overflow was reported by the producer
-  const long long nitems = ntiles + nf;
+  long long nitems;
+  if constexpr (Cfg::kTiles) {
+    nitems = *ntiles_p;
+  } else {
+    nitems = *fin_n;
+    if (nitems > fin_cap) nitems = fin_cap;  // overflow was reported by the producer
+  }
 
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-    for (int w = t; w < WORDS; w += B) bits[w] = 0;
-    if (t == 0) {
+    if constexpr (Cfg::kTiles) {
+      for (int w = t; w < WORDS; w += B) bits[w] = 0;
+    } else if (t == 0) {
       s_min = 0xFFFFFFFFu;
       s_max = 0u;
     }
     long long base;
     int buf = BUF_OUT;
-    uint32_t myL = 0;
-    long long o0 = 0;
-    if (item < ntiles) {
+    int E;
+    if constexpr (Cfg::kTiles) {
+      uint32_t myL = 0;
+      long long o0 = 0;
       const long long r0 = tile_first[item];
       long long r1 = tile_first[item + 1];
       base = vp[r0];
@@ -577,56 +583,57 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
           else myL = uint32_t(L);
         }
       }
+      // packed start (high half) and rank among the item's rows (low half)
+      uint32_t tot;
+      const uint32_t pre = block_excl_sum<B>(myL ? ((myL << 16) | 1u) : 0u, tmp32, &tot);
+      E = int(tot >> 16);  // <= 2 * Cfg::CP by the partition
+      if (E > CAP) {       // cannot happen: see RowsPartition
+        if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -19);
+        __syncthreads();
+        continue;
+      }
+      if (myL) {
+        const uint32_t k = pre & 0xFFFFu, ps = pre >> 16;
+        const uint32_t nb = ss_nb(myL);
+        rps[k] = uint16_t(ps);
+        rnm[k] = uint16_t(nb - 1);
+        rsc[k] = float(nb) * isr;
+        rdel[k] = uint32_t(o0 - base) - ps;
+        atomicOr(&bits[ps >> 5], 1u << (ps & 31));
+      }
+      for (int x = t; x < E; x += B) cnt[x] = 0;
+      __syncthreads();
+      if (t < 32) {
+        constexpr int WL = WORDS / 32;  // words per lane
+        uint32_t c[WL], s = 0;
+#pragma unroll
+        for (int j = 0; j < WL; ++j) {
+          c[j] = __popc(bits[t * WL + j]);
+          s += c[j];
+        }
+        uint32_t run = warp_incl_sum(s) - s;
+#pragma unroll
+        for (int j = 0; j < WL; ++j) {
+          wpre[t * WL + j] = run;
+          run += c[j];
+        }
+      }
+      __syncthreads();
     } else {
-      const FinalEntry fe = fin[item - ntiles];
+      const FinalEntry fe = fin[item];
       base = fe.off;
       buf = fe.buf;
+      E = int(fe.len);
       if (fe.len < 0 || fe.len > CAP) {
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -18);
-      } else if (t == 0) {
-        myL = uint32_t(fe.len);
-        o0 = base;
+        E = 0;
       }
-    }
-    // packed start (high half) and rank among the item's rows (low half)
-    uint32_t tot;
-    const uint32_t pre = block_excl_sum<B>(myL ? ((myL << 16) | 1u) : 0u, tmp32, &tot);
-    const int E = int(tot >> 16);  // <= 2 * Cfg::CP by the partition
-    if (E > CAP) {                 // cannot happen: see RowsPartition
-      if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -19);
+      for (int x = t; x < E; x += B) cnt[x] = 0;
       __syncthreads();
-      continue;
     }
-    if (myL) {
-      const uint32_t k = pre & 0xFFFFu, ps = pre >> 16;
-      const uint32_t nb = ss_nb(myL);
-      rps[k] = uint16_t(ps);
-      rnm[k] = uint16_t(nb - 1);
-      rsc[k] = float(nb) * isr;
-      rdel[k] = uint32_t(o0 - base) - ps;
-      atomicOr(&bits[ps >> 5], 1u << (ps & 31));
-    }
-    for (int x = t; x < E; x += B) cnt[x] = 0;
-    __syncthreads();
-    if (t < 32) {
-      constexpr int WL = WORDS / 32;  // words per lane
-      uint32_t c[WL], s = 0;
-#pragma unroll
-      for (int j = 0; j < WL; ++j) {
-        c[j] = __popc(bits[t * WL + j]);
-        s += c[j];
-      }
-      uint32_t run = warp_incl_sum(s) - s;
-#pragma unroll
-      for (int j = 0; j < WL; ++j) {
-        wpre[t * WL + j] = run;
-        run += c[j];
-      }
-    }
-    __syncthreads();
     // load: key and value of every packed entry, bucket histogram
     constexpr int LU = 4;
-    if (item < ntiles) {
+    if constexpr (Cfg::kTiles) {
       for (int x0 = t; x0 < E; x0 += B * LU) {
         uint32_t kk[LU], kr[LU], oo[LU];  // key, row, offset from base
         VT vv[LU];
@@ -720,7 +727,6 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
       for (int x = t; x < E; x += B) {
         const uint32_t sl = ss_bucket(skey[x] - lo, sc, last);
         slot[x] = uint16_t(sl);
-        rowk[x] = 0;
         atomicAdd(&cnt[sl], 1u);
       }
     }
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
       const uint32_t x = tidx[p], k = tkey[p];
       const uint32_t s = slot[x];
       const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
-      const uint32_t rd = rdel[rowk[x]];
+      const uint32_t rd = Cfg::kTiles ? rdel[rowk[x]] : 0u;
       if (hv && end - start > uint32_t(SS_HEAVY)) {
         st_stream(oc + rd + p, CI(k));
         st_stream(ov + rd + p, sval[x]);
@@ -875,7 +881,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     (void)once_h;
     {
       SP_PHASE(SP_PHASE_HUGE);
-      k_split<CI, VT><<<nsm, SPLIT_BLOCK, hsm, s>>>(w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval,
+      k_split<CI, VT><<<2 * nsm, SPLIT_BLOCK, hsm, s>>>(w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval,
                                                     out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt, nxt_n,
                                                     w.nxt_cap, ctx->dstatus);
     }
@@ -885,7 +891,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     if ((1ll << (key_bits > SPLIT_NB_LOG ? key_bits - SPLIT_NB_LOG : 0)) > SS_RUN_MAX) {
       {
         SP_PHASE(SP_PHASE_HUGE);
-        k_split<CI, VT><<<nsm, SPLIT_BLOCK, hsm, s>>>(w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval,
+        k_split<CI, VT><<<2 * nsm, SPLIT_BLOCK, hsm, s>>>(w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval,
                                                       out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt,
                                                       w.counters + 5, 0, ctx->dstatus);
       }
