@@ -178,8 +178,10 @@ SP_API sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, const v
 /* ------------------------------------------------------------------------------
  * Extraction  (Sec. 2.2; HipExtract, Algorithms 3 and 5)
  *   B = A(I, J): B[i, j] = A[I[i], J[j]] for (i, j) in I x J; B is nI x nJ.
- *   I: nI row indices (may repeat, any order); J: nJ column indices (distinct, any
- *   order; unsorted J permutes the columns of the result).  Both of idx_type.
+ *   I: nI row indices (may repeat, any order); J: nJ column indices (any order; unsorted
+ *   J permutes the columns of the result; a repeated column is copied under each of its
+ *   positions).  Both of idx_type.  Consecutive J (J[k] = J[0] + k) takes a per-row
+ *   binary search of the kept segment; ascending J needs no row sort.
  *
  * sp_extract_count: builds the column map and the row pointer of B, and returns the
  *   number of stored entries of B in *nnz_out (host).  Synchronises.  *plan receives
@@ -189,7 +191,7 @@ SP_API sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, const v
  *   counted value when caller-owned).  The plan can be filled more than once.
  * sp_extract: count + allocate + fill in one call (synchronises once).
  *   Errors: SP_ERR_INVALID_ARG, SP_ERR_SHAPE, SP_ERR_OVERFLOW; from the device
- *   SP_ERR_INDEX_RANGE, SP_ERR_DUPLICATE_INDEX (repeated J).
+ *   SP_ERR_INDEX_RANGE.
  * ------------------------------------------------------------------------------ */
 SP_API sp_status sp_extract_count(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
                            const void* J, int64_t nJ, sp_itype idx_type, sp_plan** plan,

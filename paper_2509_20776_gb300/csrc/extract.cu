@@ -88,6 +88,83 @@ struct ExtractRangeGs {
   __device__ CI map(CI c) const { return CI((long long)c - j0); }
 };
 
+// Repeated J (Sec. 2.2 allows repeats): column c of A feeds every position b with
+// J[b] = c.  The map is a CSR of the inverse: jcnt[c] positions starting at jptr[c] in
+// jpos.  One warp per listed row counts (pass 0: sum of jcnt over the row's columns)
+// or fills (pass 1: an entry with column c writes its value under each of its
+// positions, slots from a warp scan of the multiplicities); the row sort orders them.
+template <class IX>
+__global__ void k_jmulti_count(const IX* __restrict__ J, long long nJ, long long n, uint32_t* jcnt) {
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nJ;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long c = (long long)J[b];
+    if (c >= 0 && c < n) atomicAdd(jcnt + c, 1u);  // out-of-range J was reported
+  }
+}
+
+template <class IX>
+__global__ void k_jmulti_fill(const IX* __restrict__ J, long long nJ, long long n,
+                              const long long* __restrict__ jptr, uint32_t* jfill, IX* __restrict__ jpos) {
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nJ;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long c = (long long)J[b];
+    if (c < 0 || c >= n) continue;
+    jpos[jptr[c] + atomicAdd(jfill + c, 1u)] = IX(b);
+  }
+}
+
+template <int PASS, class RP, class CI, class VT, class IX>
+__global__ void k_extract_multi(const RP* __restrict__ rowptr, const CI* __restrict__ col,
+                                const VT* __restrict__ val, const IX* __restrict__ I, long long nI,
+                                long long m, long long n, long long nnz, const uint32_t* __restrict__ jcnt,
+                                const long long* __restrict__ jptr, const IX* __restrict__ jpos,
+                                long long* __restrict__ vp, CI* __restrict__ out_col,
+                                VT* __restrict__ out_val, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = w0; i < nI; i += nw) {
+    const long long r = (long long)I[i];
+    long long s = 0, e = 0;
+    if (r >= 0 && r < m) {
+      s = (long long)rowptr[r];
+      e = (long long)rowptr[r + 1];
+      if (s < 0 || e < s || e > nnz) s = e = 0;
+    }
+    long long run = PASS ? vp[i] : 0;
+    const long long end = PASS ? vp[i + 1] : 0;
+    for (long long k0 = s; k0 < e; k0 += 32) {
+      const long long k = k0 + lane;
+      long long c = -1;
+      long long mlt = 0;
+      if (k < e) {
+        c = (long long)ld_stream(col + k);
+        if (c >= 0 && c < n) mlt = jcnt[c];
+      }
+      if (PASS == 0) {
+        run += warp_sum(mlt);
+      } else {
+        const long long incl = warp_incl_sum(mlt);
+        const long long base = run + incl - mlt;
+        if (mlt) {
+          const VT v = ld_stream(val + k);
+          const long long p0 = jptr[c];
+          for (long long t = 0; t < mlt; ++t) {
+            if (base + t < end) {
+              st_stream(out_col + base + t, CI(jpos[p0 + t]));
+              st_stream(out_val + base + t, v);
+            } else {
+              dev_fail(st, SP_ERR_INTERNAL, -24);
+            }
+          }
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    if (PASS == 0 && lane == 0) vp[i] = run;
+  }
+}
+
 // copy an int64 row pointer into a typed output row pointer
 sp_status store_rowptr(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n1,
                        sp_itype t, void* out) {
@@ -144,7 +221,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_cn = cv.reserve(64);
   const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
   const size_t o_ss = cv.reserve(size_t(nI) * 8);
-  const size_t o_fl = cv.reserve(16);
+  const size_t o_fl = cv.reserve(16);  // J strictly ascending / consecutive / repeats
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
   pl->sstart = cv.at<long long>(o_ss);
@@ -166,15 +243,74 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     }
     SP_CUDA(cudaGetLastError());
   }
-  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 1, flags, 8, cudaMemcpyDeviceToHost, s));
-  if (nJ > 0) SP_CUDA(cudaMemcpyAsync(pl->h_tail + 2, J, sizeof(IX), cudaMemcpyDeviceToHost, s));
+  // membership bitmap of J; repeats are flagged (flags[2]) and take the multi-map path
+  SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
+  if (nJ > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jbits, ctx->dstatus,
+                                                                  SP_ERR_DUPLICATE_INDEX, flags + 2);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 1, flags, 16, cudaMemcpyDeviceToHost, s));
+  if (nJ > 0) SP_CUDA(cudaMemcpyAsync(pl->h_tail + 3, J, sizeof(IX), cudaMemcpyDeviceToHost, s));
   SP_TRY(ctx_collect(ctx, s));
-  int fl[2];
-  std::memcpy(fl, pl->h_tail + 1, 8);
-  pl->j_shape = nJ == 0 ? 0 : (fl[1] == 0 ? 2 : (fl[0] == 0 ? 1 : 0));
+  int fl[3];
+  std::memcpy(fl, pl->h_tail + 1, 12);
+  pl->j_shape = nJ == 0 ? 0 : (fl[2] ? 3 : (fl[1] == 0 ? 2 : (fl[0] == 0 ? 1 : 0)));
+  if (pl->j_shape == 3) {
+    if (nI > 0) {
+      SP_PHASE(SP_PHASE_MAP);
+      k_range_check<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    Carver c2;
+    const size_t o_cnt = c2.reserve(size_t(n) * 4);
+    const size_t o_fil = c2.reserve(size_t(n) * 4);
+    const size_t o_ptr = c2.reserve(size_t(n + 1) * 8);
+    const size_t o_pos = c2.reserve(size_t(nJ) * sizeof(IX));
+    const size_t o_sc2 = c2.reserve(scan_ws_bytes(n));
+    pl->buf2 = static_cast<char*>(ctx_alloc(ctx, c2.total(), s));
+    if (!pl->buf2) return SP_ERR_OOM;
+    pl->buf2_bytes = c2.total();
+    c2.bind(pl->buf2);
+    pl->jcnt = c2.at<uint32_t>(o_cnt);
+    uint32_t* jfill = c2.at<uint32_t>(o_fil);
+    pl->jptr = c2.at<long long>(o_ptr);
+    IX* jpos = c2.at<IX>(o_pos);
+    pl->jpos = jpos;
+    SP_CUDA(cudaMemsetAsync(pl->jcnt, 0, size_t(n) * 4, s));
+    SP_CUDA(cudaMemsetAsync(jfill, 0, size_t(n) * 4, s));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_jmulti_count<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, pl->jcnt);
+    }
+    SP_CUDA(cudaGetLastError());
+    SP_TRY(launch_scan(ctx, s, LoadArray<uint32_t>{pl->jcnt},
+                       StoreDual<long long>{pl->jptr, nullptr, ctx->dstatus}, n, c2.at<char>(o_sc2)));
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_jmulti_fill<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, pl->jptr, jfill, jpos);
+    }
+    SP_CUDA(cudaGetLastError());
+    if (nI > 0) {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_extract_multi<0, RP, CI, uint32_t, IX><<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(
+          static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), nullptr, I, nI, m, n, nnz,
+          pl->jcnt, pl->jptr, jpos, pl->vp, nullptr, nullptr, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
+                       StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_scan)));
+    SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+    SP_TRY(ctx_collect(ctx, s));
+    pl->nnz_out = pl->h_tail[0];
+    return SP_OK;
+  }
   if (pl->j_shape == 2) {
     IX first;
-    std::memcpy(&first, pl->h_tail + 2, sizeof(IX));
+    std::memcpy(&first, pl->h_tail + 3, sizeof(IX));
     pl->j0 = (long long)first;
     if (pl->j0 < 0 || pl->j0 + nJ > n) return SP_ERR_INDEX_RANGE;
     ExtractRangeLen<RP, CI, IX> len{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), I,
@@ -188,14 +324,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   }
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
   SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
-  SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
   if (nJ > 0) {
-    {
-      SP_PHASE(SP_PHASE_MAP);
-      k_mark_bits<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jbits, ctx->dstatus,
-                                                                  SP_ERR_DUPLICATE_INDEX);
-    }
-    SP_CUDA(cudaGetLastError());
     {
       SP_PHASE(SP_PHASE_MAP);
       k_inverse_map<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jinv, ctx->dstatus,
@@ -253,6 +382,24 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
     const RowsWs w = rows_bind(cv, nI, nnz_out, ro, false);
     return run_rows(ctx, s, pl->vp, nI, nnz_out, 0, w, &g, false, oc, ov);
   }
+  if (pl->j_shape == 3) {
+    // repeated J: every kept entry once per position of its column, then the row sort
+    rows_reserve(cv, nI, nnz_out, sizeof(VT), ro);
+    char* base;
+    SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
+    cv.bind(base);
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_extract_multi<1, RP, CI, VT, IX><<<grid_for(nI * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
+          static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
+          static_cast<const IX*>(pl->I), nI, A.nrows, A.ncols, A.nnz, pl->jcnt, pl->jptr,
+          static_cast<const IX*>(pl->jpos), pl->vp, oc, ov, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    const RowsWs w = rows_bind(cv, nI, nnz_out, ro);
+    const int kb = ceil_log2_u64(uint64_t(pl->nJ));
+    return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nnz_out, kb, w, nullptr, true, oc, ov);
+  }
   const bool sorted = pl->j_shape == 1;  // ascending J: the fill keeps rows in order
   rows_reserve(cv, nI, nnz_out, sizeof(VT), ro, !sorted);
   const size_t o_tk = cv.reserve(16);
@@ -289,6 +436,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
 sp_status plan_release(sp_ctx* ctx, sp_plan* pl) {
   if (!pl) return SP_OK;
   if (pl->buf) ctx_free(ctx, pl->buf, pl->buf_bytes, pl->stream);
+  if (pl->buf2) ctx_free(ctx, pl->buf2, pl->buf2_bytes, pl->stream);
   if (pl->h_tail) {
     cudaStreamSynchronize(pl->stream);
     cudaFreeHost(pl->h_tail);
@@ -320,7 +468,6 @@ extern "C" sp_status sp_extract_count(sp_ctx* ctx, const sp_csr* A, const void* 
   SP_TRY(check_csr(A));
   SP_TRY(check_index_args(A, I, nI, J, nJ, idx_type));
   if (nJ > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
-  if (nJ > A->ncols) return SP_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
   SP_TRY(validate_if_asked(ctx, A, s));

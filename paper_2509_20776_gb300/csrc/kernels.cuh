@@ -30,10 +30,12 @@ __global__ void k_inverse_map(const IX* __restrict__ idx, long long len, long lo
   }
 }
 
-// membership bitmap (1 bit per index); repeated indices are reported
+// membership bitmap (1 bit per index); repeated indices are reported as dup_code, or
+// only flagged in *dup_flag when one is given
 template <class IX>
 __global__ void k_mark_bits(const IX* __restrict__ idx, long long len, long long n,
-                            uint32_t* __restrict__ bits, DevStatus* st, int dup_code) {
+                            uint32_t* __restrict__ bits, DevStatus* st, int dup_code,
+                            int* dup_flag = nullptr) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len;
        k += (long long)gridDim.x * blockDim.x) {
     const long long v = (long long)idx[k];
@@ -43,7 +45,10 @@ __global__ void k_mark_bits(const IX* __restrict__ idx, long long len, long long
     }
     const uint32_t m = 1u << (v & 31);
     const uint32_t old = atomicOr(bits + (v >> 5), m);
-    if (old & m) dev_fail(st, dup_code, k);
+    if (old & m) {
+      if (dup_flag) *dup_flag = 1;  // repeats are allowed here: only flagged
+      else dev_fail(st, dup_code, k);
+    }
   }
 }
 

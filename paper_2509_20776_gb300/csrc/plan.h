@@ -27,9 +27,16 @@ struct sp_plan {
   long long* cl_rows = nullptr;
   // extraction: shape of J (0 general, 1 ascending, 2 consecutive), its first index, and
   // for consecutive J the start of every selected row's kept segment
-  int j_shape = 0;
+  int j_shape = 0;  // 3: J repeats indices (multi-map path)
   long long j0 = 0;
   long long* sstart = nullptr;
+  // repeated J: jcnt[c] = #{b : J[b] = c}, jptr = its exclusive scan, jpos the positions b
+  // grouped by column (in the plan's second buffer)
+  char* buf2 = nullptr;
+  size_t buf2_bytes = 0;
+  uint32_t* jcnt = nullptr;
+  long long* jptr = nullptr;
+  void* jpos = nullptr;
   long long list_cap = 0;
   unsigned* counters = nullptr;  // [0] n_cl [3] count ticket
   long long* h_tail = nullptr;   // pinned host: totals read back by the count call

@@ -229,6 +229,21 @@ def test_extract_ordered_j(ctx, shape):
     assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
 
 
+@pytest.mark.parametrize("size", ["small", "hubs"])
+def test_extract_repeated_j(ctx, size):
+    """J with repeats (more positions than columns): every position of a column gets a copy
+    (Sec. 2.2 allows repeated indices); I repeats too."""
+    A = special_values(er(3000, 8, seed=21) if size == "small" else rmat(14))
+    n = A.ncols
+    g = torch.Generator().manual_seed(22)
+    I = torch.randint(0, A.nrows, (A.nrows // 2,), generator=g).to(torch.int32)
+    J = torch.randint(0, n, (n + n // 3,), generator=g).to(torch.int32)
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), f"extract repeated J {size}")
+    kc = ctx.sp_kept_counts(to_dev(A), I.cuda(), J.cuda())
+    assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
+
+
 def test_extract_consecutive_j_out_of_range(ctx):
     from paper_2509_20776_gb300 import SpError
     A = to_dev(er(100, 4, seed=1))
@@ -431,9 +446,9 @@ def test_errors(ctx):
     with pytest.raises(SpError) as e:
         ctx.sp_permute(A, None, oob)
     assert e.value.name == "SP_ERR_INDEX_RANGE"
-    with pytest.raises(SpError) as e:
-        ctx.sp_extract(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
-                       torch.tensor([3, 3], dtype=torch.int32).cuda())
+    with pytest.raises(SpError) as e:  # assignment needs distinct J (extraction allows repeats)
+        ctx.sp_assign(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
+                      torch.tensor([3, 3], dtype=torch.int32).cuda(), to_dev(er(2, 2, seed=1)))
     assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
     with pytest.raises(SpError) as e:
         ctx.sp_extract(A, torch.tensor([0, 100], dtype=torch.int32).cuda(),
