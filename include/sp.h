@@ -236,6 +236,43 @@ SP_API sp_status sp_assign_permute(sp_ctx* ctx, const sp_csr* A, const void* I, 
                                    sp_assign_mode mode, const void* p, const void* q, sp_csr* out,
                                    sp_stream_t stream);
 
+/* ------------------------------------------------------------------------------
+ * Batched extraction (the batching pattern for serving many small requests; no
+ * counterpart in the paper, whose Algorithm 5 binary search per (i, j) it reuses for
+ * identification)
+ *   B_k = A_{mat}(I_k, J_k) for nreq requests over nmats device-resident matrices, all
+ *   matrices of one type combination; I_k may repeat, J_k distinct (idx_type; device
+ *   pointers).  Every step runs once for the whole batch (a fixed number of launches).
+ * sp_extract_batch_count: validates the requests, sorts every J_k, counts the kept
+ *   entries of every output row and returns the batch's total in *nnz_total (host).
+ *   Synchronises once.  *batch keeps the sorted J's and the row pointer; it borrows the
+ *   matrices and the index vectors until destroyed.
+ * sp_extract_batch_fill: writes all results into one CSR `out`: the rows of request k
+ *   are rows [sp_batch_row_offset(k), sp_batch_row_offset(k+1)) with column j meaning
+ *   position j of J_k; out has sum(nI) rows and max(nJ) columns.  out's arrays must be
+ *   caller-allocated (nnz from the count, A's colidx / value types, any rowptr type).
+ *   Never synchronises and allocates nothing, so it can be captured in a CUDA graph
+ *   and replayed while the inputs keep their addresses.
+ *   Errors: SP_ERR_INVALID_ARG, SP_ERR_SHAPE, SP_ERR_OVERFLOW; from the device
+ *   SP_ERR_INDEX_RANGE, SP_ERR_DUPLICATE_INDEX.
+ * ------------------------------------------------------------------------------ */
+typedef struct sp_extract_req {
+  int64_t mat;    /* index of the matrix in mats */
+  int64_t nI, nJ; /* lengths of I and J */
+  const void* I;  /* device, nI row indices */
+  const void* J;  /* device, nJ distinct column indices */
+} sp_extract_req;
+typedef struct sp_batch sp_batch;
+
+SP_API sp_status sp_extract_batch_count(sp_ctx* ctx, const sp_csr* mats, int64_t nmats,
+                                        const sp_extract_req* reqs, int64_t nreq, sp_itype idx_type,
+                                        sp_batch** batch, int64_t* nnz_total, sp_stream_t stream);
+SP_API sp_status sp_extract_batch_fill(sp_ctx* ctx, sp_batch* batch, sp_csr* out, sp_stream_t stream);
+/* First output row of request k (k = nreq gives the total); -1 for a bad k. */
+SP_API int64_t sp_batch_row_offset(const sp_batch* batch, int64_t k);
+/* Release a batch (stream-ordered on the stream of its count).  NULL is a no-op. */
+SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
+
 /* Release a plan (stream-ordered on the stream of its last call).  NULL is a no-op. */
 SP_API sp_status sp_plan_destroy(sp_ctx* ctx, sp_plan* plan);
 

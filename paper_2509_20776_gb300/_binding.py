@@ -42,10 +42,16 @@ class sp_csr(ctypes.Structure):
                 ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
+class sp_extract_req(ctypes.Structure):
+    _fields_ = [("mat", ctypes.c_int64), ("nI", ctypes.c_int64), ("nJ", ctypes.c_int64),
+                ("I", ctypes.c_void_p), ("J", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
 _PCSR = ctypes.POINTER(sp_csr)
+_PREQ = ctypes.POINTER(sp_extract_req)
 SIGNATURES = {
     "sp_status_str": (ctypes.c_char_p, [_int]),
     "sp_version": (_int, []),
@@ -66,6 +72,10 @@ SIGNATURES = {
     "sp_assign_permute_fill": (_int, [_vp, _vp, _vp, _vp, _PCSR, _vp]),
     "sp_assign_permute": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, _PCSR, _int, _vp, _vp, _PCSR,
                                  _vp]),
+    "sp_extract_batch_count": (_int, [_vp, _PCSR, _i64, _PREQ, _i64, _int, _vp, _vp, _vp]),
+    "sp_extract_batch_fill": (_int, [_vp, _vp, _PCSR, _vp]),
+    "sp_batch_row_offset": (_i64, [_vp, _i64]),
+    "sp_batch_destroy": (_int, [_vp, _vp]),
     "sp_plan_destroy": (_int, [_vp, _vp]),
     "sp_csr_free": (_int, [_vp, _PCSR]),
     "sp_inverse_map": (_int, [_vp, _vp, _i64, _i64, _int, _vp, _int, _vp]),
@@ -287,6 +297,22 @@ class Context:
             self.sync(stream)
         return out
 
+    def extract_batch(self, mats, requests, stream=None) -> "ExtractBatch":
+        """Count a batch of extractions B_k = mats[m_k](I_k, J_k); ``requests`` holds
+        (m_k, I_k, J_k) with device index tensors of one dtype.  Synchronises once."""
+        return ExtractBatch(self, mats, requests, stream)
+
+    def sp_extract_batch(self, mats, requests, rowptr_dtype=torch.int64, stream=None):
+        """All results of a batch in one CSR plus the first row of every request."""
+        bt = self.extract_batch(mats, requests, stream)
+        try:
+            out = bt.alloc(rowptr_dtype)
+            bt.fill(out, stream)
+            self.sync(stream)
+            return out, bt.row_offsets()
+        finally:
+            bt.close()
+
     def _alloc(self, nrows, ncols, nnz, rowptr_dtype, like: CSR) -> CSR:
         dev = like.colidx.device
         return CSR(nrows, ncols, torch.empty(nrows + 1, dtype=rowptr_dtype, device=dev),
@@ -334,3 +360,64 @@ class Context:
     def sp_csr_validate(self, A: CSR, stream=None):
         self._check(self.lib.sp_csr_validate(self.handle, ctypes.byref(A.desc()),
                                              _stream(stream)), "sp_csr_validate")
+
+
+class ExtractBatch:
+    """A counted batch of extractions (``sp_extract_batch_count``): ``fill`` launches the
+    whole batch without synchronising (capturable in a CUDA graph)."""
+
+    def __init__(self, ctx: Context, mats, requests, stream=None):
+        self.ctx = ctx
+        self.mats = list(mats)
+        self.requests = list(requests)
+        self.handle = None
+        if not self.mats:
+            raise ValueError("a batch needs at least one matrix")
+        dt = self.requests[0][1].dtype if self.requests else torch.int32
+        idx_t = _itype(dt)
+        self._descs = (sp_csr * len(self.mats))(*[m.desc() for m in self.mats])
+        self._reqs = (sp_extract_req * max(1, len(self.requests)))()
+        for k, (mi, I, J) in enumerate(self.requests):
+            if I.dtype != dt or J.dtype != dt:
+                raise TypeError("all index tensors of a batch share one dtype")
+            self._reqs[k] = sp_extract_req(int(mi), I.numel(), J.numel(),
+                                           I.data_ptr() if I.numel() else None,
+                                           J.data_ptr() if J.numel() else None)
+        h = ctypes.c_void_p()
+        nnz = ctypes.c_int64()
+        ctx._check(ctx.lib.sp_extract_batch_count(ctx.handle, self._descs, len(self.mats), self._reqs,
+                                                  len(self.requests), idx_t, ctypes.byref(h),
+                                                  ctypes.byref(nnz), _stream(stream)),
+                   "sp_extract_batch_count")
+        self.handle = h
+        self.nnz = nnz.value
+        self.rows = int(ctx.lib.sp_batch_row_offset(h, len(self.requests)))
+        self.ncols = max([J.numel() for _, _, J in self.requests] + [0])
+
+    def row_offsets(self):
+        return [int(self.ctx.lib.sp_batch_row_offset(self.handle, k))
+                for k in range(len(self.requests) + 1)]
+
+    def alloc(self, rowptr_dtype=torch.int64) -> CSR:
+        like = self.mats[0]
+        dev = like.colidx.device
+        return CSR(self.rows, self.ncols, torch.empty(self.rows + 1, dtype=rowptr_dtype, device=dev),
+                   torch.empty(self.nnz, dtype=like.colidx.dtype, device=dev),
+                   torch.empty(self.nnz, dtype=like.values.dtype, device=dev))
+
+    def fill(self, out: CSR, stream=None):
+        self._out_desc = out.desc()  # kept alive: a captured graph replays with these pointers
+        self.ctx._check(self.ctx.lib.sp_extract_batch_fill(self.ctx.handle, self.handle,
+                                                           ctypes.byref(self._out_desc), _stream(stream)),
+                        "sp_extract_batch_fill")
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.sp_batch_destroy(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
