@@ -1,0 +1,182 @@
+"""Continuous-batching request server over device-resident matrices.
+
+Requests (permute / extract / assign on one of the registered matrices) arrive over
+time.  Every scheduling round the server
+  * retires the requests whose work has finished on the device (latency = completion
+    time seen by the host - arrival time);
+  * admits the requests that have arrived, in arrival order, while their output bound
+    fits the device-memory budget (permutation: nnz(A); assignment: nnz(A) + nnz(B);
+    extraction: the batch's exact count);
+  * runs all admitted extractions as one batch (``ExtractBatch``: one count, one fill for
+    the whole round) and issues the permutations and assignments round-robin on several
+    stream slots, each with its own library context, so their work overlaps on the GPU.
+Requests that arrive while others are on the GPU join the next round: slots and memory
+free up as earlier work retires.  ``run_plain`` serves the same stream one synchronous
+call per request, for comparison.  Every kernel is the library's; this module only
+schedules.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+from ._binding import CSR, Context, ExtractBatch
+
+
+@dataclass
+class Request:
+    kind: str            # "permute" | "extract" | "assign"
+    mat: int             # index of the matrix handle
+    arrival: float       # seconds from the start of the stream
+    p: torch.Tensor | None = None   # permute: row / column permutation (P A P^T)
+    I: torch.Tensor | None = None   # extract / assign
+    J: torch.Tensor | None = None
+    B: CSR | None = None            # assign
+    done: float = -1.0
+    nnz_out: int = 0
+    result: CSR | tuple | None = None
+
+
+def _bytes(m: CSR) -> int:
+    return m.nnz * (m.colidx.element_size() + m.values.element_size()) + (m.nrows + 1) * 8
+
+
+@dataclass
+class Server:
+    mats: list[CSR]
+    slots: int = 4
+    mem_budget: int = 16 << 30      # bytes of outputs in flight
+    max_batch: int = 4096           # extractions per round
+    keep_results: bool = False
+    device: int = 0
+    _ctx: list = field(default_factory=list)
+    _streams: list = field(default_factory=list)
+
+    def __post_init__(self):
+        self._ctx = [Context(self.device) for _ in range(self.slots)]
+        self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
+
+    def close(self):
+        for c in self._ctx:
+            c.close()
+
+    def _bound(self, r: Request) -> int:
+        a = self.mats[r.mat]
+        if r.kind == "permute":
+            return _bytes(a)
+        if r.kind == "assign":
+            return _bytes(a) + _bytes(r.B)
+        return 0  # extractions are admitted by their exact count (below)
+
+    def run(self, reqs: list[Request]) -> list[Request]:
+        """Serve ``reqs`` (sorted by arrival); fills ``done`` / ``nnz_out`` of each."""
+        t0 = time.perf_counter()
+        i, n = 0, len(reqs)
+        inflight: list[tuple[list[Request], torch.cuda.Event, int, object]] = []
+        used = 0
+        turn = 0
+        while i < n or inflight:
+            now = time.perf_counter() - t0
+            # retire finished work (in issue order is not required)
+            still = []
+            for group, ev, nbytes, keep in inflight:
+                if ev.query():
+                    tdone = time.perf_counter() - t0
+                    for r in group:
+                        r.done = tdone
+                    if isinstance(keep, tuple):  # an extraction batch: per-request sizes
+                        _, out, offs = keep
+                        rp = out.rowptr.cpu()
+                        for j, r in enumerate(group):
+                            r.nnz_out = int(rp[offs[j + 1]] - rp[offs[j]])
+                    used -= nbytes
+                else:
+                    still.append((group, ev, nbytes, keep))
+            inflight = still
+            # admit what has arrived
+            ex, other = [], []
+            while i < n and reqs[i].arrival <= now and len(ex) < self.max_batch:
+                r = reqs[i]
+                b = self._bound(r)
+                if b and used + b > self.mem_budget and (inflight or ex or other):
+                    break  # wait for memory to free up
+                if r.kind == "extract":
+                    ex.append(r)
+                else:
+                    other.append(r)
+                    used += b
+                i += 1
+            if not ex and not other:
+                if inflight:
+                    continue
+                if i < n:  # idle until the next arrival
+                    while time.perf_counter() - t0 < reqs[i].arrival:
+                        pass
+                continue
+            for r in other:
+                k = turn % self.slots
+                turn += 1
+                ctx, st = self._ctx[k], self._streams[k]
+                a = self.mats[r.mat]
+                with torch.cuda.stream(st):
+                    if r.kind == "permute":
+                        out = ctx.sp_permute(a, r.p, r.p, stream=st, sync=False)
+                    else:
+                        out = ctx.sp_assign(a, r.I, r.J, r.B, stream=st, sync=False)
+                    r.nnz_out = out.nnz
+                    if self.keep_results:
+                        r.result = out
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                inflight.append(([r], ev, self._bound(r), out))
+            if ex:
+                k = turn % self.slots
+                turn += 1
+                ctx, st = self._ctx[k], self._streams[k]
+                with torch.cuda.stream(st):
+                    bt = ExtractBatch(ctx, self.mats, [(r.mat, r.I, r.J) for r in ex], stream=st)
+                    out = bt.alloc()
+                    nbytes = _bytes(out)
+                    bt.fill(out, st)
+                    offs = bt.row_offsets()
+                    if self.keep_results:
+                        for j, r in enumerate(ex):
+                            r.result = (out, offs[j], offs[j + 1])
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                used += nbytes
+                inflight.append((ex, ev, nbytes, (bt, out, offs)))
+        torch.cuda.synchronize()
+        for c in self._ctx:
+            c.sync()
+        return reqs
+
+
+def run_plain(ctx: Context, mats: list[CSR], reqs: list[Request], keep_results=False) -> list[Request]:
+    """One synchronous library call per request, in arrival order (the baseline)."""
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival:
+            pass
+        a = mats[r.mat]
+        if r.kind == "permute":
+            out = ctx.sp_permute(a, r.p, r.p)
+        elif r.kind == "extract":
+            out = ctx.sp_extract(a, r.I, r.J)
+        else:
+            out = ctx.sp_assign(a, r.I, r.J, r.B)
+        r.nnz_out = out.nnz
+        r.done = time.perf_counter() - t0
+        if keep_results:
+            r.result = out
+    return reqs
+
+
+def latency_stats(reqs: list[Request]) -> dict:
+    lat = torch.tensor([r.done - r.arrival for r in reqs], dtype=torch.float64)
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    return {"p50_ms": round(float(lat.quantile(0.5)) * 1e3, 3),
+            "p99_ms": round(float(lat.quantile(0.99)) * 1e3, 3),
+            "mean_ms": round(float(lat.mean()) * 1e3, 3), "span_s": round(span, 3)}
