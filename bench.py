@@ -318,6 +318,12 @@ def run_ours(args, ws, rank, local):
             log("batch done")
         except Exception as e:  # noqa: BLE001
             ops_res["batch_extract"] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
+        try:
+            ops_res["serve"] = bench_serve(ctx, args, dev)
+            log("serve done")
+        except Exception as e:  # noqa: BLE001
+            ops_res["serve"] = {"error": repr(e)[:300]}
         result["ops"] = ops_res
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
@@ -564,6 +570,65 @@ def bench_batch(ctx, args, dev, ws):
             "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1),
             "plain_ms": round(ms_plain, 3), "plain_value": round(nnz / (ms_plain * 1e-3), 1),
             "unit": UNIT, "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2)}
+
+
+def bench_serve(ctx, args, dev, nreq=10000):
+    """Poisson stream of mixed requests (60 % P A P^T, 30 % extraction, 10 % assignment)
+    over the batching workload's 64 matrices, at 0.8 x the plain path's measured capacity;
+    continuous batching against one synchronous call per request."""
+    import torch
+    import synth
+    from paper_2509_20776_gb300 import CSR
+    from paper_2509_20776_gb300.serving import Request, Server, latency_stats, run_plain
+    mats, ex = batch_workload(dev, nreq=nreq)
+    dms = [CSR(m.nrows, m.ncols, m.rowptr, m.colidx, m.values) for m in mats]
+    perms = [synth.random_permutation(m.nrows, 7, t, device=dev) for t, m in enumerate(mats)]
+    k2 = 256
+    Bm = synth.er_csr(k2, k2, 4, seed=9, value_kind="f32u01", rowptr_dtype=torch.int64,
+                      colidx_dtype=torch.int32, device=dev)
+    Bd = CSR(Bm.nrows, Bm.ncols, Bm.rowptr, Bm.colidx, Bm.values)
+    g = torch.Generator().manual_seed(11)
+    kinds = torch.rand(nreq, generator=g)
+
+    def make(arrivals):
+        reqs = []
+        for k in range(nreq):
+            mi, I, J = ex[k]
+            if kinds[k] < 0.6:
+                reqs.append(Request("permute", mi, arrivals[k], p=perms[mi]))
+            elif kinds[k] < 0.9:
+                reqs.append(Request("extract", mi, arrivals[k], I=I, J=J))
+            else:
+                m = mats[mi].nrows
+                sel = perms[mi][:2 * k2]
+                reqs.append(Request("assign", mi, arrivals[k], I=sel[:k2], J=sel[k2:2 * k2] if m >= 2 * k2 else sel[:k2],
+                                    B=Bd))
+        return reqs
+
+    # capacity of the plain path: a sample served back to back
+    ns = min(500, nreq)
+    sample = make([0.0] * nreq)[:ns]
+    run_plain(ctx, dms, sample)
+    cap = ns / max(max(r.done for r in sample), 1e-9)
+    res = {"workload": f"{nreq} requests (60/30/10 % permute/extract/assign) on the batching "
+                       f"workload's {len(mats)} matrices, Poisson arrivals",
+           "plain_capacity_per_s": round(cap, 1), "unit": UNIT}
+    srv = Server(dms, slots=4)
+    for load in (0.8, 2.0):  # below and above the plain path's capacity
+        rate = load * cap
+        gaps = torch.empty(nreq, dtype=torch.float64).exponential_(rate, generator=g)
+        arrivals = torch.cumsum(gaps, 0).tolist()
+        plain = run_plain(ctx, dms, make(arrivals))
+        served = srv.run(make(arrivals))
+        nnz_p = sum(r.nnz_out for r in plain)
+        nnz_s = sum(r.nnz_out for r in served)
+        sp, ss = latency_stats(plain), latency_stats(served)
+        res[f"load_{load}x"] = {"rate_per_s": round(rate, 1),
+                                "plain": {**sp, "value": round(nnz_p / sp["span_s"], 1)},
+                                "served": {**ss, "value": round(nnz_s / ss["span_s"], 1)},
+                                "same_nnz": nnz_p == nnz_s}
+    srv.close()
+    return res
 
 
 # ---------------------------------------------------------------------------------------
