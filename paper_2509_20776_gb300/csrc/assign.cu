@@ -52,6 +52,7 @@ struct AssignLoader {
   }
   static constexpr bool kAllKept = false;
   static constexpr bool kLoadVals = true;
+  static constexpr bool kEagerVals = false;
   static constexpr bool kRowCtx = false;
   __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
   __device__ const CI* cols(int part) const { return part ? colB : colA; }
@@ -96,6 +97,7 @@ struct AssignMergeLoader {
   int plus;  // 0: SELECT2ND, 1: PLUS
   static constexpr bool kAllKept = false;
   static constexpr bool kLoadVals = true;
+  static constexpr bool kEagerVals = false;
   static constexpr bool kRowCtx = true;
   __device__ RowSrc row(long long i) const {
     const long long r = (long long)I[i];

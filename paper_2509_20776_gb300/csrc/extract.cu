@@ -33,6 +33,7 @@ struct ExtractLoader {
   }
   static constexpr bool kAllKept = false;
   static constexpr bool kLoadVals = true;
+  static constexpr bool kEagerVals = true;  // about half the entries survive: cheaper than a trip
   static constexpr bool kRowCtx = false;
   __device__ const CI* cols(int) const { return col; }
   __device__ const VT* vals(int) const { return val; }
@@ -221,10 +222,12 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_cn = cv.reserve(64);
   const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
   const size_t o_ss = cv.reserve(size_t(nI) * 8);
+  const size_t o_sn = cv.reserve(size_t(nI) * 8);
   const size_t o_fl = cv.reserve(16);  // J strictly ascending / consecutive / repeats
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
   pl->sstart = cv.at<long long>(o_ss);
+  pl->slen = cv.at<long long>(o_sn);
   IX* jinv = cv.at<IX>(o_jinv);
   uint32_t* jbits = cv.at<uint32_t>(o_jb);
   pl->jmap = jinv;
@@ -341,7 +344,7 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     ExtractLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
                                            static_cast<const CI*>(A.colidx), nullptr, I, jinv,
                                            jbits, m, n, nnz};
-    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->sstart, pl->slen};
     {
       SP_PHASE(SP_PHASE_COUNT);
       k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
@@ -406,11 +409,12 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
-  ExtractLoader<RP, CI, VT, IX> ld{static_cast<const RP*>(A.rowptr),
-                                   static_cast<const CI*>(A.colidx),
-                                   static_cast<const VT*>(A.values), static_cast<const IX*>(pl->I),
-                                   static_cast<const IX*>(pl->jmap),
-                                   static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz};
+  // every listed row's source range was recorded by the count (k_count_warp)
+  RecordedRows<ExtractLoader<RP, CI, VT, IX>> ld{
+      {static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
+       static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->jmap),
+       static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz},
+      pl->sstart, pl->slen};
   // fill: kept entries, relabelled through jinv, into their output rows in source order
   unsigned* ticket = cv.at<unsigned>(o_tk);
   SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));

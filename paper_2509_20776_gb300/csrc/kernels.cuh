@@ -106,6 +106,8 @@ struct CountLists {
   long long* cl_rows;  // source-long rows waiting for k_count_long
   unsigned* n_cl;
   long long cl_cap;
+  long long* rs0 = nullptr;  // when given: source start and length of every listed row
+  long long* rsn = nullptr;  //   (single-run loaders), for a fill that reads them back
 };
 
 __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long cap, long long r,
@@ -138,6 +140,10 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
     for (int u = 0; u < COUNT_RB; ++u) {
       const long long i = i0 + u;
       rs[u] = i < nlisted ? ct.row(i) : RowSrc{0, 0, 0, 0};
+      if (cl.rs0 && lane == 0 && i < nlisted) {
+        cl.rs0[i] = rs[u].s0;
+        cl.rsn[i] = rs[u].n0;
+      }
       Ls[u] = rs[u].n0 + rs[u].n1;
       lng[u] = Ls[u] > SRC_LONG;
       bt.valid[u] = !lng[u] && lane < Ls[u];

@@ -5,6 +5,8 @@
 //     using CI = ...;  using VT = ...;           // column index / value word types
 //     static constexpr bool kAllKept;            // no source entry is ever dropped
 //     static constexpr bool kLoadVals;           // the pass needs the values
+//     static constexpr bool kEagerVals;          // load values with the columns, before
+//                                                // knowing which survive
 //     RowSrc row(int64 i) const;                 // source runs of listed row i
 //     const CI* cols(int part) const;            // column / value arrays of run `part`
 //     const VT* vals(int part) const;
@@ -71,15 +73,16 @@ struct Batch {
           if (kept[u]) v[u] = ld.value_ctx(part[u], pos[u], aux[u]);
       }
     } else {
-      if constexpr (Ld::kLoadVals && Ld::kAllKept) {
-        // nothing is dropped: the value loads need not wait for the map lookups
+      if constexpr (Ld::kLoadVals && (Ld::kAllKept || Ld::kEagerVals)) {
+        // the value loads need not wait for the map lookups (nothing is dropped, or the
+        // loader prefers loading dropped values to another round trip)
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (valid[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) kept[u] = valid[u] && ld.map(part[u], (long long)c[u], key[u]);
-      if constexpr (Ld::kLoadVals && !Ld::kAllKept) {
+      if constexpr (Ld::kLoadVals && !Ld::kAllKept && !Ld::kEagerVals) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
           if (kept[u]) v[u] = ld_stream(ld.vals(part[u]) + pos[u]);
@@ -95,6 +98,16 @@ struct Batch {
 
 constexpr int LOAD_U = 4;  // entries per thread per batch
 
+// A loader whose rows come from arrays recorded by the count pass (source start and
+// length of every listed row: one contiguous read instead of the index -> row pointer
+// chain), with every survival test and relabel of the underlying single-run loader.
+template <class Ld>
+struct RecordedRows : Ld {
+  const long long* rs0;
+  const long long* rsn;
+  __device__ __forceinline__ RowSrc row(long long i) const { return RowSrc{rs0[i], 0, rsn[i], 0}; }
+};
+
 // A loader view for counting passes: membership only (no key, no value loads).
 template <class Ld>
 struct CountOnly {
@@ -103,6 +116,7 @@ struct CountOnly {
   using VT = Nothing;
   static constexpr bool kLoadVals = false;
   static constexpr bool kAllKept = false;
+  static constexpr bool kEagerVals = false;
   static constexpr bool kRowCtx = Ld::kRowCtx;
   Ld ld;
   __device__ __forceinline__ const CI* cols(int part) const { return ld.cols(part); }

@@ -29,7 +29,8 @@ struct sp_plan {
   // for consecutive J the start of every selected row's kept segment
   int j_shape = 0;  // 3: J repeats indices (multi-map path)
   long long j0 = 0;
-  long long* sstart = nullptr;
+  long long* sstart = nullptr;  // consecutive J: kept-segment start; else the source start
+  long long* slen = nullptr;    // general J: source length of every listed row
   // repeated J: jcnt[c] = #{b : J[b] = c}, jptr = its exclusive scan, jpos the positions b
   // grouped by column (in the plan's second buffer)
   char* buf2 = nullptr;
