@@ -33,8 +33,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "output nnz/s & %HBM peak for permute/extract/assign; served p50/p99 vs plain"
 UNIT = "output nnz/s"
-WORKLOAD = ("R-MAT scale 25 (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, symmetrised; "
+WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, symmetrised; "
             "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
+
+# DRAM bytes (read + write) of one launch from the full ncu capture of the first P A P^T
+# at R-MAT scale 22 (profiles/kernels_permute_rmat22_full.md), and that launch's
+# algorithmic bytes; a launch of another size scales by its algorithmic bytes.  Only
+# valid for the kernels as captured: retake the capture when one changes.
+NCU_TRAFFIC = {
+    "gather": (2.636367e9, 2_633_332_664),
+    "tile": (1.290212e9, 1_341_222_304),
+    "huge": (0.472802e9, 428_803_080),
+}
 
 
 _T0 = time.time()
@@ -204,12 +214,16 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs):
             best = (ph, ms, cnt)
     ph, ms, cnt = best
     kernel = {"gather": "k_gather_chunks", "tile": "k_seg_sort<SsTile>", "long": "k_seg_sort<SsRun>",
-              "huge": "k_huge", "scan": "k_scan", "map": "k_inverse_map", "partition": "k_scan"}[ph]
+              "huge": "k_split", "scan": "k_scan", "map": "k_inverse_map", "partition": "k_scan"}[ph]
     byts = per_op[ph] * launches_total
     achieved = byts / (ms * 1e-3) / 1e9
+    traffic = None
+    if ph in NCU_TRAFFIC:
+        t_cap, alg_cap = NCU_TRAFFIC[ph]
+        traffic = round(t_cap * per_op[ph] / alg_cap)
     return {"bound": "hbm", "kernel": kernel, "phase": ph, "achieved": round(achieved, 1),
             "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
-            "traffic": None, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
+            "traffic": traffic, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
             "avg_launch_ms": round(ms / cnt, 4),
             "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
 
@@ -281,7 +295,7 @@ def run_ours(args, ws, rank, local):
         "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32 indices / fp32 values moved as 32-bit words",
         "data": "synthetic (seeded R-MAT; the paper's SuiteSparse graphs are not available)",
-        "config": {"workload": WORKLOAD, "rows": m, "nnz": nnz, "ops_per_step": len(ops),
+        "config": {"workload": WORKLOAD.format(scale=args.scale), "rows": m, "nnz": nnz, "ops_per_step": len(ops),
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{ws}"},
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -693,7 +707,7 @@ def run_reference(args):
             "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64 indices / fp32 values",
             "data": "synthetic (seeded R-MAT)",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": WORKLOAD.format(scale=args.scale), "sample": sample},
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
