@@ -165,7 +165,7 @@ def permute_workload(scale: int, device):
     return A, [("PAPt_random", p, p), ("PAPt_degree", pdeg, pdeg), ("PAQt_random", p, q)]
 
 
-TILE_CP, LONG_CAP = 1024, 4096  # row-length limits of the tile and long-row kernels
+TILE_CP, LONG_CAP = 512, 4096  # row-length limits of the tile and long-row kernels
 
 
 def row_classes(rowptr):

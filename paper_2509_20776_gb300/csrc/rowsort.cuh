@@ -12,6 +12,8 @@
 // and lists the rows that do not fit a tile.
 #pragma once
 
+#include <type_traits>
+
 #include "scan.cuh"
 
 namespace sp {
@@ -20,21 +22,29 @@ constexpr int SS_ROW_W = 4;                    // partition weight of a row
 constexpr int SS_HEAVY = 128;                  // larger buckets are sorted by a later pass
 constexpr int SS_PASSES = 3;                   // passes over queued heavy buckets
 
-// A sort configuration: BLOCK threads sort items of at most CAP entries; a tile holds
-// the rows whose partition coordinate starts in a window of CP = CAP / 2, so at most
-// ROWS = CP / SS_ROW_W rows (one thread each) of at most CP entries.
-template <int BLOCK_, int CAP_, bool TILES_>
+// A sort configuration: BLOCK threads sort items of at most CAP entries, MINB CTAs per
+// SM; a tile holds the rows whose partition coordinate starts in a window of
+// CP = CAP / 2, so at most ROWS = CP / SS_ROW_W rows (one thread each) of at most CP
+// entries.  A single run of L entries uses at most ss_nb(L) <= CAP / 2 bucket counters.
+template <int BLOCK_, int CAP_, bool TILES_, int MINB_>
 struct SsCfg {
-  static constexpr int B = BLOCK_, CAP = CAP_, CP = CAP_ / 2, ROWS = CP / SS_ROW_W;
+  static constexpr int B = BLOCK_, CAP = CAP_, CP = CAP_ / 2, ROWS = CP / SS_ROW_W, MINB = MINB_;
   static constexpr int WORDS = CAP_ / 32;  // row-start bitmap words
   static constexpr bool kTiles = TILES_;   // items are tiles (else: single runs)
-  static_assert(ROWS <= B, "one thread per row of a tile");
+  static constexpr int CNT = TILES_ ? CAP_ : CAP_ / 2;  // bucket counters
+  static_assert(!TILES_ || ROWS <= B, "one thread per row of a tile");
   static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
+  static_assert(B % 32 == 0 && B * MINB <= 2048, "whole warps, resident CTAs");
 };
-using SsTile = SsCfg<256, 2048, true>;   // tiles of rows of at most 1024 entries, 4 CTAs per SM
-using SsRun = SsCfg<512, 4096, false>;   // single runs of at most 4096 entries, 2 CTAs per SM
+using SsTile = SsCfg<128, 1024, true, 8>;  // tiles of rows of at most 512 entries
+// single runs of at most 4096 entries: with 4-byte values three CTAs of 384 threads fit
+// an SM (72 KB of shared memory each), with 8-byte values two of 512 (88 KB)
+template <class VT>
+using SsRunT = std::conditional_t<sizeof(VT) == 4, SsCfg<384, 4096, false, 3>, SsCfg<512, 4096, false, 2>>;
 constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts
-constexpr int SS_RUN_MAX = SsRun::CAP;   // longest row sorted alone
+constexpr int SS_RUN_MAX = 4096;         // longest row sorted alone
+static_assert(SsRunT<uint32_t>::CAP == SS_RUN_MAX && SsRunT<unsigned long long>::CAP == SS_RUN_MAX,
+              "one run capacity");
 
 // Runs handed from one kernel to the next: in the output arrays or in the temporary
 // arrays (keys as uint32, values) at the same offsets.
@@ -55,8 +65,8 @@ struct HugeEntry {  // a run longer than SS_RUN_MAX, keys in [lo, lo + 2^wb)
   int pad;
 };
 
-constexpr int GC_BLOCK = 512;                  // gather: threads per CTA
-constexpr int GC_CH = 4096;                    // gather: output positions per CTA
+constexpr int GC_BLOCK = 256;                  // gather: threads per CTA
+constexpr int GC_CH = 2048;                    // gather: output positions per CTA
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
 
 // ---- partition ----------------------------------------------------------------------
@@ -195,7 +205,7 @@ __device__ void smem_incl_max_w(uint32_t* a, int n, uint32_t* tmp) {
 //     __device__ typename Gs::CI map(typename Gs::CI c) const;  // new column
 //     __device__ typename Gs::VT val(long long pos) const;
 template <class Gs>
-__global__ void __launch_bounds__(GC_BLOCK, 2) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
+__global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
                                                             long long nrows, long long total,
                                                             const long long* __restrict__ chunk_first,
                                                             long long nchunks,
@@ -488,8 +498,11 @@ __device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_
 
 template <class Cfg, class VT>
 __host__ __device__ constexpr size_t ss_smem_bytes() {
-  return size_t(Cfg::CAP) * (sizeof(VT) + 4 * 3 + 2 * 3) + size_t(Cfg::ROWS) * (4 * 2 + 2 * 2) +
-         size_t(Cfg::WORDS) * 4 * 2;
+  // values, keys in packed and bucket order, counters, bucket and source of each entry;
+  // tiles add the per-row tables, the row-start bitmap and the row of each entry
+  return size_t(Cfg::CAP) * (sizeof(VT) + 4 * 2 + 2 * 2) + size_t(Cfg::CNT) * 4 +
+         (Cfg::kTiles ? size_t(Cfg::CAP) * 2 + size_t(Cfg::ROWS) * (4 * 2 + 2 * 2) + size_t(Cfg::WORDS) * 4 * 2
+                      : 0);
 }
 
 // In-place exclusive sum of a[0, n); thread t owns the ceil(n / B) consecutive entries
@@ -520,7 +533,7 @@ __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
 // run for a later pass, which buckets it over its own key range; without hv (the last
 // pass) every bucket is ranked directly.
 template <class Cfg, class CI, class VT>
-__global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
+__global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
     k_seg_sort(const long long* __restrict__ vp, const long long* __restrict__ tile_first,
                const long long* __restrict__ ntiles_p, const FinalEntry* __restrict__ fin,
                const unsigned* __restrict__ fin_n, long long fin_cap, const uint32_t* __restrict__ tkey_g,
@@ -533,13 +546,14 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
   uint32_t* skey = reinterpret_cast<uint32_t*>(smem + size_t(CAP) * sizeof(VT));  // packed order
   uint32_t* tkey = skey + CAP;        // bucket order
   uint32_t* cnt = tkey + CAP;         // bucket counters
-  uint32_t* rdel = cnt + CAP;         // per row: output offset from base - packed start
+  uint16_t* slot = reinterpret_cast<uint16_t*>(cnt + Cfg::CNT);  // bucket of packed entry
+  uint16_t* tidx = slot + CAP;        // packed entry of each bucket-order position
+  // tiles only (runs allocate none of these)
+  uint32_t* rdel = reinterpret_cast<uint32_t*>(tidx + CAP);  // per row: output offset from base - packed start
+  float* rsc = reinterpret_cast<float*>(rdel + ROWS);        // per row: bucket scale
   uint32_t* bits = rdel + 2 * ROWS;   // row starts
   uint32_t* wpre = bits + WORDS;      // row starts in earlier words
-  uint16_t* slot = reinterpret_cast<uint16_t*>(wpre + WORDS);  // bucket of packed entry
-  uint16_t* tidx = slot + CAP;        // packed entry of each bucket-order position
-  uint16_t* rowk = tidx + CAP;        // row of each packed entry
-  float* rsc = reinterpret_cast<float*>(rdel + ROWS);  // per row: bucket scale
+  uint16_t* rowk = reinterpret_cast<uint16_t*>(wpre + WORDS);  // row of each packed entry
   uint16_t* rps = rowk + CAP;         // per row: packed start
   uint16_t* rnm = rps + ROWS;         // per row: last bucket
   __shared__ uint32_t tmp32[B / 32 + 1];
@@ -555,7 +569,20 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
     if (nitems > fin_cap) nitems = fin_cap;  // overflow was reported by the producer
   }
 
+  // the next item's descriptor is loaded one item ahead, so its latency hides behind
+  // the current item's sort
+  long long pf0 = 0, pf1 = 0;  // tiles: row range
+  FinalEntry pfe{0, 0, 0, 0};  // runs
+  if (blockIdx.x < nitems) {
+    if constexpr (Cfg::kTiles) {
+      pf0 = tile_first[blockIdx.x];
+      pf1 = tile_first[blockIdx.x + 1];
+    } else {
+      pfe = fin[blockIdx.x];
+    }
+  }
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const long long nx = item + gridDim.x;
     if constexpr (Cfg::kTiles) {
       for (int w = t; w < WORDS; w += B) bits[w] = 0;
     } else if (t == 0) {
@@ -568,8 +595,12 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
     if constexpr (Cfg::kTiles) {
       uint32_t myL = 0;
       long long o0 = 0;
-      const long long r0 = tile_first[item];
-      long long r1 = tile_first[item + 1];
+      const long long r0 = pf0;
+      long long r1 = pf1;
+      if (nx < nitems) {
+        pf0 = tile_first[nx];
+        pf1 = tile_first[nx + 1];
+      }
       base = vp[r0];
       if (r1 - r0 > ROWS) {  // cannot happen: see RowsPartition
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -17);
@@ -620,7 +651,8 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
       }
       __syncthreads();
     } else {
-      const FinalEntry fe = fin[item];
+      const FinalEntry fe = pfe;
+      if (nx < nitems) pfe = fin[nx];
       base = fe.off;
       buf = fe.buf;
       E = int(fe.len);
@@ -628,7 +660,7 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -18);
         E = 0;
       }
-      for (int x = t; x < E; x += B) cnt[x] = 0;
+      for (int x = t; x < int(ss_nb(uint32_t(E))); x += B) cnt[x] = 0;
       __syncthreads();
     }
     // load: key and value of every packed entry, bucket histogram
@@ -731,7 +763,8 @@ __global__ void __launch_bounds__(Cfg::B, 1024 / Cfg::B)
       }
     }
     __syncthreads();
-    ss_excl_sum<B>(cnt, E, tmp32);
+    // counters in use: a tile's rows' buckets lie in [0, E), a run's in [0, ss_nb(E))
+    ss_excl_sum<B>(cnt, Cfg::kTiles ? E : int(ss_nb(uint32_t(E))), tmp32);
     // scatter to bucket order; afterwards cnt[s] = end of bucket s, cnt[s-1] its start
     for (int x = t; x < E; x += B) {
       const uint32_t p = atomicAdd(&cnt[slot[x]], 1u);
@@ -867,7 +900,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
     {
       SP_PHASE(SP_PHASE_GATHER);
-      const long long g = w.nchunks < 2ll * nsm ? w.nchunks : 2ll * nsm;  // persistent, 2 per SM
+      const long long g = w.nchunks < 4ll * nsm ? w.nchunks : 4ll * nsm;  // persistent, 4 per SM
       k_gather_chunks<Gs><<<unsigned(g), GC_BLOCK, 0, s>>>(*gs, vp, nrows, nnz, w.chunk_first, w.nchunks,
                                                            out_col, out_val);
     }
@@ -898,22 +931,23 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
       SP_CUDA(cudaGetLastError());
     }
   }
-  // tiles (4 CTAs per SM), then the runs, then the heavy buckets queued by either
+  // tiles, then the runs, then the heavy buckets queued by either
   const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   const unsigned* no_runs = w.counters + 8;
+  using SsRun = SsRunT<VT>;
   constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), rsm = ss_smem_bytes<SsRun, VT>();
   static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
   (void)once_s;
   {
     SP_PHASE(SP_PHASE_TILE);
-    k_seg_sort<SsTile, CI, VT><<<4 * nsm, SsTile::B, tsm, s>>>(
+    k_seg_sort<SsTile, CI, VT><<<SsTile::MINB * nsm, SsTile::B, tsm, s>>>(
         vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0], w.counters + 6,
         w.hv_cap, key_bits, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   {
     SP_PHASE(SP_PHASE_LONG);
-    k_seg_sort<SsRun, CI, VT><<<2 * nsm, SsRun::B, rsm, s>>>(
+    k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
         vp, w.tile_first, no_tiles, w.fin, fin_n, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
         w.counters + 6, w.hv_cap, key_bits, ctx->dstatus);
   }
@@ -925,7 +959,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     SP_CUDA(cudaMemsetAsync(w.counters + 6 + b, 0, 4, s));
     {
       SP_PHASE(SP_PHASE_LONG);
-      k_seg_sort<SsRun, CI, VT><<<2 * nsm, SsRun::B, rsm, s>>>(
+      k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
           vp, w.tile_first, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
           last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, ctx->dstatus);
     }

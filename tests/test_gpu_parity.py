@@ -144,7 +144,7 @@ def boundary_matrix(lengths, ncols, seed=0, kind="f32u01"):
 
 def test_row_length_boundaries(ctx):
     Ls = [0, 1, 2, 15, 16, 17, 31, 32, 33, 0, 0, 1023, 1024, 1025, 2047, 2048, 2049, 0, 4095,
-          4096, 4097, 8191, 8192, 8193, 16384, 3, 0, 70000, 1, 5, 129, 128, 127]
+          4096, 4097, 8191, 8192, 8193, 16384, 3, 0, 70000, 1, 5, 129, 128, 127, 511, 512, 513]
     A = boundary_matrix(Ls, 200000, seed=2)
     q = synth.random_permutation(200000, 2, 1)
     p = synth.random_permutation(len(Ls), 2, 0)
