@@ -36,15 +36,12 @@ UNIT = "output nnz/s"
 WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, symmetrised; "
             "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
 
-# DRAM bytes (read + write) of one launch from the full ncu capture of the first P A P^T
-# at R-MAT scale 22 (profiles/kernels_permute_rmat22_full.md), and that launch's
-# algorithmic bytes; a launch of another size scales by its algorithmic bytes.  Only
-# valid for the kernels as captured: retake the capture when one changes.
-NCU_TRAFFIC = {
-    "gather": (2.636367e9, 2_633_332_664),
-    "tile": (1.290212e9, 1_341_222_304),
-    "huge": (0.472802e9, 428_803_080),
-}
+# DRAM bytes (read + write) of one launch of a kernel on the first P A P^T (random p)
+# of the workload at a given R-MAT scale, from a one-pass ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum at that size
+# (profiles/dram_permute_rmat25.md).  Only valid for the kernels as captured: retake
+# the capture when one changes; other scales report null.
+NCU_TRAFFIC = {}
 
 
 _T0 = time.time()
@@ -183,7 +180,7 @@ def row_classes(rowptr):
     return out
 
 
-def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs):
+def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, scale):
     """Roofline of the phase that takes the most device time: its algorithmic bytes per
     launch (per-entry and per-row byte counts of the kernel, int32 indices and fp32
     values) over its average CUDA-event duration."""
@@ -217,10 +214,7 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs):
               "huge": "k_split", "scan": "k_scan", "map": "k_inverse_map", "partition": "k_scan"}[ph]
     byts = per_op[ph] * launches_total
     achieved = byts / (ms * 1e-3) / 1e9
-    traffic = None
-    if ph in NCU_TRAFFIC:
-        t_cap, alg_cap = NCU_TRAFFIC[ph]
-        traffic = round(t_cap * per_op[ph] / alg_cap)
+    traffic = NCU_TRAFFIC.get((scale, ph))
     return {"bound": "hbm", "kernel": kernel, "phase": ph, "achieved": round(achieved, 1),
             "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
             "traffic": traffic, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
@@ -285,7 +279,7 @@ def run_ours(args, ws, rank, local):
     ms = max_over_ranks(ms, ws)
     out_per_step = nnz * len(ops)
     value = out_per_step * args.steps * ws / (ms * 1e-3)
-    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm)
+    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, args.scale)
     # whole op: read and write col + val per entry, p and rowptr pair per row, q and qinv
     alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols
     op_frac = alg_bytes_op * len(ops) * args.steps / (ms * 1e-3) / 1e9 / hbm

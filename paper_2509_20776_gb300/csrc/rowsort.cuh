@@ -313,32 +313,81 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
   }
 }
 
-// ---- key-range split of long runs ------------------------------------------------------
-// A run of more than SS_RUN_MAX entries with keys in [lo, lo + 2^wb) is cut into
-// SPLIT_NB buckets of 2^(wb - SPLIT_NB_LOG) consecutive keys: pass 1 counts the bucket
-// sizes, one scan gives their offsets, pass 2 scatters the run bucket by bucket into the
-// other buffer (output <-> temporary) at the same offsets.  Consecutive small buckets
-// whose starts fall in one GROUP_CAP window form one run for k_seg_sort; a bucket of
-// more than GROUP_CAP entries is a run of its own, or (more than SS_RUN_MAX entries,
-// only when a bucket spans more than SS_RUN_MAX keys) a run for the next split round.
-constexpr int SPLIT_BLOCK = 512;   // two CTAs (two long rows) per SM
-constexpr int SPLIT_NB_LOG = 13;
-constexpr int SPLIT_NB = 1 << SPLIT_NB_LOG;
-constexpr int SPLIT_U = 4;                 // entries per thread per batch
-constexpr int GROUP_CAP = SS_RUN_MAX / 2;  // small buckets grouped up to this start window
-constexpr size_t split_smem_bytes() { return size_t(SPLIT_NB) * 4 * 3; }
+// ---- approximate square-root bucketing of the row sort -----------------------------------
+// Bucket of key k in a row of L entries: nb = 2^(ceil(log2 L) - 1) buckets spaced evenly
+// in an approximate square root of k over the row's key range [0, kmax].  The root is
+// the exponent-halving bit trick on the float of k (exact at even powers of two, up to
+// 6% high in between): monotone in k (every step is), so buckets stay in key order; the
+// scale nb / root(kmax) maps [0, kmax] onto the nb buckets.  The square root keeps
+// buckets balanced both for uniformly relabelled columns and for labels crowded at the
+// low end (degree-descending orderings).
+__device__ __forceinline__ uint32_t ss_nb(uint32_t L) { return L <= 2 ? 1u : 1u << (31 - __clz(L - 1)); }
+__device__ __forceinline__ float ss_root(uint32_t k) {
+  return __uint_as_float((__float_as_uint(__uint2float_rn(k)) >> 1) + 0x1FC00000u);
+}
+// 1 / root(kmax): the scale of a range [0, kmax] is nb * ss_inv_root(kmax)
+__device__ __forceinline__ float ss_inv_root(uint32_t kmax) { return kmax ? 1.0f / ss_root(kmax) : 0.0f; }
+// bucket of `key` given the row's scale and last bucket nb - 1
+__device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_t last) {
+  const uint32_t b = __float2uint_rz(ss_root(key) * scale);
+  return b < last ? b : last;
+}
 
-template <class CI, class VT>
-__global__ void __launch_bounds__(SPLIT_BLOCK, 2)
+// ---- key-range split of long runs ------------------------------------------------------
+// A run of more than SS_RUN_MAX entries with keys in [lo, lo + 2^wb) is cut into nb = 2^nbl
+// buckets of 2^(wb - nbl) consecutive keys: pass 1 counts the bucket sizes, one scan gives
+// their offsets, pass 2 moves the run bucket by bucket into the other buffer (output <->
+// temporary) at the same offsets.  Consecutive small buckets whose starts fall in one
+// GROUP_CAP window form one run for k_seg_sort; a bucket of more than GROUP_CAP entries is
+// a run of its own, or (more than SS_RUN_MAX entries) a run for the next split round.
+//   Round 1 (SplitCoarse): nb = 2^10 buckets evenly spaced over [lo, lo + 2^wb).  A run
+//     is sorted as a whole afterwards, so pass 2 only has to bring every entry into its
+//     group's range, not its bucket's: it stages each chunk of B * U entries in shared
+//     memory by group and writes every group's share of the chunk as one contiguous piece
+//     (groups hold hundreds to thousands of entries, so the writes are coalesced whatever
+//     the key distribution).
+//   Round 2 (SplitFine, the buckets of round 1 that hold more than SS_RUN_MAX entries,
+//     e.g. hub rows under a degree-descending relabelling): 2^13 buckets evenly spaced over
+//     the bucket's own [min, max] keys (found by a first pass), scattered directly.  A
+//     round-1 bucket spans 2^(wb - 10) <= 2^22 keys, so a round-2 bucket spans at most
+//     2^9 < SS_RUN_MAX keys: with keys unique within a row it holds fewer than SS_RUN_MAX
+//     entries and no third round is needed.
+struct SplitCoarse {
+  static constexpr int NBL = 10, B = 256, MINB = 4, U = 8;
+  static constexpr bool kStaged = true;
+};
+struct SplitFine {
+  static constexpr int NBL = 13, B = 512, MINB = 2, U = 4;
+  static constexpr bool kStaged = false;
+};
+constexpr int SS_RUN_LOG = 12;             // SS_RUN_MAX = 2^SS_RUN_LOG
+static_assert((1 << SS_RUN_LOG) == SS_RUN_MAX, "run capacity is a power of two");
+constexpr int GROUP_CAP = SS_RUN_MAX / 2;  // small buckets grouped up to this start window
+template <class S, class VT>
+constexpr size_t split_smem_bytes() {
+  // counts / starts / cursors, previous non-empty bucket, next group boundary; staged:
+  // the group of each bucket, the chunk's counts / starts per group, the chunk's base in
+  // each group, the chunk's keys and values
+  return size_t(1 << S::NBL) * 4 * 3 +
+         (S::kStaged ? size_t(1 << S::NBL) * 4 * 3 + size_t(S::B * S::U) * (4 + sizeof(VT)) : 0);
+}
+
+template <class S, class CI, class VT>
+__global__ void __launch_bounds__(S::B, S::MINB)
     k_split(const HugeEntry* __restrict__ runs, const unsigned* __restrict__ nruns_p, long long runs_cap,
             unsigned* ticket, uint32_t* __restrict__ tkey, VT* __restrict__ tval, CI* __restrict__ out_col,
             VT* __restrict__ out_val, FinalEntry* __restrict__ fin, unsigned* fin_n, long long fin_cap,
             HugeEntry* __restrict__ nxt, unsigned* nxt_n, long long nxt_cap, DevStatus* st) {
-  constexpr int B = SPLIT_BLOCK, U = SPLIT_U;
+  constexpr int B = S::B, U = S::U, NBM = 1 << S::NBL;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem);  // bucket sizes, then starts, then cursors
-  uint32_t* prv = hist + SPLIT_NB;   // 1 + last non-empty bucket at or before x (0: none)
-  uint32_t* nxb = prv + SPLIT_NB;    // reversed: L - start of the first group boundary >= x
+  uint32_t* prv = hist + NBM;   // 1 + last non-empty bucket at or before x (0: none)
+  uint32_t* nxb = prv + NBM;    // reversed: L - start of the first group boundary >= x
+  uint32_t* hd = nxb + NBM;     // staged: 1 + first bucket of each bucket's group
+  uint32_t* lh = hd + NBM;      // staged: the chunk's count, then start, in each group
+  uint32_t* gb = lh + NBM;      // staged: the chunk's offset in each group
+  uint32_t* sk = gb + NBM;      // staged: the chunk's keys by group
+  VT* sv = reinterpret_cast<VT*>(sk + B * U);  // and values
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ unsigned s_item;
   const int t = threadIdx.x;
@@ -351,35 +400,84 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 2)
     if (item >= count) break;
     const HugeEntry he = runs[item];
     const long long g0 = he.off, L = he.len;
-    const unsigned lo = he.lo;
-    const int wb = he.wb, sbuf = he.buf;
+    const int sbuf = he.buf;
     const int dbuf = sbuf == BUF_TEMP ? BUF_OUT : BUF_TEMP;
-    const int nbl = wb < SPLIT_NB_LOG ? wb : SPLIT_NB_LOG;
-    const int nb = 1 << nbl;
-    const int sh = wb - nbl;
-    for (int x = t; x < SPLIT_NB; x += B) hist[x] = 0;
-    __syncthreads();
     const uint32_t* skp = tkey + g0;
     const CI* sop = out_col + g0;
+    auto key_at = [&](long long e) -> uint32_t {
+      return sbuf == BUF_TEMP ? ld_stream(skp + e) : uint32_t(ld_stream(sop + e));
+    };
+    uint32_t lo;
+    int wb, nbl;
+    if constexpr (S::kStaged) {
+      lo = he.lo;
+      wb = he.wb;
+      nbl = wb < S::NBL ? wb : S::NBL;
+      static_assert(32 - S::NBL - SplitFine::NBL <= SS_RUN_LOG, "round-2 buckets fit a run");
+    } else {
+      // the bucket's own key range
+      uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+      for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
+        uint32_t k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + (long long)u * B < L) k[u] = key_at(e0 + (long long)u * B);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + (long long)u * B < L) {
+            mn = k[u] < mn ? k[u] : mn;
+            mx = k[u] > mx ? k[u] : mx;
+          }
+      }
+      mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+      mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+      if ((t & 31) == 0) {
+        tmp32[t >> 5] = mn;
+        hist[t >> 5] = mx;  // hist is cleared below
+      }
+      __syncthreads();
+      mn = 0xFFFFFFFFu;
+      mx = 0u;
+      for (int w = 0; w < B / 32; ++w) {
+        mn = tmp32[w] < mn ? tmp32[w] : mn;
+        mx = hist[w] > mx ? hist[w] : mx;
+      }
+      __syncthreads();
+      lo = mn;
+      const uint32_t span = mx >= mn ? mx - mn : 0u;  // keys in [lo, lo + span]
+      wb = span ? 32 - __clz(span) : 0;                // 2^wb > span
+      nbl = wb < S::NBL ? wb : S::NBL;
+    }
+    const int nb = 1 << nbl;
+    const int sh = wb - nbl;
+    const uint32_t rmax = wb >= 32 ? 0xFFFFFFFFu : (1u << wb) - 1u;  // largest offset from lo
+    // bucket of key k, or 0xFFFFFFFF for a key outside the run's range (a column outside
+    // [0, ncols): reported by pass 1)
+    auto bucket = [&](uint32_t k) -> uint32_t {
+      if (k < lo || k - lo > rmax) return 0xFFFFFFFFu;
+      return (k - lo) >> sh;
+    };
+    for (int x = t; x < NBM; x += B) hist[x] = 0;
+    __syncthreads();
     // pass 1: bucket sizes
     for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
       uint32_t k[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const long long e = e0 + (long long)u * B;
-        if (e < L) k[u] = sbuf == BUF_TEMP ? ld_stream(skp + e) : uint32_t(ld_stream(sop + e));
+        if (e < L) k[u] = key_at(e);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const long long e = e0 + (long long)u * B;
         if (e >= L) continue;
-        const uint32_t bk = (k[u] - lo) >> sh;
-        if (k[u] >= lo && bk < uint32_t(nb)) atomicAdd(&hist[bk], 1u);
+        const uint32_t bk = bucket(k[u]);
+        if (bk != 0xFFFFFFFFu) atomicAdd(&hist[bk], 1u);
         else dev_fail(st, SP_ERR_INDEX_RANGE, g0 + e);  // a column outside [0, ncols)
       }
     }
     __syncthreads();
-    const uint32_t total = smem_excl_sum_w<B>(hist, SPLIT_NB, tmp32);
+    const uint32_t total = smem_excl_sum_w<B>(hist, NBM, tmp32);
     if (total != uint32_t(L)) {
       if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -5);
       continue;
@@ -387,9 +485,9 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 2)
     // bucket x holds [hist[x], end(x)); bucket order is key order
     auto bend = [&](int x) { return x + 1 < nb ? hist[x + 1] : uint32_t(L); };
     // previous non-empty bucket (inclusive max-scan of x+1 over non-empty buckets)
-    for (int x = t; x < SPLIT_NB; x += B) prv[x] = (x < nb && bend(x) > hist[x]) ? uint32_t(x + 1) : 0u;
+    for (int x = t; x < NBM; x += B) prv[x] = (x < nb && bend(x) > hist[x]) ? uint32_t(x + 1) : 0u;
     __syncthreads();
-    smem_incl_max_w<B>(prv, SPLIT_NB, tmp32);
+    smem_incl_max_w<B>(prv, NBM, tmp32);
     // Groups: a bucket of more than GROUP_CAP entries ("big") stands alone; a small
     // non-empty bucket starts a new group ("head") unless the previous non-empty
     // bucket is small and starts in the same GROUP_CAP window.
@@ -409,13 +507,15 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 2)
     };
     // next group boundary after each bucket: suffix min of boundary starts, as a prefix
     // max over the reversed array of (L - start)
-    for (int x = t; x < SPLIT_NB; x += B) {
+    for (int x = t; x < NBM; x += B) {
       bool big, head;
       kind(x, big, head);
-      nxb[SPLIT_NB - 1 - x] = (big || head) ? uint32_t(L) - hist[x] : 0u;
+      nxb[NBM - 1 - x] = (big || head) ? uint32_t(L) - hist[x] : 0u;
+      if constexpr (S::kStaged) hd[x] = (big || head) ? uint32_t(x + 1) : 0u;
     }
     __syncthreads();
-    smem_incl_max_w<B>(nxb, SPLIT_NB, tmp32);
+    smem_incl_max_w<B>(nxb, NBM, tmp32);
+    if constexpr (S::kStaged) smem_incl_max_w<B>(hd, NBM, tmp32);  // group of each bucket
     for (int x = t; x < nb; x += B) {
       bool big, head;
       kind(x, big, head);
@@ -426,13 +526,13 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 2)
           if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, cc, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -6);
         } else {
-          const unsigned q = atomicAdd(nxt_n, 1u);
-          if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb, cc, lo + (uint32_t(x) << sh), sh, dbuf, 0};
+          const unsigned q = atomicAdd(nxt_n, 1u);  // round 2 finds its key range itself
+          if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb, cc, 0u, 0, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -7);
         }
       } else if (head) {
         // reversed index of x+1 holds max over buckets >= x+1 of (L - start) -> min start
-        const uint32_t nx = (x + 1 < SPLIT_NB) ? nxb[SPLIT_NB - 1 - (x + 1)] : 0u;
+        const uint32_t nx = (x + 1 < NBM) ? nxb[NBM - 1 - (x + 1)] : 0u;
         const uint32_t end = nx ? uint32_t(L) - nx : uint32_t(L);
         const unsigned q = atomicAdd(fin_n, 1u);
         if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, (long long)(end - sb), dbuf, 0};
@@ -440,61 +540,104 @@ __global__ void __launch_bounds__(SPLIT_BLOCK, 2)
       }
     }
     __syncthreads();
-    // pass 2: scatter bucket by bucket (hist now serves as the bucket cursors)
+    // pass 2 (hist now serves as the bucket cursors)
     const VT* svp = sbuf == BUF_TEMP ? tval + g0 : out_val + g0;
-    for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
-      uint32_t k[U];
-      VT v[U];
+    if constexpr (S::kStaged) {
+      // chunk by chunk: rank every entry within its group's share of the chunk, stage the
+      // chunk by group, then write each share to the group's next free range
+      constexpr int CH = B * U;
+      for (long long c0 = 0; c0 < L; c0 += CH) {
+        const int n = L - c0 < CH ? int(L - c0) : CH;
+        for (int x = t; x < NBM; x += B) lh[x] = 0;
+        __syncthreads();
+        uint32_t k[U], pk[U];  // key; group << 16 | rank in the group's share (CH <= 2^16)
+        VT v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long e = e0 + (long long)u * B;
-        if (e < L) k[u] = sbuf == BUF_TEMP ? ld_stream(skp + e) : uint32_t(ld_stream(sop + e));
+        for (int u = 0; u < U; ++u) {
+          const int e = t + u * B;
+          if (e < n) k[u] = key_at(c0 + e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = t + u * B;
+          if (e < n) v[u] = ld_stream(svp + c0 + e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = t + u * B;
+          pk[u] = 0xFFFFFFFFu;
+          if (e >= n) continue;
+          const uint32_t bk = bucket(k[u]);
+          if (bk == 0xFFFFFFFFu) continue;
+          const uint32_t g = hd[bk] - 1u;  // every non-empty bucket lies in a group
+          pk[u] = (g << 16) | atomicAdd(&lh[g], 1u);
+        }
+        __syncthreads();
+        for (int x = t; x < nb; x += B) {
+          gb[x] = hist[x];
+          hist[x] += lh[x];
+        }
+        const uint32_t nst = smem_excl_sum_w<B>(lh, NBM, tmp32);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (pk[u] == 0xFFFFFFFFu) continue;
+          const uint32_t q = lh[pk[u] >> 16] + (pk[u] & 0xFFFFu);
+          sk[q] = k[u];
+          sv[q] = v[u];
+        }
+        __syncthreads();
+        for (int i = t; i < int(nst); i += B) {
+          const uint32_t key = sk[i], g = hd[bucket(key)] - 1u;
+          const uint32_t q = gb[g] + (uint32_t(i) - lh[g]);
+          if (q >= uint32_t(L)) continue;
+          if (dbuf == BUF_TEMP) {
+            st_stream(tkey + g0 + q, key);
+            st_stream(tval + g0 + q, sv[i]);
+          } else {
+            st_stream(out_col + g0 + q, CI(key));
+            st_stream(out_val + g0 + q, sv[i]);
+          }
+        }
+        __syncthreads();
       }
+    } else {
+      // scatter entry by entry
+      for (long long e0 = t; e0 < L; e0 += (long long)B * U) {
+        uint32_t k[U];
+        VT v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long e = e0 + (long long)u * B;
-        if (e < L) v[u] = ld_stream(svp + e);
-      }
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + (long long)u * B;
+          if (e < L) k[u] = key_at(e);
+        }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long e = e0 + (long long)u * B;
-        if (e >= L) continue;
-        const uint32_t bk = (k[u] - lo) >> sh;
-        if (k[u] < lo || bk >= uint32_t(nb)) continue;
-        const uint32_t q = atomicAdd(&hist[bk], 1u);
-        if (q >= uint32_t(L)) continue;
-        if (dbuf == BUF_TEMP) {
-          st_stream(tkey + g0 + q, k[u]);
-          st_stream(tval + g0 + q, v[u]);
-        } else {
-          st_stream(out_col + g0 + q, CI(k[u]));
-          st_stream(out_val + g0 + q, v[u]);
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + (long long)u * B;
+          if (e < L) v[u] = ld_stream(svp + e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long e = e0 + (long long)u * B;
+          if (e >= L) continue;
+          const uint32_t bk = bucket(k[u]);
+          if (bk == 0xFFFFFFFFu) continue;
+          const uint32_t q = atomicAdd(&hist[bk], 1u);
+          if (q >= uint32_t(L)) continue;
+          if (dbuf == BUF_TEMP) {
+            st_stream(tkey + g0 + q, k[u]);
+            st_stream(tval + g0 + q, v[u]);
+          } else {
+            st_stream(out_col + g0 + q, CI(k[u]));
+            st_stream(out_val + g0 + q, v[u]);
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 // ---- phase 2: in-place sort of output rows ---------------------------------------------
-// Bucket of key k in a row of L entries: nb = 2^(ceil(log2 L) - 1) buckets spaced evenly
-// in an approximate square root of k over the row's key range [0, kmax].  The root is
-// the exponent-halving bit trick on the float of k (exact at even powers of two, up to
-// 6% high in between): monotone in k (every step is), so buckets stay in key order; the
-// scale nb / root(kmax) maps [0, kmax] onto the nb buckets.  The square root keeps
-// buckets balanced both for uniformly relabelled columns and for labels crowded at the
-// low end (degree-descending orderings).
-__device__ __forceinline__ uint32_t ss_nb(uint32_t L) { return L <= 2 ? 1u : 1u << (31 - __clz(L - 1)); }
-__device__ __forceinline__ float ss_root(uint32_t k) {
-  return __uint_as_float((__float_as_uint(__uint2float_rn(k)) >> 1) + 0x1FC00000u);
-}
-// 1 / root(kmax): the scale of a range [0, kmax] is nb * ss_inv_root(kmax)
-__device__ __forceinline__ float ss_inv_root(uint32_t kmax) { return kmax ? 1.0f / ss_root(kmax) : 0.0f; }
-// bucket of `key` given the row's scale and last bucket nb - 1
-__device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_t last) {
-  const uint32_t b = __float2uint_rz(ss_root(key) * scale);
-  return b < last ? b : last;
-}
 
 template <class Cfg, class VT>
 __host__ __device__ constexpr size_t ss_smem_bytes() {
@@ -909,27 +1052,25 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   if (!sort) return SP_OK;
   VT* tval = static_cast<VT*>(w.tval);
   if (nnz > SS_RUN_MAX) {
-    constexpr size_t hsm = split_smem_bytes();
-    static bool once_h = (set_smem(k_split<CI, VT>, hsm), true);
+    constexpr size_t csm = split_smem_bytes<SplitCoarse, VT>(), fsm = split_smem_bytes<SplitFine, VT>();
+    static bool once_h = (set_smem(k_split<SplitCoarse, CI, VT>, csm), set_smem(k_split<SplitFine, CI, VT>, fsm), true);
     (void)once_h;
     {
       SP_PHASE(SP_PHASE_HUGE);
-      k_split<CI, VT><<<2 * nsm, SPLIT_BLOCK, hsm, s>>>(w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval,
-                                                    out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt, nxt_n,
-                                                    w.nxt_cap, ctx->dstatus);
+      k_split<SplitCoarse, CI, VT><<<SplitCoarse::MINB * nsm, SplitCoarse::B, csm, s>>>(
+          w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval, out_col, out_val, w.fin, fin_n, w.fin_cap,
+          w.nxt, nxt_n, w.nxt_cap, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
-    // a second round only when a bucket of the first (2^(key_bits - SPLIT_NB_LOG) keys)
-    // can hold more than SS_RUN_MAX entries
-    if ((1ll << (key_bits > SPLIT_NB_LOG ? key_bits - SPLIT_NB_LOG : 0)) > SS_RUN_MAX) {
-      {
-        SP_PHASE(SP_PHASE_HUGE);
-        k_split<CI, VT><<<2 * nsm, SPLIT_BLOCK, hsm, s>>>(w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval,
-                                                      out_col, out_val, w.fin, fin_n, w.fin_cap, w.nxt,
-                                                      w.counters + 5, 0, ctx->dstatus);
-      }
-      SP_CUDA(cudaGetLastError());
+    // round 2: the buckets of round 1 that hold more than SS_RUN_MAX entries (skewed keys
+    // or very long rows); an empty list costs one short launch
+    {
+      SP_PHASE(SP_PHASE_HUGE);
+      k_split<SplitFine, CI, VT><<<SplitFine::MINB * nsm, SplitFine::B, fsm, s>>>(
+          w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval, out_col, out_val, w.fin, fin_n, w.fin_cap,
+          w.nxt, w.counters + 5, 0, ctx->dstatus);
     }
+    SP_CUDA(cudaGetLastError());
   }
   // tiles, then the runs, then the heavy buckets queued by either
   const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);

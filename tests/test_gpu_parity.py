@@ -152,9 +152,11 @@ def test_row_length_boundaries(ctx):
     assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "boundaries")
 
 
-def test_skewed_keys_long_row(ctx):
-    """Keys packed into a narrow range with outliers (forces several refine rounds)."""
-    n = 1 << 22
+@pytest.mark.parametrize("n", [1 << 22, 1 << 24])
+def test_skewed_keys_long_row(ctx, n):
+    """Keys packed into a narrow range with outliers: heavy buckets in the row sort and,
+    at 2^24 columns, a key-range bucket of the split holding more than 4096 entries (the
+    second split round, over the bucket's own key range)."""
     L = 6000
     g = torch.Generator().manual_seed(5)
     dense = torch.randperm(5000, generator=g)[:L - 200]
