@@ -37,11 +37,15 @@ WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16
             "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
 
 # DRAM bytes (read + write) of one launch of a kernel on the first P A P^T (random p)
-# of the workload at a given R-MAT scale, from a one-pass ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum at that size
-# (profiles/dram_permute_rmat25.md).  Only valid for the kernels as captured: retake
+# of the workload at a given R-MAT scale, from an ncu capture of only
+# dram__bytes_read.sum + dram__bytes_write.sum (and the duration) at that size
+# (profiles/launches_permute_rmat25.md).  Only valid for the kernels as captured: retake
 # the capture when one changes; other scales report null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    (25, "gather"): 26_446_941_184,
+    (25, "tile"): 7_057_768_192,
+    (25, "huge"): 4_478_052_864,  # both split rounds (the second is empty for random keys)
+}
 
 
 _T0 = time.time()
