@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
   __shared__ long long r_o1[B];
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ long long s_last;  // output end of the batch's last row
+  __shared__ int s_single;      // the batch's first row covers the whole chunk
   const int t = threadIdx.x;
   // row r's output range [o0, o1) and source start
   auto setup = [&](long long r, long long& a, long long& b, long long& s) {
@@ -250,12 +251,17 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
       r_o1[t] = o1;
     }
     if (t == B - 1) s_last = o1;
+    if (t == 0) s_single = active && o0 <= c0 && o1 >= c1;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) owner[t + j * B] = 0;
     __syncthreads();
-    if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint32_t(t + 1);
-    __syncthreads();
-    smem_incl_max_w<B>(owner, GC_CH, tmp32);
+    // a chunk inside one long row (most of a long row's chunks) needs no owner search
+    const bool single = s_single;
+    if (!single) {
+      if (active) owner[(o0 > c0 ? o0 : c0) - c0] = uint32_t(t + 1);
+      __syncthreads();
+      smem_incl_max_w<B>(owner, GC_CH, tmp32);
+    }
     // the chunk ends with this batch once its last row reaches the end of the chunk
     const bool last_batch = rb + B - 1 >= nrows - 1 || s_last >= c1;
     const bool more = !last_batch || cn < nchunks;
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
       for (int u = 0; u < H; ++u) {
         const int x = t + (h + u) * B;
         const long long g = c0 + x;
-        const int ow = int(owner[x]);
+        const int ow = single ? 1 : int(owner[x]);
         ok[u] = false;
         pos[u] = 0;
         if (g < c1 && ow > 0) {
