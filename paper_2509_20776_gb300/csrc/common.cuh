@@ -87,6 +87,15 @@ __device__ __forceinline__ void st_stream(T* p, T v) {
   }
 }
 
+// Asynchronous global -> shared copy of one 8-byte word; commit closes the thread's
+// group of copies, wait_all waits for all of the thread's groups.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ---- relaxed 64-bit status words (decoupled look-back) -------------------------
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;

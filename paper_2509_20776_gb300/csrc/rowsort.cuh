@@ -707,6 +707,8 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
   uint16_t* rnm = rps + ROWS;         // per row: last bucket
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ uint32_t s_min, s_max;
+  // tiles: row pointers vp[r0 .. r1] of the next tile, copied in while this one is sorted
+  __shared__ long long pre_o[Cfg::kTiles ? ROWS + 1 : 1];
   const int t = threadIdx.x;
   const uint32_t kmax = key_bits >= 32 ? 0xFFFFFFFFu : (1u << key_bits) - 1u;
   const float isr = ss_inv_root(kmax);
@@ -722,10 +724,20 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
   // the current item's sort
   long long pf0 = 0, pf1 = 0;  // tiles: row range
   FinalEntry pfe{0, 0, 0, 0};  // runs
+  // tiles: start copying the row pointers of the tile whose range is in (pf0, pf1)
+  auto prefetch_rows = [&](bool any) {
+    if (any) {
+      long long n = pf1 - pf0;
+      n = n < 0 ? 0 : (n < ROWS ? n : ROWS);
+      for (int x = t; x <= n; x += B) cp_async8(pre_o + x, vp + pf0 + x);
+    }
+    cp_async_commit();
+  };
   if (blockIdx.x < nitems) {
     if constexpr (Cfg::kTiles) {
       pf0 = tile_first[blockIdx.x];
       pf1 = tile_first[blockIdx.x + 1];
+      prefetch_rows(true);
     } else {
       pfe = fin[blockIdx.x];
     }
@@ -750,14 +762,16 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
         pf0 = tile_first[nx];
         pf1 = tile_first[nx + 1];
       }
-      base = vp[r0];
+      cp_async_wait_all();  // this tile's row pointers
+      __syncthreads();
+      base = pre_o[0];
       if (r1 - r0 > ROWS) {  // cannot happen: see RowsPartition
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -17);
         r1 = r0;
       }
       if (t < r1 - r0) {
-        o0 = vp[r0 + t];
-        const long long L = vp[r0 + t + 1] - o0;
+        o0 = pre_o[t];
+        const long long L = pre_o[t + 1] - o0;
         if (L > 0 && L <= Cfg::CP) {
           if (o0 - base > 0xFFFFFFFFll - CAP) dev_fail(st, SP_ERR_OVERFLOW, r0 + t);
           else myL = uint32_t(L);
@@ -769,6 +783,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
       E = int(tot >> 16);  // <= 2 * Cfg::CP by the partition
       if (E > CAP) {       // cannot happen: see RowsPartition
         if (t == 0) dev_fail(st, SP_ERR_INTERNAL, -19);
+        prefetch_rows(nx < nitems);  // every thread has read pre_o (barriers above)
         __syncthreads();
         continue;
       }
@@ -799,6 +814,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
         }
       }
       __syncthreads();
+      prefetch_rows(nx < nitems);  // the next tile's row pointers arrive during this sort
     } else {
       const FinalEntry fe = pfe;
       if (nx < nitems) pfe = fin[nx];
