@@ -66,7 +66,7 @@ struct HugeEntry {  // a run longer than SS_RUN_MAX, keys in [lo, lo + 2^wb)
 };
 
 constexpr int GC_BLOCK = 256;                  // gather: threads per CTA
-constexpr int GC_CH = 2048;                    // gather: output positions per CTA
+constexpr int GC_CH = 4096;                    // gather: output positions per CTA
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
 
 // ---- partition ----------------------------------------------------------------------
