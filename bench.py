@@ -575,13 +575,64 @@ def bench_batch(ctx, args, dev, ws):
     torch.cuda.synchronize()
     ms_plain = (time.perf_counter() - t0) * 1e3
     bt.close()
-    return {"workload": f"{len(mats)} R-MAT matrices (rows 2^10..2^22, ~12/row, {sum(m.nnz for m in mats)} "
-                        f"entries); {len(reqs)} extractions, |I|,|J| log-uniform in [16, 65536]",
-            "nnz_out": nnz, "same_nnz_as_plain": plain_nnz == nnz,
+    res = {"workload": f"{len(mats)} R-MAT matrices (rows 2^10..2^22, ~12/row, {sum(m.nnz for m in mats)} "
+                       f"entries); {len(reqs)} extractions, |I|,|J| log-uniform in [16, 65536]",
+           "nnz_out": nnz, "same_nnz_as_plain": plain_nnz == nnz,
+           "batched_ms": round(ms_batch, 3), "batched_value": round(nnz / (ms_batch * 1e-3), 1),
+           "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1),
+           "plain_ms": round(ms_plain, 3), "plain_value": round(nnz / (ms_plain * 1e-3), 1),
+           "unit": UNIT, "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2)}
+    res["autotuned"] = bench_batch_tuned(ctx, dms, reqs, nnz, steps, ws)
+    return res
+
+
+def bench_batch_tuned(ctx, dms, reqs, nnz, steps, ws):
+    """The autotuner on the batch itself (rows per warp, tile shape, heavy threshold;
+    every candidate's output compared with the default shapes' output), then the batch
+    and its graph-replayed fill again with the tuning table installed."""
+    import time
+    import torch
+    from paper_2509_20776_gb300 import autotune
+
+    def run():
+        b = ctx.extract_batch(dms, reqs)
+        o = b.alloc(torch.int64)
+        b.fill(o)
+        b.close()
+        return o
+
+    t0 = time.perf_counter()
+    table = autotune.autotune(ctx, [("batch", 1 << 62, run)], reps=3)
+    tune_s = time.perf_counter() - t0
+    ctx.set_tuning(table)
+    try:
+        bt = ctx.extract_batch(dms, reqs)
+        out = bt.alloc(torch.int64)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            bt.fill(out, s)
+        torch.cuda.current_stream().wait_stream(s)
+        ctx.sync()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            bt.fill(out, torch.cuda.current_stream())
+        ms_fill = time_steps(graph.replay, steps, 2, ws) / steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            run()
+            ctx.sync()
+        ms_batch = (time.perf_counter() - t0) * 1e3 / 3
+        same = bt.nnz == nnz
+        bt.close()
+    finally:
+        ctx.set_tuning(None)
+    e = table["entries"][0]
+    return {"shapes": {k: e[k] for k in autotune.KNOBS["batch"]}, "tune_s": round(tune_s, 2),
+            "tuner_ms_default": e["default_ms"], "tuner_ms_best": e["ms"], "same_nnz": same,
             "batched_ms": round(ms_batch, 3), "batched_value": round(nnz / (ms_batch * 1e-3), 1),
-            "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1),
-            "plain_ms": round(ms_plain, 3), "plain_value": round(nnz / (ms_plain * 1e-3), 1),
-            "unit": UNIT, "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2)}
+            "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1)}
 
 
 def bench_serve(ctx, args, dev, nreq=10000):

@@ -128,13 +128,46 @@ SP_API int64_t sp_ctx_error_detail(const sp_ctx* ctx);
  *                          the call reports SP_ERR_TIMEOUT (default -1 = off);
  *   SP_OPT_VALIDATE        1: every op first checks its input matrices are canonical
  *                          (SP_ERR_NOT_CANONICAL); default 0. */
+/* Kernel shapes (the autotuner's knobs; every value gives the same output, bit for bit):
+ *   SP_OPT_TILE_SHAPE      row sort of short rows: 0 = tiles of 1024 entries holding rows
+ *                          of at most 512, 128 threads, 8 CTAs per SM (default);
+ *                          1 = tiles of 2048 entries holding rows of at most 1024,
+ *                          256 threads, 4 CTAs per SM;
+ *   SP_OPT_HEAVY           a bucket of the row sort with more keys than this is written
+ *                          in bucket order and sorted by a later pass: 128 (default) to
+ *                          4096;
+ *   SP_OPT_COUNT_ROWS      rows a warp takes per step in the kept-entry count of
+ *                          extraction / assignment: 1 to 4 (default 4);
+ *   SP_OPT_FILL_ROWS       the same for their compacting fill: 1 or 2 (default 2);
+ *   SP_OPT_BATCH_ROWS      rows a warp serves at once in the batched extraction's count
+ *                          and fill (32 / rows lanes per row): 1 (default), 2, 4 or 8. */
 typedef enum sp_option {
   SP_OPT_SPIN_LIMIT = 0,
   SP_OPT_SCAN_HOLD_TILE = 1,
   SP_OPT_VALIDATE = 2,
-  SP_OPT_TIMING = 3 /* 1: bracket every kernel launch with CUDA events (see below) */
+  SP_OPT_TIMING = 3, /* 1: bracket every kernel launch with CUDA events (see below) */
+  SP_OPT_TILE_SHAPE = 4,
+  SP_OPT_HEAVY = 5,
+  SP_OPT_COUNT_ROWS = 6,
+  SP_OPT_FILL_ROWS = 7,
+  SP_OPT_BATCH_ROWS = 8
 } sp_option;
 SP_API sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value);
+
+/* Tuning table (written by the autotuner, paper_2509_20776_gb300/autotune.py).  Each
+ * call of an operation takes the first entry with its op whose size_max is at least the
+ * call's size, and uses that entry's kernel shapes (fields < 0 keep the context's
+ * option) for this call only.  Size: nnz(A) for permute / extract / assign (and the
+ * fused assign + permute), the total number of selected rows (sum of |I|) for a batch.
+ * The table is copied; n = 0 removes it.  Errors: SP_ERR_INVALID_ARG for a NULL ctx, a
+ * NULL table with n > 0, n < 0, an unknown op or an out-of-range shape value. */
+typedef enum sp_op { SP_OP_PERMUTE = 0, SP_OP_EXTRACT = 1, SP_OP_ASSIGN = 2, SP_OP_BATCH = 3 } sp_op;
+typedef struct sp_tune_entry {
+  int32_t op;        /* sp_op */
+  int32_t tile_shape, heavy, count_rows, fill_rows, batch_rows; /* as the options above */
+  int64_t size_max;  /* the entry covers calls of size <= size_max */
+} sp_tune_entry;
+SP_API sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n);
 
 /* Per-phase kernel statistics (tracing).  Every kernel the library launches belongs to
  * one phase; the context counts launches per phase always, and with SP_OPT_TIMING=1
@@ -147,10 +180,10 @@ typedef enum sp_phase {
   SP_PHASE_COUNT = 1,     /* kept-entry counting passes */
   SP_PHASE_SCAN = 2,      /* exclusive scans (row pointers) */
   SP_PHASE_PARTITION = 3, /* tile partition / row classification */
-  SP_PHASE_TILE = 4,      /* gather + relabel + sort of short rows, many per CTA */
-  SP_PHASE_LONG = 5,      /* rows / runs of up to 8192 entries, one CTA each */
-  SP_PHASE_HUGE = 6,      /* key-range partition of longer rows */
-  SP_PHASE_GATHER = 7,    /* load-balanced row copy (identity map, assignment assembly) */
+  SP_PHASE_TILE = 4,      /* in-place sort of short rows, many per CTA */
+  SP_PHASE_LONG = 5,      /* in-place sort of rows / runs of up to 4096 entries, one CTA each */
+  SP_PHASE_HUGE = 6,      /* key-range split of longer rows into runs */
+  SP_PHASE_GATHER = 7,    /* load-balanced row gather / compacting fill into the output */
   SP_PHASE_OTHER = 8,     /* row-pointer width conversion, validation */
   SP_NUM_PHASES = 9
 } sp_phase;

@@ -20,6 +20,13 @@ SP_I32, SP_I64 = 0, 1
 SP_F32, SP_F64 = 0, 1
 SP_ASSIGN_REPLACE, SP_ASSIGN_SELECT2ND, SP_ASSIGN_PLUS = 0, 1, 2
 SP_OPT_SPIN_LIMIT, SP_OPT_SCAN_HOLD_TILE, SP_OPT_VALIDATE, SP_OPT_TIMING = 0, 1, 2, 3
+# kernel shapes (run-time; every value gives the same output)
+SP_OPT_TILE_SHAPE, SP_OPT_HEAVY, SP_OPT_COUNT_ROWS, SP_OPT_FILL_ROWS, SP_OPT_BATCH_ROWS = 4, 5, 6, 7, 8
+SHAPE_OPTIONS = {"tile_shape": SP_OPT_TILE_SHAPE, "heavy": SP_OPT_HEAVY, "count_rows": SP_OPT_COUNT_ROWS,
+                 "fill_rows": SP_OPT_FILL_ROWS, "batch_rows": SP_OPT_BATCH_ROWS}
+SHAPE_VALUES = {"tile_shape": (0, 1), "heavy": (128, 256, 512, 1024, 2048, 4096), "count_rows": (1, 2, 3, 4),
+                "fill_rows": (1, 2), "batch_rows": (1, 2, 4, 8)}
+OPS = {"permute": 0, "extract": 1, "assign": 2, "batch": 3}
 PHASES = ["map", "count", "scan", "partition", "tile", "long", "huge", "gather", "other"]
 STATUS = ["SP_OK", "SP_ERR_INVALID_ARG", "SP_ERR_SHAPE", "SP_ERR_INDEX_RANGE",
           "SP_ERR_DUPLICATE_INDEX", "SP_ERR_NOT_PERMUTATION", "SP_ERR_NOT_CANONICAL",
@@ -42,6 +49,34 @@ class sp_csr(ctypes.Structure):
                 ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
+class sp_tune_entry(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("heavy", ctypes.c_int32),
+                ("count_rows", ctypes.c_int32), ("fill_rows", ctypes.c_int32), ("batch_rows", ctypes.c_int32),
+                ("size_max", ctypes.c_int64)]
+
+
+def tune_entries(table) -> list:
+    """Validated tuning entries from a table (the autotuner's JSON object, or its list of
+    entries): dicts with "op" (permute / extract / assign / batch), "size_max" and any of
+    the shape names; absent shapes are -1 (keep the context's option).  Entries come out
+    ordered by (op, size_max), so the first entry that covers a call is its tightest
+    size class."""
+    items = table["entries"] if isinstance(table, dict) else table
+    out = []
+    for e in items:
+        if e["op"] not in OPS:
+            raise ValueError(f"unknown op {e['op']!r}")
+        row = {"op": OPS[e["op"]], "size_max": int(e["size_max"])}
+        for k, allowed in SHAPE_VALUES.items():
+            v = int(e.get(k, -1))
+            if v >= 0 and v not in allowed:
+                raise ValueError(f"{k}={v} not in {allowed}")
+            row[k] = v
+        out.append(row)
+    out.sort(key=lambda r: (r["op"], r["size_max"]))
+    return out
+
+
 class sp_extract_req(ctypes.Structure):
     _fields_ = [("mat", ctypes.c_int64), ("nI", ctypes.c_int64), ("nJ", ctypes.c_int64),
                 ("I", ctypes.c_void_p), ("J", ctypes.c_void_p)]
@@ -60,6 +95,7 @@ SIGNATURES = {
     "sp_ctx_sync": (_int, [_vp, _vp]),
     "sp_ctx_error_detail": (_i64, [_vp]),
     "sp_ctx_set_option": (_int, [_vp, _int, _i64]),
+    "sp_ctx_set_tuning": (_int, [_vp, ctypes.POINTER(sp_tune_entry), _int]),
     "sp_permute": (_int, [_vp, _PCSR, _vp, _vp, _int, _PCSR, _vp]),
     "sp_extract_count": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(_vp),
                                 ctypes.POINTER(_i64), _vp]),
@@ -189,6 +225,26 @@ class Context:
 
     def set_option(self, key: int, value: int):
         self._check(self.lib.sp_ctx_set_option(self.handle, key, value), "sp_ctx_set_option")
+
+    def set_shapes(self, **shapes):
+        """Context-wide kernel shapes by name (tile_shape, heavy, count_rows, fill_rows,
+        batch_rows); -1 restores a default."""
+        for k, v in shapes.items():
+            self.set_option(SHAPE_OPTIONS[k], int(v))
+
+    def set_tuning(self, table):
+        """Installs a tuning table (see ``tune_entries``; a path to the autotuner's JSON
+        file also works); None or [] removes it."""
+        if isinstance(table, str):
+            import json
+            with open(table) as f:
+                table = json.load(f)
+        rows = tune_entries(table) if table else []
+        arr = (sp_tune_entry * max(1, len(rows)))()
+        for i, r in enumerate(rows):
+            arr[i] = sp_tune_entry(r["op"], r["tile_shape"], r["heavy"], r["count_rows"], r["fill_rows"],
+                                   r["batch_rows"], r["size_max"])
+        self._check(self.lib.sp_ctx_set_tuning(self.handle, arr, len(rows)), "sp_ctx_set_tuning")
 
     def phase_stats(self, reset: bool = False) -> dict:
         """{phase: (device ms, kernel launches)} accumulated since the last reset."""

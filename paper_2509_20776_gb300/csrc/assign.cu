@@ -291,7 +291,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     auto count = [&](const auto& ct) -> sp_status {
       {
         SP_PHASE(SP_PHASE_COUNT);
-        k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+        k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->cur.count_rows,
+                                                                         ctx->dstatus);
       }
       SP_CUDA(cudaGetLastError());
       {
@@ -338,7 +339,8 @@ sp_status assign_stage(sp_ctx* ctx, sp_plan* pl, CI* tcol, VT* tval, unsigned* t
   auto fill = [&](const auto& ld) -> sp_status {
     {
       SP_PHASE(SP_PHASE_GATHER);
-      k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->dstatus);
+      k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, tcol, tval, ctx->cur.fill_rows,
+                                                                        ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
     {
@@ -368,7 +370,6 @@ sp_status assign_stage(sp_ctx* ctx, sp_plan* pl, CI* tcol, VT* tval, unsigned* t
 template <class RP, class CI, class VT, class IX>
 sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s) {
   const sp_csr& A = pl->A;
-  const sp_csr& B = pl->B;
   const long long m = A.nrows, nI = pl->nI, nt = pl->nnz_temp, nnz_out = pl->nnz_out;
   SP_TRY(store_rowptr(ctx, s, pl->vp_out, m + 1, Ap->rowptr_type, Ap->rowptr));
   if (nnz_out == 0) return SP_OK;
@@ -384,7 +385,6 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   cv.bind(base);
   CI* tcol = cv.at<CI>(o_tc);
   VT* tval = cv.at<VT>(o_tv);
-  const int nsm = ctx->num_sms;
   if (nt > 0) {
     // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
     SP_TRY((assign_stage<RP, CI, VT, IX>(ctx, pl, tcol, tval, cv.at<unsigned>(o_tk), s)));
@@ -551,6 +551,7 @@ extern "C" sp_status sp_assign_count(sp_ctx* ctx, const sp_csr* A, const void* I
   if (A->ncols > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_ASSIGN, A->nnz);
   SP_TRY(validate_if_asked(ctx, A, s));
   SP_TRY(validate_if_asked(ctx, B, s));
   sp_plan* pl = new sp_plan();
@@ -589,6 +590,7 @@ extern "C" sp_status sp_assign_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, sp_str
   if (Ap->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_ASSIGN, pl->A.nnz);
   pl->stream = s;
   Ap->nrows = pl->A.nrows;
   Ap->ncols = pl->A.ncols;
@@ -631,6 +633,7 @@ extern "C" sp_status sp_assign_permute_fill(sp_ctx* ctx, sp_plan* pl, const void
   if (out->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_ASSIGN, pl->A.nnz);
   pl->stream = s;
   const sp_csr& A = pl->A;
   out->nrows = A.nrows;

@@ -95,53 +95,64 @@ __global__ void k_batch_jdup(const long long* __restrict__ joff, long long nreq,
   }
 }
 
-// One warp per output row (global index r over the batch): the selected source row,
-// each stored column looked up in the request's sorted J.  PASS 0 counts the kept
-// entries into vp[r]; PASS 1 writes them (position in J as the column, ballot slots,
-// source order) at the row pointer vp.
+// rpw output rows per warp (global index r over the batch; 1, 2, 4 or 8, a run-time
+// kernel shape), each served by a group of 32 / rpw lanes: the selected source row, each
+// stored column looked up in the request's sorted J.  PASS 0 counts the kept entries
+// into vp[r]; PASS 1 writes them (position in J as the column, ballot slots within the
+// lane group, source order) at the row pointer vp.
 template <int PASS, class RP, class CI, class VT, class IX>
 __global__ void k_batch_rows(const BatchReq* __restrict__ reqs, const BatchMat* __restrict__ mats,
                              const long long* __restrict__ roff, long long nreq, long long rows,
                              const IX* __restrict__ jkey, const uint32_t* __restrict__ jpos,
                              long long* __restrict__ vp, CI* __restrict__ out_col, VT* __restrict__ out_val,
-                             DevStatus* st) {
+                             int rpw, DevStatus* st) {
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
+  const int G = 32 / rpw, grp = lane / G, gl = lane - grp * G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (grp * G);
+  const unsigned lt = ((1u << gl) - 1u) << (grp * G);  // lanes of the group below this one
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long r = w0; r < rows; r += nw) {
-    const long long k = batch_req_of(roff, nreq, r);
-    const BatchReq q = reqs[k];
-    const BatchMat a = mats[q.mat];
-    const long long src = (long long)static_cast<const IX*>(q.I)[r - q.roff];
-    long long s = 0, e = 0;
-    if (src < 0 || src >= a.nrows) {
-      if (lane == 0 && PASS == 0) dev_fail(st, SP_ERR_INDEX_RANGE, r);
-    } else {
-      const RP* rp = static_cast<const RP*>(a.rowptr);
-      s = (long long)rp[src];
-      e = (long long)rp[src + 1];
-      if (s < 0 || e < s || e > a.nnz) s = e = 0;
+  for (long long rb = w0 * rpw; rb < rows; rb += nw * rpw) {  // warp-uniform
+    const long long r = rb + grp;
+    long long s = 0, e = 0, nJ = 0, joff = 0;
+    const CI* col = nullptr;
+    const VT* val = nullptr;
+    if (r < rows) {
+      const long long k = batch_req_of(roff, nreq, r);
+      const BatchReq q = reqs[k];
+      const BatchMat a = mats[q.mat];
+      const long long src = (long long)static_cast<const IX*>(q.I)[r - q.roff];
+      if (src < 0 || src >= a.nrows) {
+        if (gl == 0 && PASS == 0) dev_fail(st, SP_ERR_INDEX_RANGE, r);
+      } else {
+        const RP* rp = static_cast<const RP*>(a.rowptr);
+        s = (long long)rp[src];
+        e = (long long)rp[src + 1];
+        if (s < 0 || e < s || e > a.nnz) s = e = 0;
+      }
+      col = static_cast<const CI*>(a.colidx);
+      val = static_cast<const VT*>(a.values);
+      nJ = q.nJ;
+      joff = q.joff;
     }
-    const CI* col = static_cast<const CI*>(a.colidx);
-    const VT* val = static_cast<const VT*>(a.values);
-    const IX* jk = jkey + q.joff;
-    long long o = PASS ? vp[r] : 0;
-    const long long oe = PASS ? vp[r + 1] : 0;
-    for (long long k0 = s; k0 < e; k0 += 32) {
-      const long long x = k0 + lane;
+    const IX* jk = jkey + joff;
+    long long o = PASS && r < rows ? vp[r] : 0;
+    const long long oe = PASS && r < rows ? vp[r + 1] : 0;
+    // every lane steps until all groups of the warp are done (the ballots need them all)
+    for (long long k0 = s; __any_sync(0xffffffffu, k0 < e); k0 += G) {
+      const long long x = k0 + gl;
       bool kept = false;
       long long hit = 0;
       if (x < e) {
         const long long c = (long long)ld_stream(col + x);
-        hit = lower_bound_col(jk, 0, q.nJ, c);
-        kept = hit < q.nJ && (long long)jk[hit] == c;
+        hit = lower_bound_col(jk, 0, nJ, c);
+        kept = hit < nJ && (long long)jk[hit] == c;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, kept);
+      const unsigned m = __ballot_sync(0xffffffffu, kept) & gmask;
       if (PASS == 1 && kept) {
         const long long pos = o + __popc(m & lt);
         if (pos < oe) {
-          st_stream(out_col + pos, CI(jpos[q.joff + hit]));
+          st_stream(out_col + pos, CI(jpos[joff + hit]));
           st_stream(out_val + pos, ld_stream(val + x));
         } else {
           dev_fail(st, SP_ERR_INTERNAL, -25);
@@ -149,7 +160,7 @@ __global__ void k_batch_rows(const BatchReq* __restrict__ reqs, const BatchMat* 
       }
       o += __popc(m);
     }
-    if (PASS == 0 && lane == 0) vp[r] = o;
+    if (PASS == 0 && gl == 0 && r < rows) vp[r] = o;
   }
 }
 
@@ -211,8 +222,9 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   if (rows > 0) {
     {
       SP_PHASE(SP_PHASE_COUNT);
-      k_batch_rows<0, RP, CI, VT, IX><<<grid_for(rows * 32, 256, nsm * 16), 256, 0, s>>>(
-          b->reqs, b->mats, b->droff, nreq, rows, jkey, b->jpos, b->vp, nullptr, nullptr, ctx->dstatus);
+      const int rpw = ctx->cur.batch_rows;
+      k_batch_rows<0, RP, CI, VT, IX><<<grid_for((rows + rpw - 1) / rpw * 32, 256, nsm * 16), 256, 0, s>>>(
+          b->reqs, b->mats, b->droff, nreq, rows, jkey, b->jpos, b->vp, nullptr, nullptr, rpw, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
   }
@@ -252,8 +264,9 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
   VT* ov = static_cast<VT*>(out->values);
   {
     SP_PHASE(SP_PHASE_GATHER);
-    k_batch_rows<1, RP, CI, VT, IX><<<grid_for(rows * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
-        b->reqs, b->mats, b->droff, b->nreq, rows, static_cast<const IX*>(b->jkey), b->jpos, b->vp, oc, ov,
+    const int rpw = ctx->cur.batch_rows;
+    k_batch_rows<1, RP, CI, VT, IX><<<grid_for((rows + rpw - 1) / rpw * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
+        b->reqs, b->mats, b->droff, b->nreq, rows, static_cast<const IX*>(b->jkey), b->jpos, b->vp, oc, ov, rpw,
         ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
@@ -323,6 +336,7 @@ extern "C" sp_status sp_extract_batch_count(sp_ctx* ctx, const sp_csr* mats, int
   cudaStream_t s = (cudaStream_t)stream;
   b->stream = s;
   sp_status st = cudaSetDevice(ctx->device) == cudaSuccess ? SP_OK : SP_ERR_CUDA;
+  ctx_begin_call(ctx, SP_OP_BATCH, b->rows);
   if (st == SP_OK && nmats > 0) {
     st = dispatch_i(b->rowptr_type, [&](auto rp) {
       using RP = decltype(rp);
@@ -358,6 +372,7 @@ extern "C" sp_status sp_extract_batch_fill(sp_ctx* ctx, sp_batch* b, sp_csr* out
   out->nnz = b->nnz;
   if (b->nmats == 0) return SP_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  ctx_begin_call(ctx, SP_OP_BATCH, b->rows);
   return dispatch_i(b->rowptr_type, [&](auto rp) {
     using RP = decltype(rp);
     return dispatch_i(b->colidx_type, [&](auto ci) {

@@ -181,8 +181,43 @@ sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
     case SP_OPT_SCAN_HOLD_TILE: ctx->hold_tile = value < 0 ? -1 : value; return SP_OK;
     case SP_OPT_VALIDATE: ctx->validate = value > 0 ? 1 : 0; return SP_OK;
     case SP_OPT_TIMING: ctx->timing = value > 0 ? 1 : 0; return SP_OK;
+    case SP_OPT_TILE_SHAPE:
+      if (value > 1) return SP_ERR_INVALID_ARG;
+      ctx->opt.tile_shape = value < 0 ? 0 : int(value);
+      return SP_OK;
+    case SP_OPT_HEAVY:
+      if (value >= 0 && (value < 128 || value > 4096)) return SP_ERR_INVALID_ARG;
+      ctx->opt.heavy = value < 0 ? 128 : int(value);
+      return SP_OK;
+    case SP_OPT_COUNT_ROWS:
+      if (value == 0 || value > 4) return SP_ERR_INVALID_ARG;
+      ctx->opt.count_rows = value < 0 ? 4 : int(value);
+      return SP_OK;
+    case SP_OPT_FILL_ROWS:
+      if (value == 0 || value > 2) return SP_ERR_INVALID_ARG;
+      ctx->opt.fill_rows = value < 0 ? 2 : int(value);
+      return SP_OK;
+    case SP_OPT_BATCH_ROWS:
+      if (value >= 0 && value != 1 && value != 2 && value != 4 && value != 8) return SP_ERR_INVALID_ARG;
+      ctx->opt.batch_rows = value < 0 ? 1 : int(value);
+      return SP_OK;
   }
   return SP_ERR_INVALID_ARG;
+}
+
+sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n) {
+  if (!ctx || n < 0 || (n > 0 && !table)) return SP_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const sp_tune_entry& e = table[i];
+    const bool ok = e.op >= SP_OP_PERMUTE && e.op <= SP_OP_BATCH && e.tile_shape <= 1 &&
+                    (e.heavy < 0 || (e.heavy >= 128 && e.heavy <= 4096)) && e.count_rows != 0 &&
+                    e.count_rows <= 4 && e.fill_rows != 0 && e.fill_rows <= 2 &&
+                    (e.batch_rows < 0 || e.batch_rows == 1 || e.batch_rows == 2 || e.batch_rows == 4 ||
+                     e.batch_rows == 8);
+    if (!ok) return SP_ERR_INVALID_ARG;
+  }
+  ctx->tuning.assign(table, table + n);
+  return SP_OK;
 }
 
 sp_status sp_ctx_phase_stats(sp_ctx* ctx, double* ms, int64_t* launches, int reset) {

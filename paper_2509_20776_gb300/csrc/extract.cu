@@ -347,7 +347,8 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->sstart, pl->slen};
     {
       SP_PHASE(SP_PHASE_COUNT);
-      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->dstatus);
+      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->cur.count_rows,
+                                                                         ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
     {
@@ -421,7 +422,8 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   const int nsm = ctx->num_sms;
   {
     SP_PHASE(SP_PHASE_GATHER);
-    k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, oc, ov, ctx->dstatus);
+    k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, oc, ov, ctx->cur.fill_rows,
+                                                                      ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   {
@@ -474,6 +476,7 @@ extern "C" sp_status sp_extract_count(sp_ctx* ctx, const sp_csr* A, const void* 
   if (nJ > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_EXTRACT, A->nnz);
   SP_TRY(validate_if_asked(ctx, A, s));
   sp_plan* pl = new sp_plan();
   pl->op = 0;
@@ -509,6 +512,7 @@ extern "C" sp_status sp_extract_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* B, sp_str
   if (B->rowptr_type == SP_I32 && pl->nnz_out > INT32_MAX) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_EXTRACT, pl->A.nnz);
   pl->stream = s;
   B->nrows = pl->nI;
   B->ncols = pl->nJ;

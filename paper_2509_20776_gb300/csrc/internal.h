@@ -37,6 +37,13 @@ struct sp_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double phase_ms[SP_NUM_PHASES] = {};
   long long phase_launches[SP_NUM_PHASES] = {};
+  // kernel shapes: the context's options, the tuning table, and the values in force for
+  // the call being issued (options overridden by the table entry that covers the call)
+  struct Shapes {
+    int tile_shape = 0, heavy = 128, count_rows = 4, fill_rows = 2, batch_rows = 1;
+  };
+  Shapes opt, cur;
+  std::vector<sp_tune_entry> tuning;
 };
 
 namespace sp {
@@ -127,5 +134,21 @@ sp_status alloc_csr(sp_ctx* ctx, sp_csr* B, cudaStream_t s);
 
 // With SP_OPT_VALIDATE set, check A is canonical (synchronises); else SP_OK.
 sp_status validate_if_asked(sp_ctx* ctx, const sp_csr* A, cudaStream_t s);
+
+// Shapes for the call about to be issued: the context's options, overridden by the
+// first tuning-table entry of `op` that covers `size` (op < 0: no table lookup).
+inline void ctx_begin_call(sp_ctx* ctx, int op, long long size) {
+  ctx->cur = ctx->opt;
+  if (op < 0) return;
+  for (const sp_tune_entry& e : ctx->tuning) {
+    if (e.op != op || size > e.size_max) continue;
+    if (e.tile_shape >= 0) ctx->cur.tile_shape = e.tile_shape;
+    if (e.heavy >= 0) ctx->cur.heavy = e.heavy;
+    if (e.count_rows >= 0) ctx->cur.count_rows = e.count_rows;
+    if (e.fill_rows >= 0) ctx->cur.fill_rows = e.fill_rows;
+    if (e.batch_rows >= 0) ctx->cur.batch_rows = e.batch_rows;
+    return;
+  }
+}
 
 }  // namespace sp

@@ -124,14 +124,15 @@ __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long
 // k_count_long (one CTA per row).
 constexpr int COUNT_RB = 4;
 
+// rb (1 to COUNT_RB) rows per warp step: a run-time kernel shape.
 template <class Ct>
 __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ counts,
-                             CountLists cl, DevStatus* st) {
+                             CountLists cl, int rb, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const CountOnly<Ct> ko{ct};
-  for (long long i0 = w0 * COUNT_RB; i0 < nlisted; i0 += nw * COUNT_RB) {
+  for (long long i0 = w0 * rb; i0 < nlisted; i0 += nw * rb) {
     RowSrc rs[COUNT_RB];
     long long Ls[COUNT_RB], cnt[COUNT_RB];
     bool lng[COUNT_RB];
@@ -139,8 +140,9 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
 #pragma unroll
     for (int u = 0; u < COUNT_RB; ++u) {
       const long long i = i0 + u;
-      rs[u] = i < nlisted ? ct.row(i) : RowSrc{0, 0, 0, 0};
-      if (cl.rs0 && lane == 0 && i < nlisted) {
+      const bool mine = u < rb && i < nlisted;
+      rs[u] = mine ? ct.row(i) : RowSrc{0, 0, 0, 0};
+      if (cl.rs0 && lane == 0 && mine) {
         cl.rs0[i] = rs[u].s0;
         cl.rsn[i] = rs[u].n0;
       }
@@ -174,7 +176,7 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
 #pragma unroll
       for (int u = 0; u < COUNT_RB; ++u) {
         const long long i = i0 + u;
-        if (i >= nlisted) break;
+        if (u >= rb || i >= nlisted) break;
         if (lng[u]) push_row(cl.cl_rows, cl.n_cl, cl.cl_cap, i, st);
         else counts[i] = cnt[u];
       }
@@ -247,15 +249,16 @@ __device__ __forceinline__ void fill_put(const Ld&, typename Ld::CI* out_col, ty
 
 constexpr int FILL_RB = 2;  // rows per warp step of the fill (fewer than counting: values)
 
+// rb (1 to FILL_RB) rows per warp step: a run-time kernel shape.
 template <class Ld>
 __global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, const long long* __restrict__ vp,
                             typename Ld::CI* __restrict__ out_col, typename Ld::VT* __restrict__ out_val,
-                            DevStatus* st) {
+                            int rb, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i0 = w0 * FILL_RB; i0 < nlisted; i0 += nw * FILL_RB) {
+  for (long long i0 = w0 * rb; i0 < nlisted; i0 += nw * rb) {
     RowSrc rs[FILL_RB];
     long long Ls[FILL_RB], o[FILL_RB], oe[FILL_RB];
     bool lng[FILL_RB];
@@ -263,9 +266,10 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, 
 #pragma unroll
     for (int u = 0; u < FILL_RB; ++u) {
       const long long i = i0 + u;
-      rs[u] = i < nlisted ? ld.row(i) : RowSrc{0, 0, 0, 0};
-      o[u] = i < nlisted ? vp[i] : 0;
-      oe[u] = i < nlisted ? vp[i + 1] : 0;
+      const bool mine = u < rb && i < nlisted;
+      rs[u] = mine ? ld.row(i) : RowSrc{0, 0, 0, 0};
+      o[u] = mine ? vp[i] : 0;
+      oe[u] = mine ? vp[i + 1] : 0;
       Ls[u] = rs[u].n0 + rs[u].n1;
       lng[u] = Ls[u] > SRC_LONG;
       bt.valid[u] = !lng[u] && lane < Ls[u];

@@ -154,6 +154,7 @@ extern "C" sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, con
   if (A->ncols > (int64_t(1) << 32)) return SP_ERR_OVERFLOW;  // 32-bit sort keys
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_PERMUTE, A->nnz);
   SP_TRY(validate_if_asked(ctx, A, s));
   B->nrows = A->nrows;
   B->ncols = A->ncols;

@@ -19,7 +19,7 @@
 namespace sp {
 
 constexpr int SS_ROW_W = 4;                    // partition weight of a row
-constexpr int SS_HEAVY = 128;                  // larger buckets are sorted by a later pass
+constexpr int SS_HEAVY = 128;                  // default (and smallest) heavy-bucket threshold
 constexpr int SS_PASSES = 3;                   // passes over queued heavy buckets
 
 // A sort configuration: BLOCK threads sort items of at most CAP entries, MINB CTAs per
@@ -36,12 +36,13 @@ struct SsCfg {
   static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
   static_assert(B % 32 == 0 && B * MINB <= 2048, "whole warps, resident CTAs");
 };
-using SsTile = SsCfg<128, 1024, true, 8>;  // tiles of rows of at most 512 entries
+using SsTile = SsCfg<128, 1024, true, 8>;   // tiles of rows of at most 512 entries
+using SsTileL = SsCfg<256, 2048, true, 4>;  // tile shape 1: rows of at most 1024 entries
 // single runs of at most 4096 entries: with 4-byte values three CTAs of 384 threads fit
 // an SM (72 KB of shared memory each), with 8-byte values two of 512 (88 KB)
 template <class VT>
 using SsRunT = std::conditional_t<sizeof(VT) == 4, SsCfg<384, 4096, false, 3>, SsCfg<512, 4096, false, 2>>;
-constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts
+constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts (the smaller tile shape)
 constexpr int SS_RUN_MAX = 4096;         // longest row sorted alone
 static_assert(SsRunT<uint32_t>::CAP == SS_RUN_MAX && SsRunT<unsigned long long>::CAP == SS_RUN_MAX,
               "one run capacity");
@@ -70,18 +71,19 @@ constexpr int GC_CH = 4096;                    // gather: output positions per C
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
 
 // ---- partition ----------------------------------------------------------------------
-// Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= SS_TILE_MAX).
-// With c(r) the exclusive prefix of the weights, tile t holds the rows with c(r) in
-// [t*SS_TILE_MAX, (t+1)*SS_TILE_MAX): at most SsTile::ROWS rows and 2*SS_TILE_MAX
-// entries.  Gather chunk k starts at the row holding output position k*GC_CH.
-__device__ __forceinline__ long long rows_weight(const long long* vp, long long r) {
+// Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= tmax, the tile
+// shape's CP).  With c(r) the exclusive prefix of the weights, tile t holds the rows with
+// c(r) in [t*tmax, (t+1)*tmax): at most tmax / SS_ROW_W rows and 2*tmax entries.  Gather
+// chunk k starts at the row holding output position k*GC_CH.
+__device__ __forceinline__ long long rows_weight(const long long* vp, long long r, long long tmax) {
   const long long L = vp[r + 1] - vp[r];
-  return SS_ROW_W + (L <= SS_TILE_MAX ? L : 0);
+  return SS_ROW_W + (L <= tmax ? L : 0);
 }
 
 struct RowsWeight {
   const long long* vp;
-  __device__ long long operator()(long long r) const { return rows_weight(vp, r); }
+  long long tmax;
+  __device__ long long operator()(long long r) const { return rows_weight(vp, r, tmax); }
 };
 
 struct RowsPartition {
@@ -100,10 +102,11 @@ struct RowsPartition {
   long long huge_cap;
   int key_bits;
   int classify;  // list the rows that do not fit a tile (only when the rows are sorted)
+  long long tmax;  // longest row a tile accepts
   DevStatus* st;
   __device__ void operator()(long long r, long long c) const {
     if (r == nrows) {  // c = total weight
-      long long nt = c / SS_TILE_MAX + 1;
+      long long nt = c / tmax + 1;
       if (nt > ntiles_cap) {
         dev_fail(st, SP_ERR_INTERNAL, -14);
         nt = ntiles_cap;
@@ -114,15 +117,15 @@ struct RowsPartition {
     }
     if (r == 0) tile_first[0] = 0;
     const long long o0 = vp[r], o1 = vp[r + 1], L = o1 - o0;
-    const long long e = c + SS_ROW_W + (L <= SS_TILE_MAX ? L : 0);
-    long long t_lo = c / SS_TILE_MAX + 1, t_hi = e / SS_TILE_MAX;
+    const long long e = c + SS_ROW_W + (L <= tmax ? L : 0);
+    long long t_lo = c / tmax + 1, t_hi = e / tmax;
     if (t_hi > ntiles_cap - 1) t_hi = ntiles_cap - 1;
     for (long long t = t_lo; t <= t_hi; ++t) tile_first[t] = r + 1;
     if (L <= 0) return;
     long long k_hi = (o1 - 1) / GC_CH;
     if (k_hi > nchunks - 1) k_hi = nchunks - 1;
     for (long long k = (o0 + GC_CH - 1) / GC_CH; k <= k_hi; ++k) chunk_first[k] = r;
-    if (classify && L > SS_TILE_MAX) {
+    if (classify && L > tmax) {
       if (L <= SS_RUN_MAX) {
         const unsigned q = atomicAdd(fin_n, 1u);
         if (q < fin_cap) fin[q] = FinalEntry{o0, L, BUF_OUT, 0};
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
                const long long* __restrict__ ntiles_p, const FinalEntry* __restrict__ fin,
                const unsigned* __restrict__ fin_n, long long fin_cap, const uint32_t* __restrict__ tkey_g,
                const VT* __restrict__ tval_g, CI* __restrict__ out_col, VT* __restrict__ out_val,
-               FinalEntry* __restrict__ hv, unsigned* hv_n, long long hv_cap, int key_bits,
+               FinalEntry* __restrict__ hv, unsigned* hv_n, long long hv_cap, int key_bits, int heavy,
                DevStatus* st) {
   constexpr int B = Cfg::B, CAP = Cfg::CAP, ROWS = Cfg::ROWS, WORDS = Cfg::WORDS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -945,7 +948,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
       const uint32_t s = slot[x];
       const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
       const uint32_t rd = Cfg::kTiles ? rdel[rowk[x]] : 0u;
-      if (hv && end - start > uint32_t(SS_HEAVY)) {
+      if (hv && end - start > uint32_t(heavy)) {
         st_stream(oc + rd + p, CI(k));
         st_stream(ov + rd + p, sval[x]);
         if (uint32_t(p) == start) {
@@ -1056,10 +1059,14 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   unsigned* fin_n = w.counters + 0;
   unsigned* huge_n = w.counters + 1;
   unsigned* nxt_n = w.counters + 2;
-  SP_TRY(launch_scan(ctx, s, RowsWeight{vp},
+  // kernel shapes of this call (context options or the tuning table)
+  const bool large_tiles = ctx->cur.tile_shape == 1;
+  const long long tmax = large_tiles ? SsTileL::CP : SsTile::CP;
+  const int heavy = ctx->cur.heavy;
+  SP_TRY(launch_scan(ctx, s, RowsWeight{vp, tmax},
                      RowsPartition{vp, nrows, w.ntiles_cap, w.tile_first, w.ntiles, w.nchunks, w.chunk_first,
                                    w.fin, fin_n, w.fin_cap, w.huge, huge_n, w.huge_cap, key_bits,
-                                   sort ? 1 : 0, ctx->dstatus},
+                                   sort ? 1 : 0, tmax, ctx->dstatus},
                      nrows, w.scan_ws, SP_PHASE_PARTITION));
   if (gs) {
     if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
@@ -1098,21 +1105,28 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   const unsigned* no_runs = w.counters + 8;
   using SsRun = SsRunT<VT>;
-  constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), rsm = ss_smem_bytes<SsRun, VT>();
-  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
+  constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), lsm = ss_smem_bytes<SsTileL, VT>(),
+                   rsm = ss_smem_bytes<SsRun, VT>();
+  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsTileL, CI, VT>, lsm),
+                        set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
   (void)once_s;
   {
     SP_PHASE(SP_PHASE_TILE);
-    k_seg_sort<SsTile, CI, VT><<<SsTile::MINB * nsm, SsTile::B, tsm, s>>>(
-        vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0], w.counters + 6,
-        w.hv_cap, key_bits, ctx->dstatus);
+    if (large_tiles)
+      k_seg_sort<SsTileL, CI, VT><<<SsTileL::MINB * nsm, SsTileL::B, lsm, s>>>(
+          vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0],
+          w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
+    else
+      k_seg_sort<SsTile, CI, VT><<<SsTile::MINB * nsm, SsTile::B, tsm, s>>>(
+          vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0],
+          w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   {
     SP_PHASE(SP_PHASE_LONG);
     k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
         vp, w.tile_first, no_tiles, w.fin, fin_n, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
-        w.counters + 6, w.hv_cap, key_bits, ctx->dstatus);
+        w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   // heavy buckets: runs over their own key range; the last pass ranks every bucket
@@ -1124,7 +1138,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
       SP_PHASE(SP_PHASE_LONG);
       k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
           vp, w.tile_first, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
-          last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, ctx->dstatus);
+          last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, heavy, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
   }

@@ -152,6 +152,7 @@ extern "C" sp_status sp_sort_rows(sp_ctx* ctx, sp_csr* M, sp_stream_t stream) {
   if (M->ncols > J_KEY_LIMIT) return SP_ERR_OVERFLOW;
   cudaStream_t s = (cudaStream_t)stream;
   SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, -1, M->nnz);
   if (M->nnz == 0 || M->nrows == 0) return SP_OK;
   return dispatch_i(M->rowptr_type, [&](auto rp) {
     using RP = decltype(rp);

@@ -1,0 +1,37 @@
+"""Host side of the tuning table: entry validation and ordering, and the option / op
+numbers of the binding against the ones include/sp.h declares."""
+import os
+import re
+
+import pytest
+
+from paper_2509_20776_gb300 import _binding as b
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_entries_validated_and_ordered():
+    rows = b.tune_entries({"entries": [
+        {"op": "batch", "size_max": 5, "batch_rows": 8},
+        {"op": "permute", "size_max": 100, "tile_shape": 1},
+        {"op": "permute", "size_max": 10, "heavy": 256}]})
+    assert [(r["op"], r["size_max"]) for r in rows] == [(0, 10), (0, 100), (3, 5)]
+    assert rows[0]["heavy"] == 256 and rows[0]["tile_shape"] == -1
+    assert rows[2]["batch_rows"] == 8 and rows[2]["count_rows"] == -1
+    for bad in ({"op": "sort", "size_max": 1}, {"op": "permute", "size_max": 1, "heavy": 100},
+                {"op": "extract", "size_max": 1, "fill_rows": 3}, {"op": "batch", "size_max": 1, "batch_rows": 16}):
+        with pytest.raises(ValueError):
+            b.tune_entries([bad])
+
+
+def test_numbers_match_header():
+    h = open(os.path.join(ROOT, "include", "sp.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"(SP_OPT_[A-Z_]+) = (\d+)", h))
+    for name, key in b.SHAPE_OPTIONS.items():
+        assert enum["SP_OPT_" + name.upper()] == key
+    ops = dict((k, int(v)) for k, v in re.findall(r"SP_OP_([A-Z]+) = (\d+)", h))
+    assert {k.lower(): v for k, v in ops.items()} == b.OPS
+    # the ctypes entry mirrors the C struct's field order and widths
+    assert [f for f, _ in b.sp_tune_entry._fields_] == ["op", "tile_shape", "heavy", "count_rows", "fill_rows",
+                                                        "batch_rows", "size_max"]
+    assert b.sp_tune_entry.size_max.offset == 24
