@@ -42,9 +42,9 @@ WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16
 # (profiles/launches_permute_rmat25.md).  Only valid for the kernels as captured: retake
 # the capture when one changes; other scales report null.
 NCU_TRAFFIC = {
-    (25, "gather"): 26_631_298_304,
-    (25, "tile"): 7_065_250_816,
-    (25, "huge"): 4_477_223_424,  # both split rounds (the second is empty for random keys)
+    (25, "gather"): 26_627_223_296,
+    (25, "tile"): 7_063_724_800,
+    (25, "huge"): 4_478_964_224,  # both split rounds (the second is empty for random keys)
 }
 
 
