@@ -364,28 +364,46 @@ def e2e_permute(ctx, A, ops, args, ws):
         for p, q in hperm)
     d2h = len(ops) * (out_rp.numel() * 8 + out_ci.numel() * 4 + out_v.numel() * 4)
 
-    # results go back on a copy stream, so each one's device-to-host copy overlaps the
-    # next permutation (and the next step's host-to-device copy of A)
-    copy = torch.cuda.Stream(device=dev)
+    # Copies of large arrays are cut into NCOPY pieces on NCOPY streams per direction.
+    # Results go back on their own streams, so each one's device-to-host copy overlaps
+    # the next permutation and the next step's host-to-device copy of A.
+    NCOPY = 8
+    cps_in = [torch.cuda.Stream(device=dev) for _ in range(NCOPY)]   # host -> device
+    cps = [torch.cuda.Stream(device=dev) for _ in range(NCOPY)]      # device -> host
+
+    def pieces(dst, src, streams):
+        n = dst.numel()
+        for k, st in enumerate(streams):
+            a, b = n * k // len(streams), n * (k + 1) // len(streams)
+            with torch.cuda.stream(st):
+                dst[a:b].copy_(src[a:b], non_blocking=True)
+
+    done = [torch.cuda.Event()]  # the previous step's last permutation (no longer reads dA)
 
     def step():
         main = torch.cuda.current_stream()
+        for st in cps_in:
+            st.wait_event(done[0])
         for d, h in zip(dA, hA):
-            d.copy_(h, non_blocking=True)
+            pieces(d, h, cps_in)
+        for st in cps_in:
+            main.wait_stream(st)
         Ad = CSR(A.nrows, A.ncols, dA[0], dA[1], dA[2])
         for (dp, dq), (hp, hq) in zip(dperm, hperm):
             dp.copy_(hp, non_blocking=True)
             if dq is not None:
                 dq.copy_(hq, non_blocking=True)
             B = ctx.sp_permute(Ad, dp, dq if dq is not None else dp, sync=False)
-            copy.wait_stream(main)
-            with torch.cuda.stream(copy):
-                out_rp.copy_(B.rowptr, non_blocking=True)
-                out_ci.copy_(B.colidx, non_blocking=True)
-                out_v.copy_(B.values, non_blocking=True)
-            for t in (B.rowptr, B.colidx, B.values):
-                t.record_stream(copy)  # keep B's memory until its copy is done
-        main.wait_stream(copy)  # the step ends when every result is on the host
+            for st in cps:
+                st.wait_stream(main)
+            for h, t in ((out_rp, B.rowptr), (out_ci, B.colidx), (out_v, B.values)):
+                pieces(h, t, cps)
+                for st in cps:
+                    t.record_stream(st)  # keep B's memory until its copies are done
+        done[0] = torch.cuda.Event()
+        done[0].record(main)
+        for st in cps:
+            main.wait_stream(st)  # the step ends when every result is on the host
 
     steps = max(1, args.steps // 2)
     ms = time_steps(step, steps, 1, ws)
