@@ -3,11 +3,14 @@
 //     at its final row position but in source order (a load-balanced gather over
 //     fixed chunks of output positions: no shared-memory sort, all loads independent);
 //   phase 2, the rows of the output are sorted in place:
-//     * rows of at most SS_TILE_MAX entries in tiles (consecutive rows, at most
-//       2 * SS_TILE_MAX entries per tile), k_seg_sort<SsTile>;
-//     * rows of SS_TILE_MAX < L <= SS_RUN_MAX entries alone, k_seg_sort<SsRun>;
-//     * longer rows are first partitioned by key range (k_split) into runs of at most
-//       SS_RUN_MAX entries, which k_seg_sort<SsRun> then sorts.
+//     * rows of at most CP entries (512, or 1024 with the run-time tile shape 1) in
+//       tiles of consecutive rows, at most 2 * CP entries each, k_seg_sort<SsTile> or
+//       k_seg_sort<SsTileL>;
+//     * rows of CP < L <= SS_RUN_MAX entries alone, k_seg_sort<SsRunT<VT>>;
+//     * longer rows are first cut by key range (k_split, two rounds) into runs of at
+//       most SS_RUN_MAX entries, which k_seg_sort<SsRunT<VT>> then sorts.
+//   Buckets of more keys than the (run-time) heavy threshold are queued as runs for up
+//   to SS_PASSES later passes.
 // One scan over the output rows (RowsPartition) cuts the tiles and the gather chunks
 // and lists the rows that do not fit a tile.
 #pragma once
@@ -57,7 +60,7 @@ struct FinalEntry {  // a run of at most SS_RUN_MAX entries left to sort in plac
   int buf;
   int pad;
 };
-struct HugeEntry {  // a run longer than SS_RUN_MAX, keys in [lo, lo + 2^wb)
+struct HugeEntry {  // a run longer than SS_RUN_MAX; round 1: keys in [lo, lo + 2^wb)
   long long off;
   long long len;
   unsigned lo;
