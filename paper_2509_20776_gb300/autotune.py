@@ -48,9 +48,20 @@ def _flatten(out) -> list:
     return []
 
 
+_BITS = {torch.float32: torch.int32, torch.float64: torch.int64, torch.float16: torch.int16,
+         torch.bfloat16: torch.int16}
+
+
+def _bits(t: torch.Tensor) -> torch.Tensor:
+    """Floating tensors as their bit patterns (so -0.0 differs from 0.0, NaN payloads count)."""
+    return t.view(_BITS[t.dtype]) if t.dtype in _BITS else t
+
+
 def _same(a, b) -> bool:
+    """Bit-for-bit equality of two results."""
     ta, tb = _flatten(a), _flatten(b)
-    return len(ta) == len(tb) and all(x.dtype == y.dtype and torch.equal(x, y) for x, y in zip(ta, tb))
+    return len(ta) == len(tb) and all(x.dtype == y.dtype and x.shape == y.shape and
+                                      torch.equal(_bits(x), _bits(y)) for x, y in zip(ta, tb))
 
 
 def _time(run, reps: int):

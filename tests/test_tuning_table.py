@@ -35,3 +35,33 @@ def test_numbers_match_header():
     assert [f for f, _ in b.sp_tune_entry._fields_] == ["op", "tile_shape", "heavy", "count_rows", "fill_rows",
                                                         "batch_rows", "size_max"]
     assert b.sp_tune_entry.size_max.offset == 24
+
+
+def test_autotune_compare_and_files(tmp_path):
+    """The tuner's bit-identity check and its table file, on CPU tensors."""
+    import json
+    import torch
+    from paper_2509_20776_gb300 import autotune as at
+
+    class M:  # a CSR-like result
+        def __init__(self, v):
+            self.rowptr = torch.tensor([0, 2, 3])
+            self.colidx = torch.tensor([1, 4, 0], dtype=torch.int32)
+            self.values = torch.tensor(v, dtype=torch.float32)
+
+    assert at._same(M([1.0, 2.0, 3.0]), M([1.0, 2.0, 3.0]))
+    assert not at._same(M([1.0, 2.0, 3.0]), M([1.0, 2.0, 4.0]))
+    assert not at._same(M([0.0, 2.0, 3.0]), M([-0.0, 2.0, 3.0]))  # bit patterns, not values
+    assert at._same((M([1.0, 2.0, 3.0]), torch.tensor([5])), (M([1.0, 2.0, 3.0]), torch.tensor([5])))
+    assert not at._same((M([1.0, 2.0, 3.0]),), (M([1.0, 2.0, 3.0]), torch.tensor([5])))
+    table = {"format": "sp-tuning-1", "entries": [{"op": "batch", "size_max": 1 << 62, "batch_rows": 2,
+                                                   "tile_shape": 0, "heavy": 128}]}
+    path = tmp_path / "t.json"
+    at.save(table, str(path))
+    assert at.load(str(path)) == table
+    b.tune_entries(at.load(str(path)))  # the binding accepts what the tuner writes
+    (tmp_path / "bad.json").write_text(json.dumps({"entries": []}))
+    with pytest.raises(ValueError):
+        at.load(str(tmp_path / "bad.json"))
+    # every knob the tuner searches is a shape the binding and the header know
+    assert set(at.SEARCH) == set(b.SHAPE_OPTIONS) and set(at.KNOBS) == set(b.OPS)
