@@ -105,7 +105,9 @@ SP_API const char* sp_status_str(sp_status s);
 SP_API int sp_version(void);
 
 /* Create a context on CUDA device `device`.  `allocator` may be NULL (see
- * sp_allocator); it is copied.  *ctx receives the new context.
+ * sp_allocator); it is copied.  *ctx receives the new context.  A context is used by
+ * one host thread at a time (its workspace, options and per-call kernel shapes are not
+ * locked); work from several threads or streams in parallel takes one context each.
  * Errors: SP_ERR_INVALID_ARG (ctx NULL), SP_ERR_CUDA (device unusable). */
 SP_API sp_status sp_ctx_create(sp_ctx** ctx, int device, const sp_allocator* allocator);
 
