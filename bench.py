@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=25, help="R-MAT scale of the headline workload")
     ap.add_argument("--no-extra", action="store_true", help="skip the extraction/assignment ops")
+    ap.add_argument("--ops", default="extract,assign,batch,serve",
+                    help="comma list of the extra sections to run (extract, assign, batch, serve)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -315,29 +317,20 @@ def run_ours(args, ws, rank, local):
     del outs
     if not args.no_extra:
         ops_res = {}
-        try:
-            ops_res["extract"] = bench_extract(ctx, args, dev, hbm, ws)
-            log("extract done")
-        except Exception as e:  # noqa: BLE001
-            ops_res["extract"] = {"error": repr(e)[:300]}
-        torch.cuda.empty_cache()
-        try:
-            ops_res["assign"] = bench_assign(ctx, args, dev, hbm, ws)
-            log("assign done")
-        except Exception as e:  # noqa: BLE001
-            ops_res["assign"] = {"error": repr(e)[:300]}
-        torch.cuda.empty_cache()
-        try:
-            ops_res["batch_extract"] = bench_batch(ctx, args, dev, ws)
-            log("batch done")
-        except Exception as e:  # noqa: BLE001
-            ops_res["batch_extract"] = {"error": repr(e)[:300]}
-        torch.cuda.empty_cache()
-        try:
-            ops_res["serve"] = bench_serve(ctx, args, dev)
-            log("serve done")
-        except Exception as e:  # noqa: BLE001
-            ops_res["serve"] = {"error": repr(e)[:300]}
+        want = set(args.ops.split(","))
+        sections = (("extract", "extract", lambda: bench_extract(ctx, args, dev, hbm, ws)),
+                    ("assign", "assign", lambda: bench_assign(ctx, args, dev, hbm, ws)),
+                    ("batch", "batch_extract", lambda: bench_batch(ctx, args, dev, ws)),
+                    ("serve", "serve", lambda: bench_serve(ctx, args, dev)))
+        for name, key, fn in sections:
+            if name not in want:
+                continue
+            try:
+                ops_res[key] = fn()
+                log(f"{name} done")
+            except Exception as e:  # noqa: BLE001
+                ops_res[key] = {"error": repr(e)[:300]}
+            torch.cuda.empty_cache()
         result["ops"] = ops_res
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
