@@ -170,6 +170,11 @@ typedef struct sp_tune_entry {
   int64_t size_max;  /* the entry covers calls of size <= size_max */
 } sp_tune_entry;
 SP_API sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n);
+/* Host only (no device work): the entry of `table` (n entries) that a call of `op` with
+ * size `size` takes — the first entry with that op and size_max >= size — copied to
+ * *out; returns 1 if one applies, 0 if none (then *out is untouched), -1 for a NULL
+ * table with n > 0, n < 0 or a NULL out.  sp_ctx_set_tuning's lookup is this one. */
+SP_API int sp_tuning_lookup(const sp_tune_entry* table, int n, int op, int64_t size, sp_tune_entry* out);
 
 /* Per-phase kernel statistics (tracing).  Every kernel the library launches belongs to
  * one phase; the context counts launches per phase always, and with SP_OPT_TIMING=1

@@ -77,6 +77,16 @@ def tune_entries(table) -> list:
     return out
 
 
+def tune_array(table):
+    """ctypes array of the entries of a table (see ``tune_entries``) and its length."""
+    rows = tune_entries(table) if table else []
+    arr = (sp_tune_entry * max(1, len(rows)))()
+    for i, r in enumerate(rows):
+        arr[i] = sp_tune_entry(r["op"], r["tile_shape"], r["heavy"], r["count_rows"], r["fill_rows"],
+                               r["batch_rows"], r["size_max"])
+    return arr, len(rows)
+
+
 class sp_extract_req(ctypes.Structure):
     _fields_ = [("mat", ctypes.c_int64), ("nI", ctypes.c_int64), ("nJ", ctypes.c_int64),
                 ("I", ctypes.c_void_p), ("J", ctypes.c_void_p)]
@@ -96,6 +106,7 @@ SIGNATURES = {
     "sp_ctx_error_detail": (_i64, [_vp]),
     "sp_ctx_set_option": (_int, [_vp, _int, _i64]),
     "sp_ctx_set_tuning": (_int, [_vp, ctypes.POINTER(sp_tune_entry), _int]),
+    "sp_tuning_lookup": (_int, [ctypes.POINTER(sp_tune_entry), _int, _int, _i64, ctypes.POINTER(sp_tune_entry)]),
     "sp_permute": (_int, [_vp, _PCSR, _vp, _vp, _int, _PCSR, _vp]),
     "sp_extract_count": (_int, [_vp, _PCSR, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(_vp),
                                 ctypes.POINTER(_i64), _vp]),
@@ -239,12 +250,8 @@ class Context:
             import json
             with open(table) as f:
                 table = json.load(f)
-        rows = tune_entries(table) if table else []
-        arr = (sp_tune_entry * max(1, len(rows)))()
-        for i, r in enumerate(rows):
-            arr[i] = sp_tune_entry(r["op"], r["tile_shape"], r["heavy"], r["count_rows"], r["fill_rows"],
-                                   r["batch_rows"], r["size_max"])
-        self._check(self.lib.sp_ctx_set_tuning(self.handle, arr, len(rows)), "sp_ctx_set_tuning")
+        arr, n = tune_array(table)
+        self._check(self.lib.sp_ctx_set_tuning(self.handle, arr, n), "sp_ctx_set_tuning")
 
     def phase_stats(self, reset: bool = False) -> dict:
         """{phase: (device ms, kernel launches)} accumulated since the last reset."""

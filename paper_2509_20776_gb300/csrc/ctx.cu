@@ -205,6 +205,16 @@ sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
   return SP_ERR_INVALID_ARG;
 }
 
+int sp_tuning_lookup(const sp_tune_entry* table, int n, int op, int64_t size, sp_tune_entry* out) {
+  if (n < 0 || (n > 0 && !table) || !out) return -1;
+  for (int i = 0; i < n; ++i) {
+    if (table[i].op != op || size > table[i].size_max) continue;
+    *out = table[i];
+    return 1;
+  }
+  return 0;
+}
+
 sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n) {
   if (!ctx || n < 0 || (n > 0 && !table)) return SP_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {

@@ -139,16 +139,13 @@ sp_status validate_if_asked(sp_ctx* ctx, const sp_csr* A, cudaStream_t s);
 // first tuning-table entry of `op` that covers `size` (op < 0: no table lookup).
 inline void ctx_begin_call(sp_ctx* ctx, int op, long long size) {
   ctx->cur = ctx->opt;
-  if (op < 0) return;
-  for (const sp_tune_entry& e : ctx->tuning) {
-    if (e.op != op || size > e.size_max) continue;
-    if (e.tile_shape >= 0) ctx->cur.tile_shape = e.tile_shape;
-    if (e.heavy >= 0) ctx->cur.heavy = e.heavy;
-    if (e.count_rows >= 0) ctx->cur.count_rows = e.count_rows;
-    if (e.fill_rows >= 0) ctx->cur.fill_rows = e.fill_rows;
-    if (e.batch_rows >= 0) ctx->cur.batch_rows = e.batch_rows;
-    return;
-  }
+  sp_tune_entry e;
+  if (op < 0 || sp_tuning_lookup(ctx->tuning.data(), int(ctx->tuning.size()), op, size, &e) != 1) return;
+  if (e.tile_shape >= 0) ctx->cur.tile_shape = e.tile_shape;
+  if (e.heavy >= 0) ctx->cur.heavy = e.heavy;
+  if (e.count_rows >= 0) ctx->cur.count_rows = e.count_rows;
+  if (e.fill_rows >= 0) ctx->cur.fill_rows = e.fill_rows;
+  if (e.batch_rows >= 0) ctx->cur.batch_rows = e.batch_rows;
 }
 
 }  // namespace sp

@@ -65,3 +65,24 @@ def test_autotune_compare_and_files(tmp_path):
         at.load(str(tmp_path / "bad.json"))
     # every knob the tuner searches is a shape the binding and the header know
     assert set(at.SEARCH) == set(b.SHAPE_OPTIONS) and set(at.KNOBS) == set(b.OPS)
+
+
+def test_library_lookup_takes_the_tightest_class():
+    """The C library's per-call lookup (host only): first entry of the op whose size_max
+    covers the call, with the binding's ordering making that the tightest class."""
+    import ctypes
+    lib = b.load_library()
+    arr, n = b.tune_array({"entries": [
+        {"op": "permute", "size_max": 1 << 40, "tile_shape": 0, "heavy": 512},
+        {"op": "permute", "size_max": 1000, "tile_shape": 1},
+        {"op": "extract", "size_max": 1 << 40, "count_rows": 2}]})
+    out = b.sp_tune_entry()
+    assert lib.sp_tuning_lookup(arr, n, b.OPS["permute"], 999, ctypes.byref(out)) == 1
+    assert (out.tile_shape, out.heavy, out.size_max) == (1, -1, 1000)
+    assert lib.sp_tuning_lookup(arr, n, b.OPS["permute"], 1001, ctypes.byref(out)) == 1
+    assert (out.tile_shape, out.heavy) == (0, 512)
+    assert lib.sp_tuning_lookup(arr, n, b.OPS["extract"], 5, ctypes.byref(out)) == 1 and out.count_rows == 2
+    assert lib.sp_tuning_lookup(arr, n, b.OPS["batch"], 5, ctypes.byref(out)) == 0
+    assert lib.sp_tuning_lookup(arr, n, b.OPS["permute"], (1 << 40) + 1, ctypes.byref(out)) == 0
+    assert lib.sp_tuning_lookup(None, 2, 0, 5, ctypes.byref(out)) == -1
+    assert lib.sp_tuning_lookup(arr, -1, 0, 5, ctypes.byref(out)) == -1
