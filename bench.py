@@ -86,7 +86,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples: SP_BENCH_CLOCKS_DIR when set, else the system's temporary folder
+        import tempfile
+        d = os.environ.get("SP_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"sp_bench_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:

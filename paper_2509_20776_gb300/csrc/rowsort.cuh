@@ -7,7 +7,7 @@
 //       tiles of consecutive rows, at most 2 * CP entries each, k_seg_sort<SsTile> or
 //       k_seg_sort<SsTileL>;
 //     * rows of CP < L <= SS_RUN_MAX entries alone, k_seg_sort<SsRunT<VT>>;
-//     * longer rows are first cut by key range (k_split, two rounds) into runs of at
+//     * longer rows are first cut by key range (k_split: a coarse, then a fine split) into runs of at
 //       most SS_RUN_MAX entries, which k_seg_sort<SsRunT<VT>> then sorts.
 //   Buckets of more keys than the (run-time) heavy threshold are queued as runs for up
 //   to SS_PASSES later passes.
@@ -60,7 +60,7 @@ struct FinalEntry {  // a run of at most SS_RUN_MAX entries left to sort in plac
   int buf;
   int pad;
 };
-struct HugeEntry {  // a run longer than SS_RUN_MAX; round 1: keys in [lo, lo + 2^wb)
+struct HugeEntry {  // a run longer than SS_RUN_MAX; coarse split: keys in [lo, lo + 2^wb)
   long long off;
   long long len;
   unsigned lo;
@@ -351,19 +351,19 @@ __device__ __forceinline__ uint32_t ss_bucket(uint32_t key, float scale, uint32_
 // their offsets, pass 2 moves the run bucket by bucket into the other buffer (output <->
 // temporary) at the same offsets.  Consecutive small buckets whose starts fall in one
 // GROUP_CAP window form one run for k_seg_sort; a bucket of more than GROUP_CAP entries is
-// a run of its own, or (more than SS_RUN_MAX entries) a run for the next split round.
-//   Round 1 (SplitCoarse): nb = 2^10 buckets evenly spaced over [lo, lo + 2^wb).  A run
+// a run of its own, or (more than SS_RUN_MAX entries) a run for the fine split.
+//   Coarse split (SplitCoarse): nb = 2^10 buckets evenly spaced over [lo, lo + 2^wb).  A run
 //     is sorted as a whole afterwards, so pass 2 only has to bring every entry into its
 //     group's range, not its bucket's: it stages each chunk of B * U entries in shared
 //     memory by group and writes every group's share of the chunk as one contiguous piece
 //     (groups hold hundreds to thousands of entries, so the writes are coalesced whatever
 //     the key distribution).
-//   Round 2 (SplitFine, the buckets of round 1 that hold more than SS_RUN_MAX entries,
+//   Fine split (SplitFine, the buckets of the coarse split that hold more than SS_RUN_MAX entries,
 //     e.g. hub rows under a degree-descending relabelling): 2^13 buckets evenly spaced over
 //     the bucket's own [min, max] keys (found by a first pass), scattered directly.  A
-//     round-1 bucket spans 2^(wb - 10) <= 2^22 keys, so a round-2 bucket spans at most
+//     coarse bucket spans 2^(wb - 10) <= 2^22 keys, so a fine bucket spans at most
 //     2^9 < SS_RUN_MAX keys: with keys unique within a row it holds fewer than SS_RUN_MAX
-//     entries and no third round is needed.
+//     entries and no third split is needed.
 struct SplitCoarse {
   static constexpr int NBL = 10, B = 256, MINB = 4, U = 8;
   static constexpr bool kStaged = true;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(S::B, S::MINB)
       lo = he.lo;
       wb = he.wb;
       nbl = wb < S::NBL ? wb : S::NBL;
-      static_assert(32 - S::NBL - SplitFine::NBL <= SS_RUN_LOG, "round-2 buckets fit a run");
+      static_assert(32 - S::NBL - SplitFine::NBL <= SS_RUN_LOG, "fine-split buckets fit a run");
     } else {
       // the bucket's own key range
       uint32_t mn = 0xFFFFFFFFu, mx = 0u;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(S::B, S::MINB)
           if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, cc, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -6);
         } else {
-          const unsigned q = atomicAdd(nxt_n, 1u);  // round 2 finds its key range itself
+          const unsigned q = atomicAdd(nxt_n, 1u);  // the fine split finds its key range itself
           if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb, cc, 0u, 0, dbuf, 0};
           else dev_fail(st, SP_ERR_INTERNAL, -7);
         }
@@ -1094,7 +1094,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
           w.nxt, nxt_n, w.nxt_cap, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
-    // round 2: the buckets of round 1 that hold more than SS_RUN_MAX entries (skewed keys
+    // the fine split: the coarse buckets that hold more than SS_RUN_MAX entries (skewed keys
     // or very long rows); an empty list costs one short launch
     {
       SP_PHASE(SP_PHASE_HUGE);
