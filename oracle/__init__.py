@@ -6,6 +6,6 @@ The library (``paper_2509_20776_gb300``) never imports it and shares no code wit
 """
 from .sparse_oracle import (  # noqa: F401
     CSR, OracleError, build_csr, assign, exclusive_scan, extract, extract_row,
-    assign_row, inverse_map, kept_counts, permute, permute_row, row_lengths_permuted,
+    assign_row, inverse_map, kept_counts, permute, permute_row,
     to_dense, from_dense, canonical_check,
 )

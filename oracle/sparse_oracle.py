@@ -149,12 +149,6 @@ def permute(A: CSR, p, q) -> CSR:
     return build_csr(m, n, pinv[r], qinv[c], v)
 
 
-def row_lengths_permuted(A: CSR, p) -> np.ndarray:
-    """len(A'[i, :]) = len(A[p[i], :]): rows move whole under a permutation."""
-    lens = np.diff(A.rowptr)
-    return lens if p is None else lens[np.asarray(p, dtype=np.int64)]
-
-
 def permute_row(A: CSR, p, qinv: np.ndarray | None, i: int):
     """Row i of A' = P A Q^T alone: the entries of row p[i], columns relabelled by qinv,
     in ascending new-column order.  Returns (cols, values)."""

@@ -250,6 +250,12 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
 template <class RP, class CI, class VT, class IX>
 sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s) {
   const long long rows = b->rows, nnz = b->nnz;
+  // the row sort's workspace was reserved by the count: check it before any launch, so
+  // a failure leaves the output untouched
+  Carver cf;
+  size_t rf[kRowsSlots];
+  rows_reserve(cf, rows, nnz, sizeof(VT), rf);
+  if (nnz > 0 && cf.total() > ctx->ws_cap) return SP_ERR_INTERNAL;
   // the int64 row pointer is the batch's own; an int32 output gets a narrowed copy
   if (out->rowptr_type == SP_I64) {
     SP_CUDA(cudaMemcpyAsync(out->rowptr, b->vp, size_t(rows + 1) * 8, cudaMemcpyDeviceToDevice, s));
@@ -270,10 +276,6 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
         ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
-  Carver cf;
-  size_t rf[kRowsSlots];
-  rows_reserve(cf, rows, nnz, sizeof(VT), rf);
-  if (cf.total() > ctx->ws_cap) return SP_ERR_INVALID_ARG;  // the count reserved it: no allocation here
   char* base;
   SP_TRY(ctx_workspace(ctx, cf.total(), s, &base));
   cf.bind(base);

@@ -117,7 +117,7 @@ __device__ __forceinline__ void push_row(long long* list, unsigned* n, long long
   else dev_fail(st, SP_ERR_INTERNAL, -12);
 }
 
-// Count kernels take a loader (see segsort.cuh) and count the entries its map keeps.
+// Count kernels take a loader (see loaders.cuh) and count the entries its map keeps.
 // Short rows: one warp handles COUNT_RB rows per step, reading the first 32 entries of
 // all of them in one batch (ballot + popc per row); the rest of longer rows follows
 // in batches of LOAD_U x 32.  Source-long rows (> SRC_LONG entries) are listed for

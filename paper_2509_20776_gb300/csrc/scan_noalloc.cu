@@ -1,4 +1,4 @@
-// Exclusive scan that allocates nothing: the look-back scan of pipeline.cuh with its
+// Exclusive scan that allocates nothing: the look-back scan of scan.cuh with its
 // tile-status words, tile ticket and error record held in a fixed-size file-scope
 // device array instead of context workspace.
 //

@@ -1,11 +1,14 @@
 """The request server: every result of a mixed permute / extract / assign stream, served
-with continuous batching on several streams, equals the plain one-call-per-request
-result bit-exactly (each result is the same alone and in the mix)."""
+with continuous batching on several streams, equals the oracle's result for that request
+bit-exactly, and equals the plain one-call-per-request result (each result is the same
+alone and in the mix)."""
+import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
-from helpers import to_dev
+from helpers import assert_same, bits, to_dev, to_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -54,20 +57,32 @@ def test_served_equals_plain():
     srv.run(reqs_a)
     ctx = Context(0)
     run_plain(ctx, mats, reqs_b, keep_results=True)
-    for a, b in zip(reqs_a, reqs_b):
+    hosts = [to_oracle(m) for m in mats]
+    for k, (a, b) in enumerate(zip(reqs_a, reqs_b)):
         assert a.done >= a.arrival and b.done >= b.arrival
         want = b.result
+        A = hosts[a.mat]
+        # the oracle decides: the definition of each operation on the request's inputs
+        if a.kind == "permute":
+            ref = oracle.permute(A, a.p.cpu().numpy(), a.p.cpu().numpy())
+        elif a.kind == "extract":
+            ref = oracle.extract(A, a.I.cpu().numpy(), a.J.cpu().numpy())
+        else:
+            ref = oracle.assign(A, a.I.cpu().numpy(), a.J.cpu().numpy(), to_oracle(a.B))
         if a.kind == "extract":
             out, r0, r1 = a.result
             base, end = int(out.rowptr[r0]), int(out.rowptr[r1])
-            assert torch.equal(out.rowptr[r0:r1 + 1] - base, want.rowptr.to(out.rowptr.dtype))
-            assert torch.equal(out.colidx[base:end], want.colidx)
-            assert torch.equal(out.values[base:end].view(torch.int32), want.values.view(torch.int32))
-            assert a.nnz_out == want.nnz
+            rp = (out.rowptr[r0:r1 + 1] - base).cpu().numpy().astype(np.int64)
+            assert np.array_equal(rp, ref.rowptr), f"request {k}: served extraction rowptr"
+            assert np.array_equal(out.colidx[base:end].cpu().numpy().astype(np.int64), ref.colidx), \
+                f"request {k}: served extraction colidx"
+            assert np.array_equal(bits(out.values[base:end].cpu().numpy()), bits(ref.values)), \
+                f"request {k}: served extraction values"
+            assert a.nnz_out == ref.nnz
+            assert_same(want, ref, f"request {k}: plain extraction")
         else:
-            got = a.result
-            assert torch.equal(got.rowptr, want.rowptr) and torch.equal(got.colidx, want.colidx)
-            assert torch.equal(got.values.view(torch.int32), want.values.view(torch.int32))
+            assert_same(a.result, ref, f"request {k}: served {a.kind}")
+            assert_same(want, ref, f"request {k}: plain {a.kind}")
     st = latency_stats(reqs_a)
     assert st["p99_ms"] >= st["p50_ms"] >= 0
     srv.close()
