@@ -36,17 +36,14 @@ UNIT = "output nnz/s"
 WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16, symmetrised; "
             "P A P^T random p + P A P^T degree-descending p + P A Q^T random p,q")
 
-# DRAM bytes (read + write) of one launch of a kernel on the first P A P^T (random p)
-# of the workload at a given R-MAT scale, from an ncu capture of only
-# dram__bytes_read.sum + dram__bytes_write.sum (and the duration) at that size
-# (profiles/launches_permute_rmat25.md).  Only valid for the kernels as captured: retake
-# the capture when one changes; other scales report null.
-NCU_TRAFFIC = {
-    (25, "gather"): 26_627_223_296,
-    (25, "tile"): 7_063_724_800,
-    (25, "huge"): 4_478_964_224,  # both split rounds (the second is empty for random keys)
-}
-
+# DRAM bytes (read + write) per output entry of one k_gather_chunks launch on the
+# first P A P^T (random p), from a one-kernel ncu capture of only
+# dram__bytes_read.sum + dram__bytes_write.sum on the rows-limited instance of the same
+# workload (bench.py --rows-limit 2097152: the first 2^21 rows, all 2^25 columns, so
+# the relabel map keeps its full-size L2 pressure); scaled to a full launch by the
+# entries it moves (profiles/gather_dram_rmat25_rows2m.md).  Only valid for the kernel
+# as captured: retake the capture when it changes.
+GATHER_DRAM_BYTES_PER_ENTRY = None
 
 _T0 = time.time()
 
@@ -67,6 +64,9 @@ def parse():
                     help="comma list of the extra sections to run (extract, assign, batch, serve)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--rows-limit", type=int, default=0,
+                    help="profiling case: the headline matrix's first R rows (all columns), one "
+                         "permutation with independent random p, q; prints its line and exits")
     return ap.parse_args()
 
 
@@ -190,17 +190,19 @@ def row_classes(rowptr):
     return out
 
 
-def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, scale):
+def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup_peak):
     """Roofline of the phase that takes the most device time: its algorithmic bytes per
-    launch (per-entry and per-row byte counts of the kernel, int32 indices and fp32
-    values) over its average CUDA-event duration."""
+    launch over its average CUDA-event duration (int32 columns, fp32 values).  The gather
+    moves 16 B per entry (read and write column + value, the scope's per-entry bytes) plus
+    16 B per row (output row pointer, source start); its 4-byte relabel lookup per entry is
+    counted separately (frac_incl_lookup) and against the measured random-lookup rate."""
     e_tile, r_tile = classes["tile"]
     e_long, _ = classes["long"]
     e_huge, _ = classes["huge"]
     nnz = e_tile + e_long + e_huge
     per_op = {
-        # gather: read col + val, one map lookup, write col + val; vp and source start per row
-        "gather": 20 * nnz + 16 * m,
+        # gather: read col + val, write col + val; vp pair and source start per row
+        "gather": 16 * nnz + 16 * m,
         # in-place sort of tile rows: read and write col + val; row pointer per row
         "tile": 16 * e_tile + 8 * m,
         # rows sorted alone and key-range runs of long rows: read and write col + val
@@ -223,14 +225,52 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, scale)
     kernel = {"gather": "k_gather_chunks", "tile": "k_seg_sort<SsTile>", "long": "k_seg_sort<SsRun>",
               "huge": "k_split", "scan": "k_scan", "map": "k_inverse_map", "partition": "k_scan"}[ph]
     byts = per_op[ph] * launches_total
-    achieved = byts / (ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get((scale, ph))
-    return {"bound": "hbm", "kernel": kernel, "phase": ph, "achieved": round(achieved, 1),
-            "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
-            "traffic": traffic, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
-            "frac_of_nominal_7900gbs": round(achieved / 7900.0, 4),
-            "avg_launch_ms": round(ms / cnt, 4),
-            "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
+    sec = ms * 1e-3
+    achieved = byts / sec / 1e9
+    out = {"bound": "hbm", "kernel": kernel, "phase": ph, "achieved": round(achieved, 1),
+           "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+           "traffic": None, "alg_bytes_per_launch": per_op[ph], "launches": cnt,
+           "frac_of_nominal_7900gbs": round(achieved / 7900.0, 4),
+           "avg_launch_ms": round(ms / cnt, 4),
+           "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
+    if ph == "gather":
+        with_lookup = (per_op[ph] + 4 * nnz) * launches_total / sec / 1e9
+        out["frac_incl_lookup"] = round(with_lookup / peak_gbs, 4)
+        if GATHER_DRAM_BYTES_PER_ENTRY is not None:
+            out["traffic"] = int(GATHER_DRAM_BYTES_PER_ENTRY * nnz)
+        if lookup_peak:
+            rate = nnz * launches_total / sec
+            out["lookup_roofline"] = {"achieved": round(rate / 1e9, 2), "peak": lookup_peak["g_per_s"],
+                                      "unit": "G lookups/s", "frac": round(rate / 1e9 / lookup_peak["g_per_s"], 4),
+                                      "table_bytes": lookup_peak["table_bytes"], "probe": lookup_peak["probe"]}
+    return out
+
+
+def lookup_probe(table_elems, device, n_lookups=1 << 28):
+    """Measured rate of random 4-byte lookups into an int32 table of `table_elems` entries
+    (PyTorch's gather of uniformly random indices, best of 3 after a warm-up; each lookup
+    also streams its 4-byte index in and its result out): the ceiling of a relabel step
+    whose map has that size."""
+    import torch
+    t = torch.arange(table_elems, dtype=torch.int32, device=device)
+    g = torch.Generator(device=device).manual_seed(7)
+    idx = torch.randint(0, table_elems, (n_lookups,), generator=g, device=device, dtype=torch.int64).to(torch.int32)
+    out = torch.empty(n_lookups, dtype=torch.int32, device=device)
+    torch.index_select(t, 0, idx, out=out)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        torch.index_select(t, 0, idx, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    del t, idx, out
+    torch.cuda.empty_cache()
+    return {"g_per_s": round(n_lookups / (best * 1e-3) / 1e9, 2), "table_bytes": table_elems * 4,
+            "probe": f"torch.index_select of {n_lookups} uniform random int32 indices (index read and "
+                     "result write included), best of 3"}
 
 
 def time_steps(fn, steps, warmup, ws):
@@ -251,6 +291,63 @@ def time_steps(fn, steps, warmup, ws):
     return ev[0].elapsed_time(ev[1])
 
 
+def run_rows_limited(args, ctx, A, dev):
+    """Profiling case (--rows-limit R): the first R rows of the headline matrix with all
+    its columns, B = P A Q^T with independent random p (R) and q (all columns): the
+    kernels see the full-size column maps at a few GB on the device."""
+    import torch
+    import synth
+    from paper_2509_20776_gb300 import CSR
+    R = min(args.rows_limit, A.nrows)
+    nz = int(A.rowptr[R])
+    Ar = CSR(R, A.ncols, A.rowptr[:R + 1].clone(), A.colidx[:nz].clone(), A.values[:nz].clone())
+    del A
+    torch.cuda.empty_cache()
+    p = synth.random_permutation(R, 1, 0, device=dev)
+    q = synth.random_permutation(Ar.ncols, 1, 1, device=dev)
+    B = ctx.sp_permute(Ar, p, q)
+    ms = time_steps(lambda: ctx.sp_permute(Ar, p, q, sync=False, out=B), max(1, args.steps), args.warmup, 1)
+    ctx.sync()
+    return {"rows_limit": R, "ncols": Ar.ncols, "nnz": nz, "ms_per_op": round(ms / max(1, args.steps), 4),
+            "workload": "first R rows of the headline matrix, P A Q^T with random p, q"}
+
+
+def log_summary(res):
+    """One short line per measured operation on stderr (the driver keeps the tail)."""
+    def line(name, d, ms_key="ms_per_op"):
+        if not isinstance(d, dict) or "value" not in d:
+            return
+        log(f"SUMMARY {name}: {d.get('workload', '')[:70]} | {d.get(ms_key, '?')} ms | "
+            f"{d['value'] / 1e9:.2f} G entries/s | op frac {d.get('op_roofline_frac', '-')} | "
+            f"alg bytes {d.get('alg_bytes_per_op', '-')}")
+    r = res.get("roofline", {})
+    log(f"SUMMARY permute: {res['config']['workload'][:70]} | {res['ms_per_step'] / res['config']['ops_per_step']:.3f} "
+        f"ms/op | {res['value'] / 1e9:.2f} G entries/s | op frac {res['op_roofline']['frac']} | "
+        f"alg bytes {res['op_roofline']['bytes_per_op']} | top kernel {r.get('kernel')} frac {r.get('frac')} "
+        f"lookup frac {r.get('lookup_roofline', {}).get('frac')}")
+    if "e2e" in res:
+        log(f"SUMMARY permute e2e: {res['e2e']['ms_per_step']} ms/step | {res['e2e']['value'] / 1e9:.2f} G entries/s")
+    ops = res.get("ops", {})
+    ex = ops.get("extract", {})
+    line("extract", ex)
+    line("extract contiguous", ex.get("contiguous_block"))
+    line("extract mesh", ex.get("mesh"))
+    asg = ops.get("assign", {})
+    line("assign", asg)
+    line("assign contiguous", asg.get("contiguous"))
+    line("assign+permute fused", asg.get("assign_permute"))
+    bt = ops.get("batch_extract", {})
+    if "batched_ms" in bt:
+        log(f"SUMMARY batch: {bt['batched_ms']} ms batched vs {bt['plain_ms']} ms plain | graph fill "
+            f"{bt['graph_fill_ms']} ms | {bt['batched_value'] / 1e9:.2f} G entries/s")
+    sv = ops.get("serve", {})
+    for k, v in sv.items():
+        if k.startswith("load_"):
+            log(f"SUMMARY serve {k}: served p50/p99 {v['served']['p50_ms']}/{v['served']['p99_ms']} ms "
+                f"{v['served']['value'] / 1e9:.2f} G/s | plain {v['plain']['p50_ms']}/{v['plain']['p99_ms']} ms "
+                f"{v['plain']['value'] / 1e9:.2f} G/s")
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -264,6 +361,9 @@ def run_ours(args, ws, rank, local):
     log("generating the permutation workload")
     A, ops = permute_workload(args.scale, dev)
     log(f"generated: {A.nrows} rows, {A.nnz} entries")
+    if args.rows_limit:
+        del ops
+        return run_rows_limited(args, ctx, A, dev)
     Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
     nnz, m = A.nnz, A.nrows
     outs = [ctx.sp_permute(Ad, p, q, sync=True) for _, p, q in ops]  # also validates
@@ -290,7 +390,8 @@ def run_ours(args, ws, rank, local):
     ms = max_over_ranks(ms, ws)
     out_per_step = nnz * len(ops)
     value = out_per_step * args.steps * ws / (ms * 1e-3)
-    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, args.scale)
+    lk = lookup_probe(A.ncols, dev)
+    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, lk)
     # whole op: read and write col + val per entry, p and rowptr pair per row, q and qinv
     alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols
     op_frac = alg_bytes_op * len(ops) * args.steps / (ms * 1e-3) / 1e9 / hbm
@@ -298,7 +399,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32 indices / fp32 values moved as 32-bit words",
+        "vs_baseline": None, "dtype": "int64 rowptr / int32 col / fp32 values (moved as 32-bit words)",
         "data": "synthetic (seeded R-MAT; the paper's SuiteSparse graphs are not available)",
         "config": {"workload": WORKLOAD.format(scale=args.scale), "rows": m, "nnz": nnz, "ops_per_step": len(ops),
                    "l2": "inputs larger than L2 (no flush needed)",
@@ -339,6 +440,8 @@ def run_ours(args, ws, rank, local):
         result["cpu_baseline"] = cpu_baseline(args)
         log("cpu baseline done")
     ctx.close()
+    if rank == 0:
+        log_summary(result)
     return result
 
 

@@ -139,10 +139,16 @@ SP_API int64_t sp_ctx_error_detail(const sp_ctx* ctx);
  *                          in bucket order and sorted by a later pass: 128 (default) to
  *                          4096;
  *   SP_OPT_COUNT_ROWS      rows a warp takes per step in the kept-entry count of
- *                          extraction / assignment: 1 to 4 (default 4);
- *   SP_OPT_FILL_ROWS       the same for their compacting fill: 1 or 2 (default 2);
+ *                          assignment: 1 to 4 (default 4);
+ *   SP_OPT_FILL_ROWS       the same for its compacting fill: 1 or 2 (default 2);
  *   SP_OPT_BATCH_ROWS      rows a warp serves at once in the batched extraction's count
- *                          and fill (32 / rows lanes per row): 1 (default), 2, 4 or 8. */
+ *                          and fill (32 / rows lanes per row): 1 (default), 2, 4 or 8;
+ *   SP_OPT_IDENTIFY        how an extraction identifies the kept columns (general or
+ *                          ascending J): 0 = rank map over the columns (a membership bit
+ *                          and a rank per column, one position per member of J: n/4 +
+ *                          |J| * idx bytes, two lookups per entry; default); 1 = J sorted
+ *                          once, binary search per stored entry (Algorithm 5's search:
+ *                          |J| log |J| set-up, no column-sized table). */
 typedef enum sp_option {
   SP_OPT_SPIN_LIMIT = 0,
   SP_OPT_SCAN_HOLD_TILE = 1,
@@ -152,7 +158,8 @@ typedef enum sp_option {
   SP_OPT_HEAVY = 5,
   SP_OPT_COUNT_ROWS = 6,
   SP_OPT_FILL_ROWS = 7,
-  SP_OPT_BATCH_ROWS = 8
+  SP_OPT_BATCH_ROWS = 8,
+  SP_OPT_IDENTIFY = 9
 } sp_option;
 SP_API sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value);
 
@@ -166,7 +173,7 @@ SP_API sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value);
 typedef enum sp_op { SP_OP_PERMUTE = 0, SP_OP_EXTRACT = 1, SP_OP_ASSIGN = 2, SP_OP_BATCH = 3 } sp_op;
 typedef struct sp_tune_entry {
   int32_t op;        /* sp_op */
-  int32_t tile_shape, heavy, count_rows, fill_rows, batch_rows; /* as the options above */
+  int32_t tile_shape, heavy, count_rows, fill_rows, batch_rows, identify; /* as the options above */
   int64_t size_max;  /* the entry covers calls of size <= size_max */
 } sp_tune_entry;
 SP_API sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n);

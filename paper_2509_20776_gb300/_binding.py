@@ -22,10 +22,11 @@ SP_ASSIGN_REPLACE, SP_ASSIGN_SELECT2ND, SP_ASSIGN_PLUS = 0, 1, 2
 SP_OPT_SPIN_LIMIT, SP_OPT_SCAN_HOLD_TILE, SP_OPT_VALIDATE, SP_OPT_TIMING = 0, 1, 2, 3
 # kernel shapes (run-time; every value gives the same output)
 SP_OPT_TILE_SHAPE, SP_OPT_HEAVY, SP_OPT_COUNT_ROWS, SP_OPT_FILL_ROWS, SP_OPT_BATCH_ROWS = 4, 5, 6, 7, 8
+SP_OPT_IDENTIFY = 9
 SHAPE_OPTIONS = {"tile_shape": SP_OPT_TILE_SHAPE, "heavy": SP_OPT_HEAVY, "count_rows": SP_OPT_COUNT_ROWS,
-                 "fill_rows": SP_OPT_FILL_ROWS, "batch_rows": SP_OPT_BATCH_ROWS}
+                 "fill_rows": SP_OPT_FILL_ROWS, "batch_rows": SP_OPT_BATCH_ROWS, "identify": SP_OPT_IDENTIFY}
 SHAPE_VALUES = {"tile_shape": (0, 1), "heavy": (128, 256, 512, 1024, 2048, 4096), "count_rows": (1, 2, 3, 4),
-                "fill_rows": (1, 2), "batch_rows": (1, 2, 4, 8)}
+                "fill_rows": (1, 2), "batch_rows": (1, 2, 4, 8), "identify": (0, 1)}
 OPS = {"permute": 0, "extract": 1, "assign": 2, "batch": 3}
 PHASES = ["map", "count", "scan", "partition", "tile", "long", "huge", "gather", "other"]
 STATUS = ["SP_OK", "SP_ERR_INVALID_ARG", "SP_ERR_SHAPE", "SP_ERR_INDEX_RANGE",
@@ -52,7 +53,7 @@ class sp_csr(ctypes.Structure):
 class sp_tune_entry(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("tile_shape", ctypes.c_int32), ("heavy", ctypes.c_int32),
                 ("count_rows", ctypes.c_int32), ("fill_rows", ctypes.c_int32), ("batch_rows", ctypes.c_int32),
-                ("size_max", ctypes.c_int64)]
+                ("identify", ctypes.c_int32), ("size_max", ctypes.c_int64)]
 
 
 def tune_entries(table) -> list:
@@ -83,7 +84,7 @@ def tune_array(table):
     arr = (sp_tune_entry * max(1, len(rows)))()
     for i, r in enumerate(rows):
         arr[i] = sp_tune_entry(r["op"], r["tile_shape"], r["heavy"], r["count_rows"], r["fill_rows"],
-                               r["batch_rows"], r["size_max"])
+                               r["batch_rows"], r["identify"], r["size_max"])
     return arr, len(rows)
 
 

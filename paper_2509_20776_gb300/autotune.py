@@ -1,8 +1,8 @@
 """Autotuner for the library's run-time kernel shapes.
 
 The shapes (``SP_OPT_TILE_SHAPE``, ``SP_OPT_HEAVY``, ``SP_OPT_COUNT_ROWS``,
-``SP_OPT_FILL_ROWS``, ``SP_OPT_BATCH_ROWS`` in ``include/sp.h``) change how the kernels
-split the work, never the output.  For each (op, size class) the tuner times candidate
+``SP_OPT_FILL_ROWS``, ``SP_OPT_BATCH_ROWS``, ``SP_OPT_IDENTIFY`` in ``include/sp.h``)
+change how the kernels split the work or identify kept columns, never the output.  For each (op, size class) the tuner times candidate
 shapes on a representative workload through the library's own calls, checks that every
 candidate's output is bit-identical to the one of the default shapes, and writes a table
 that ``Context.set_tuning`` installs: afterwards every call of that op whose size falls in
@@ -27,13 +27,13 @@ from ._binding import SHAPE_VALUES, Context
 # knobs each op's kernels read, in the order they are tuned
 KNOBS = {
     "permute": ("tile_shape", "heavy"),
-    "extract": ("count_rows", "fill_rows", "tile_shape", "heavy"),
+    "extract": ("identify", "tile_shape", "heavy"),
     "assign": ("count_rows", "fill_rows", "tile_shape", "heavy"),
     "batch": ("batch_rows", "tile_shape", "heavy"),
 }
 SEARCH = {"tile_shape": (0, 1), "heavy": (128, 256, 512), "count_rows": (1, 2, 4), "fill_rows": (1, 2),
-          "batch_rows": (1, 2, 4, 8)}
-DEFAULT = {"tile_shape": 0, "heavy": 128, "count_rows": 4, "fill_rows": 2, "batch_rows": 1}
+          "batch_rows": (1, 2, 4, 8), "identify": (0, 1)}
+DEFAULT = {"tile_shape": 0, "heavy": 128, "count_rows": 4, "fill_rows": 2, "batch_rows": 1, "identify": 0}
 assert all(set(v) <= set(SHAPE_VALUES[k]) for k, v in SEARCH.items())
 
 

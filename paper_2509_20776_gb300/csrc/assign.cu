@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "plan.h"
 #include "rowsort.cuh"
+#include "segcopy.cuh"
 
 namespace sp {
 
@@ -187,40 +188,47 @@ struct AssignLen {
   }
 };
 
-// Assembly gather of A': row r comes from A itself or, for a row of I, from the staged
-// rebuilt row; staged positions carry bit 62 (positions stay far below 2^62).
-template <class RP, class CIt, class VTt, class IX>
-struct AssignGs {
-  using CI = CIt;
-  using VT = VTt;
-  static constexpr long long kStaged = 1ll << 62;
-  const RP* rpA;
-  const CI* colA;
-  const VT* valA;
+// Assembly of A' as segments (segcopy.cuh): a segment starts at row 0, at every row of I
+// and after every row of I; a run of rows outside I is contiguous in A and in A', a row
+// of I is its staged rebuilt row.  The scan over the rows numbers the segment starts; its
+// store writes each segment (first output position, source position) and the count.
+template <class IX>
+struct SegStart {
   const IX* rowmap;
-  const long long* vt;
-  const CI* tcol;
-  const VT* tval;
-  long long nnzA, ntemp;
-  __device__ long long src(long long r) const {
+  __device__ bool operator()(long long r) const {
+    return r == 0 || (long long)rowmap[r] >= 0 || (long long)rowmap[r - 1] >= 0;
+  }
+};
+template <class IX>
+struct SegCount {
+  SegStart<IX> st;
+  __device__ long long operator()(long long r) const { return st(r) ? 1 : 0; }
+};
+template <class RP, class IX>
+struct SegStore {
+  SegStart<IX> st;
+  const IX* rowmap;
+  const RP* rpA;
+  const long long* vt;  // row pointer of the staged rebuilt rows
+  const long long* vp_out;
+  CopySeg* segs;
+  long long m, cap;
+  long long* nseg;
+  DevStatus* dst;
+  __device__ void operator()(long long r, long long j) const {
+    if (j > cap) {
+      dev_fail(dst, SP_ERR_INTERNAL, -33);
+      return;
+    }
+    if (r == m) {  // j = number of segments; the sentinel closes the last one
+      *nseg = j;
+      segs[j] = CopySeg{vp_out[m], 0};
+      return;
+    }
+    if (!st(r)) return;
     const long long i = (long long)rowmap[r];
-    return i >= 0 ? (vt[i] | kStaged) : (long long)rpA[r];
+    segs[j] = CopySeg{vp_out[r], i >= 0 ? (vt[i] | kSegB) : (long long)rpA[r]};
   }
-  __device__ CI col(long long pos) const {
-    if (pos & kStaged) {
-      const long long q = pos & ~kStaged;
-      return q < ntemp ? ld_stream(tcol + q) : CI(0);
-    }
-    return (pos >= 0 && pos < nnzA) ? ld_stream(colA + pos) : CI(0);
-  }
-  __device__ VT val(long long pos) const {
-    if (pos & kStaged) {
-      const long long q = pos & ~kStaged;
-      return q < ntemp ? ld_stream(tval + q) : VT(0);
-    }
-    return (pos >= 0 && pos < nnzA) ? ld_stream(valA + pos) : VT(0);
-  }
-  __device__ CI map(CI c) const { return c; }
 };
 
 template <class RP, class CI, class IX>
@@ -373,13 +381,18 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   const long long m = A.nrows, nI = pl->nI, nt = pl->nnz_temp, nnz_out = pl->nnz_out;
   SP_TRY(store_rowptr(ctx, s, pl->vp_out, m + 1, Ap->rowptr_type, Ap->rowptr));
   if (nnz_out == 0) return SP_OK;
+  const long long segcap = m < 2 * nI + 1 ? m : 2 * nI + 1;
+  const long long nchunks = (nnz_out + SC_CH - 1) / SC_CH;
   Carver cv;
   const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
   const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
   const size_t o_tk = cv.reserve(16);
-  size_t r1[kRowsSlots], r2[kRowsSlots];
+  const size_t o_sg = cv.reserve(size_t(segcap + 1) * sizeof(CopySeg));
+  const size_t o_ns = cv.reserve(8);
+  const size_t o_cf = cv.reserve(size_t(nchunks) * 8);
+  const size_t o_sc = cv.reserve(scan_ws_bytes(m));
+  size_t r1[kRowsSlots];
   rows_reserve(cv, nI, nt, sizeof(VT), r1);
-  rows_reserve(cv, m, nnz_out, sizeof(VT), r2, false);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
@@ -392,13 +405,37 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
     const int kb = ceil_log2_u64(uint64_t(A.ncols));
     SP_TRY((run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nt, kb, w1, nullptr, true, tcol, tval)));
   }
-  // assembly: untouched rows from A, rows of I from the staging buffer
-  const AssignGs<RP, CI, VT, IX> g{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
-                                   static_cast<const VT*>(A.values), static_cast<const IX*>(pl->rowmap),
-                                   pl->vp, tcol, tval, A.nnz, nt};
-  const RowsWs w2 = rows_bind(cv, m, nnz_out, r2, false);
-  return run_rows(ctx, s, pl->vp_out, m, nnz_out, 0, w2, &g, false, static_cast<CI*>(Ap->colidx),
-                  static_cast<VT*>(Ap->values));
+  // assembly: runs of untouched rows from A, rows of I from the staging buffer
+  const IX* rowmap = static_cast<const IX*>(pl->rowmap);
+  CopySeg* segs = cv.at<CopySeg>(o_sg);
+  long long* nseg = cv.at<long long>(o_ns);
+  long long* chunk_first = cv.at<long long>(o_cf);
+  const SegStart<IX> st{rowmap};
+  SP_TRY(launch_scan(ctx, s, SegCount<IX>{st},
+                     SegStore<RP, IX>{st, rowmap, static_cast<const RP*>(A.rowptr), pl->vp, pl->vp_out, segs, m,
+                                      segcap, nseg, ctx->dstatus},
+                     m, cv.at<char>(o_sc), SP_PHASE_PARTITION));
+  const int nsm = ctx->num_sms;
+  SP_CUDA(cudaMemsetAsync(chunk_first, 0xFF, size_t(nchunks) * 8, s));
+  {
+    SP_PHASE(SP_PHASE_PARTITION);
+    k_seg_chunks<<<grid_for(segcap, 256, nsm * 8), 256, 0, s>>>(segs, nseg, nchunks, chunk_first);
+  }
+  SP_CUDA(cudaGetLastError());
+  using CW = std::conditional_t<sizeof(CI) == 4, uint32_t, unsigned long long>;
+  using VW = std::conditional_t<sizeof(VT) == 4, uint32_t, unsigned long long>;
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int vec = al(A.colidx) && al(A.values) && al(tcol) && al(tval) && al(Ap->colidx) && al(Ap->values);
+  {
+    SP_PHASE(SP_PHASE_GATHER);
+    const long long g = nchunks < 8ll * nsm ? nchunks : 8ll * nsm;
+    k_seg_copy<CW, VW><<<unsigned(g), SC_BLOCK, 0, s>>>(
+        segs, nseg, nnz_out, chunk_first, nchunks, static_cast<const CW*>(A.colidx), static_cast<const VW*>(A.values),
+        A.nnz, reinterpret_cast<const CW*>(tcol), reinterpret_cast<const VW*>(tval), nt,
+        static_cast<CW*>(Ap->colidx), static_cast<VW*>(Ap->values), vec, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
 }
 
 

@@ -72,6 +72,12 @@ __device__ __forceinline__ unsigned ld_map(const unsigned* p) {
                : "l"(p), "l"(l2_keep_policy()));
   return v;
 }
+// Lookups into tables larger than L2 (read at random, rarely reused): plain read-only
+// loads, so they do not displace the small tables that carry the evict-last hint.
+template <class T>
+__device__ __forceinline__ T ld_plain(const T* p) {
+  return __ldg(p);
+}
 // Write-once output: store with the evict-first (streaming) hint.
 template <class T>
 __device__ __forceinline__ void st_stream(T* p, T v) {
@@ -92,6 +98,18 @@ __device__ __forceinline__ void st_stream(T* p, T v) {
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   const unsigned d = unsigned(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+// 16-byte and single-word global -> shared copies (16-byte: both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_word(void* dst, const void* src) {
+  static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte words");
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  if constexpr (BYTES == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }

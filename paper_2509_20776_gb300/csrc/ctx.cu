@@ -201,6 +201,10 @@ sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
       if (value >= 0 && value != 1 && value != 2 && value != 4 && value != 8) return SP_ERR_INVALID_ARG;
       ctx->opt.batch_rows = value < 0 ? 1 : int(value);
       return SP_OK;
+    case SP_OPT_IDENTIFY:
+      if (value > 1) return SP_ERR_INVALID_ARG;
+      ctx->opt.identify = value < 0 ? 0 : int(value);
+      return SP_OK;
   }
   return SP_ERR_INVALID_ARG;
 }
@@ -223,7 +227,8 @@ sp_status sp_ctx_set_tuning(sp_ctx* ctx, const sp_tune_entry* table, int n) {
                     (e.heavy < 0 || (e.heavy >= 128 && e.heavy <= 4096)) && e.count_rows != 0 &&
                     e.count_rows <= 4 && e.fill_rows != 0 && e.fill_rows <= 2 &&
                     (e.batch_rows < 0 || e.batch_rows == 1 || e.batch_rows == 2 || e.batch_rows == 4 ||
-                     e.batch_rows == 8);
+                     e.batch_rows == 8) &&
+                    e.identify <= 1;
     if (!ok) return SP_ERR_INVALID_ARG;
   }
   ctx->tuning.assign(table, table + n);

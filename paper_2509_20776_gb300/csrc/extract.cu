@@ -1,52 +1,20 @@
 // sp_extract: B = A(I, J), B[i, j] = A[I[i], J[j]]  (Sec. 2.2; HipExtract, Algorithms 3, 5).
 //
-// Identify: J becomes a dense inverse map jinv (old column -> position in J, -1 when
-// absent: the SpQvec_inv of Algorithm 3); the first pass of Algorithm 5 counts the
-// entries of each selected row that survive (a warp ballot + popc per 32 entries);
-// the exclusive scan of the counts is B's row pointer.  Fill: the surviving entries
-// are gathered, relabelled through jinv and sorted per row (Algorithm 5's second pass
-// and the Build step).  Rows of I may repeat; J must be distinct.
+// Identify: the columns of J become a rank map (membership bit + rank per column and the
+// position of every member: the SpQvec_inv of Algorithm 3 in compact form) or J sorted
+// once (Algorithm 5's binary search); the first pass of Algorithm 5 counts the entries
+// of each selected row that survive (a warp ballot + popc per 32 entries); the
+// exclusive scan of the counts is B's row pointer.  Fill: the surviving entries are
+// relabelled and sorted per row and written once at their final place (Algorithm 5's
+// second pass and the Build step; extract_rows.cuh).  Rows of I may repeat; J with
+// repeats takes the multi-map path below.
 #include "dispatch.h"
+#include "extract_rows.cuh"
 #include "kernels.cuh"
 #include "plan.h"
 #include "rowsort.cuh"
 
 namespace sp {
-
-template <class RP, class CIt, class VTt, class IX>
-struct ExtractLoader {
-  using CI = CIt;
-  using VT = VTt;
-  const RP* rowptr;
-  const CI* col;
-  const VT* val;
-  const IX* I;
-  const IX* jinv;         // column -> position in J, -1 when absent
-  const uint32_t* jbits;  // membership bitmap of J (n bits, small enough to stay in L2)
-  long long m, n, nnz;
-  __device__ RowSrc row(long long i) const {
-    const long long r = (long long)I[i];
-    if (r < 0 || r >= m) return RowSrc{0, 0, 0, 0};
-    const long long s = (long long)rowptr[r], e = (long long)rowptr[r + 1];
-    if (s < 0 || e < s || e > nnz) return RowSrc{0, 0, 0, 0};
-    return RowSrc{s, 0, e - s, 0};
-  }
-  static constexpr bool kAllKept = false;
-  static constexpr bool kLoadVals = true;
-  static constexpr bool kEagerVals = true;  // about half the entries survive: cheaper than a trip
-  static constexpr bool kRowCtx = false;
-  __device__ const CI* cols(int) const { return col; }
-  __device__ const VT* vals(int) const { return val; }
-  __device__ bool test(int, long long c) const {
-    return c >= 0 && c < n && ((ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u);
-  }
-  __device__ bool map(int, long long c, uint32_t& key) const {
-    if (!test(0, c)) return false;  // the inverse map is read only for kept entries
-    const long long j = (long long)ld_map(jinv + c);
-    key = uint32_t(j);
-    return j >= 0;
-  }
-};
 
 // Consecutive J = [j0, j1): the kept entries of a (sorted) row form one segment, found by
 // binary search, and keep their order (the paper's binary-search idea of Alg. 5 applied
@@ -213,14 +181,20 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const long long m = A.nrows, n = A.ncols, nnz = A.nnz, nI = pl->nI, nJ = pl->nJ;
   const IX* I = static_cast<const IX*>(pl->I);
   const IX* J = static_cast<const IX*>(pl->J);
+  pl->identify = ctx->cur.identify;
+  const long long nw32 = (n + 31) / 32;
   Carver cv;
-  const size_t o_jinv = cv.reserve(size_t(n) * sizeof(IX));
-  const size_t o_jb = cv.reserve(size_t((n + 31) / 32) * 4);
+  const size_t o_meta = cv.reserve(pl->identify == 0 ? size_t(nw32) * 8 : 0);
+  const size_t o_jrp = cv.reserve(pl->identify == 0 ? size_t(nJ) * sizeof(IX) : 0);
+  const size_t o_jsk = cv.reserve(pl->identify == 1 ? size_t(nJ) * 4 : 0);
+  const size_t o_jsp = cv.reserve(pl->identify == 1 ? size_t(nJ) * 4 : 0);
+  const size_t o_vp2 = cv.reserve(16);
+  const size_t o_jb = cv.reserve(size_t(nw32) * 4);
   const size_t o_vp = cv.reserve(size_t(nI + 1) * 8);
   pl->list_cap = nI + 1;
   const size_t o_cl = cv.reserve(size_t(pl->list_cap) * 8);
   const size_t o_cn = cv.reserve(64);
-  const size_t o_scan = cv.reserve(scan_ws_bytes(nI));
+  const size_t o_scan = cv.reserve(scan_ws_bytes(nI > nw32 ? nI : nw32));
   const size_t o_ss = cv.reserve(size_t(nI) * 8);
   const size_t o_sn = cv.reserve(size_t(nI) * 8);
   const size_t o_fl = cv.reserve(16);  // J strictly ascending / consecutive / repeats
@@ -228,9 +202,11 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   cv.bind(pl->buf);
   pl->sstart = cv.at<long long>(o_ss);
   pl->slen = cv.at<long long>(o_sn);
-  IX* jinv = cv.at<IX>(o_jinv);
+  pl->jmeta = cv.at<unsigned long long>(o_meta);
+  pl->jrpos = cv.at<void>(o_jrp);
+  pl->jsk = cv.at<uint32_t>(o_jsk);
+  pl->jsp = cv.at<uint32_t>(o_jsp);
   uint32_t* jbits = cv.at<uint32_t>(o_jb);
-  pl->jmap = jinv;
   pl->jbits = jbits;
   pl->vp = cv.at<long long>(o_vp);
   pl->cl_rows = cv.at<long long>(o_cl);
@@ -325,43 +301,73 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     pl->nnz_out = pl->h_tail[0];
     return SP_OK;
   }
+  // general or ascending J: identify tables, then the count
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
-  SP_CUDA(cudaMemsetAsync(jinv, 0xFF, size_t(n) * sizeof(IX), s));
-  if (nJ > 0) {
+  if (pl->identify == 0) {
+    if (nJ > 0) {
+      // rank words: bits | exclusive prefix of the words' popcounts; then the positions
+      SP_TRY(launch_scan(ctx, s, LoadPopc{jbits}, StoreRank{jbits, pl->jmeta, nw32}, nw32, cv.at<char>(o_scan),
+                         SP_PHASE_MAP));
+      {
+        SP_PHASE(SP_PHASE_MAP);
+        k_jrank_pos<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, pl->jmeta, static_cast<IX*>(pl->jrpos));
+      }
+      SP_CUDA(cudaGetLastError());
+    }
+  } else if (nJ > 0) {
+    // J sorted once, its positions carried as values (one row of nJ keys)
     {
       SP_PHASE(SP_PHASE_MAP);
-      k_inverse_map<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, n, jinv, ctx->dstatus,
-                                                                    SP_ERR_DUPLICATE_INDEX);
+      k_jsorted_init<IX><<<grid_for(nJ, 256, nsm * 8), 256, 0, s>>>(J, nJ, pl->jsk, pl->jsp);
     }
     SP_CUDA(cudaGetLastError());
+    long long* vp2 = cv.at<long long>(o_vp2);
+    pl->h_tail[4] = 0;
+    pl->h_tail[5] = nJ;
+    SP_CUDA(cudaMemcpyAsync(vp2, pl->h_tail + 4, 16, cudaMemcpyHostToDevice, s));
+    Carver cw;
+    size_t ro[kRowsSlots];
+    rows_reserve(cw, 1, nJ, 4, ro);
+    char* base;
+    SP_TRY(ctx_workspace(ctx, cw.total(), s, &base));
+    cw.bind(base);
+    const RowsWs w = rows_bind(cw, 1, nJ, ro);
+    SP_TRY((run_rows<uint32_t, uint32_t, NoGather<uint32_t, uint32_t>>(ctx, s, vp2, 1, nJ, ceil_log2_u64(uint64_t(n)),
+                                                                       w, nullptr, true, pl->jsk, pl->jsp)));
   }
   if (nI > 0) {
-    {
-      SP_PHASE(SP_PHASE_MAP);
-      k_range_check<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-    ExtractLoader<RP, CI, uint32_t, IX> ct{static_cast<const RP*>(A.rowptr),
-                                           static_cast<const CI*>(A.colidx), nullptr, I, jinv,
-                                           jbits, m, n, nnz};
-    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap, pl->sstart, pl->slen};
-    {
-      SP_PHASE(SP_PHASE_COUNT);
-      k_count_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ct, nI, pl->vp, cl, ctx->cur.count_rows,
-                                                                         ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-    {
-      SP_PHASE(SP_PHASE_COUNT);
-      k_count_long<<<nsm, 1024, 0, s>>>(ct, pl->vp, cl, pl->counters + 3, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
+    const RP* rp = static_cast<const RP*>(A.rowptr);
+    const CI* ci = static_cast<const CI*>(A.colidx);
+    const long long groups = (nI + 31) / 32;
+    const int g = grid_for(groups * 32, XB, nsm * 8);
+    CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
+    auto count = [&](auto test) -> sp_status {
+      using Test = decltype(test);
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        k_xcount<RP, CI, IX, Test><<<g, XB, 0, s>>>(rp, ci, I, nI, m, nnz, test, pl->vp, pl->sstart, pl->slen,
+                                                    pl->cl_rows, pl->counters + 0, pl->list_cap, pl->counters + 4,
+                                                    ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      const XLongRows<CI, uint32_t, Test> lr{ci, nullptr, test, pl->sstart, pl->slen};
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        k_count_long<<<nsm, 1024, 0, s>>>(lr, pl->vp, cl, pl->counters + 3, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      return SP_OK;
+    };
+    if (pl->identify == 0) SP_TRY(count(JBits{jbits, n}));
+    else SP_TRY(count(JSorted{pl->jsk, pl->jsp, nJ}));
   }
   SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
                      StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_scan)));
   SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 6, pl->counters + 4, 4, cudaMemcpyDeviceToHost, s));
   SP_TRY(ctx_collect(ctx, s));
   pl->nnz_out = pl->h_tail[0];
+  pl->n_slow = (long long)*reinterpret_cast<const unsigned*>(pl->h_tail + 6);
   return SP_OK;
 }
 
@@ -404,39 +410,53 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
     const int kb = ceil_log2_u64(uint64_t(pl->nJ));
     return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nnz_out, kb, w, nullptr, true, oc, ov);
   }
-  const bool sorted = pl->j_shape == 1;  // ascending J: the fill keeps rows in order
-  rows_reserve(cv, nI, nnz_out, sizeof(VT), ro, !sorted);
+  const bool sorted = pl->j_shape == 1;  // ascending J: the relabelling keeps rows in order
+  rows_reserve(cv, nI, nnz_out, sizeof(VT), ro, !sorted, pl->n_slow);
   const size_t o_tk = cv.reserve(16);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
-  // every listed row's source range was recorded by the count (k_count_warp)
-  RecordedRows<ExtractLoader<RP, CI, VT, IX>> ld{
-      {static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx), static_cast<const VT*>(A.values),
-       static_cast<const IX*>(pl->I), static_cast<const IX*>(pl->jmap),
-       static_cast<const uint32_t*>(pl->jbits), A.nrows, A.ncols, A.nnz},
-      pl->sstart, pl->slen};
-  // fill: kept entries, relabelled through jinv, into their output rows in source order
+  const RowsWs w = rows_bind(cv, nI, nnz_out, ro, !sorted, pl->n_slow);
   unsigned* ticket = cv.at<unsigned>(o_tk);
   SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
+  SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
   const int nsm = ctx->num_sms;
-  {
-    SP_PHASE(SP_PHASE_GATHER);
-    k_fill_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ld, nI, pl->vp, oc, ov, ctx->cur.fill_rows,
-                                                                      ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
-  {
-    SP_PHASE(SP_PHASE_GATHER);
-    k_fill_long<<<nsm, 1024, 0, s>>>(ld, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, oc, ov,
-                                     ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
-  if (sorted) return SP_OK;
-  // sort every row in place
-  const RowsWs w = rows_bind(cv, nI, nnz_out, ro);
   const int kb = ceil_log2_u64(uint64_t(pl->nJ));
-  return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nnz_out, kb, w, nullptr, true, oc, ov);
+  const CI* ci = static_cast<const CI*>(A.colidx);
+  const VT* vv = static_cast<const VT*>(A.values);
+  const long long groups = (nI + 31) / 32;
+  const int g = grid_for(groups * 32, XB, nsm * 8);
+  auto fill = [&](auto rel) -> sp_status {
+    using Rel = decltype(rel);
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      if (sorted)
+        k_xfill<CI, VT, Rel, true><<<g, XB, 0, s>>>(ci, vv, rel, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
+                                                    w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap, kb,
+                                                    ctx->dstatus);
+      else
+        k_xfill<CI, VT, Rel, false><<<g, XB, 0, s>>>(ci, vv, rel, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
+                                                     w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap,
+                                                     kb, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    // rows of more than SRC_LONG source entries: one CTA each, kept entries in source order
+    const XLongRows<CI, VT, Rel> lr{ci, vv, rel, pl->sstart, pl->slen};
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_fill_long<<<nsm, 1024, 0, s>>>(lr, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket, oc, ov,
+                                       ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+  };
+  if (pl->identify == 0)
+    SP_TRY(fill(JRank<IX>{pl->jmeta, static_cast<const IX*>(pl->jrpos), A.ncols}));
+  else
+    SP_TRY(fill(JSorted{pl->jsk, pl->jsp, pl->nJ}));
+  if (sorted) return SP_OK;
+  // the rows the warp path did not sort (more than XFAST source entries)
+  return sort_queued<CI, VT>(ctx, s, w, kb, oc, ov);
 }
 
 sp_status plan_release(sp_ctx* ctx, sp_plan* pl) {

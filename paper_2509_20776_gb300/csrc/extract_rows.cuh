@@ -1,0 +1,418 @@
+// Extraction by rows (Sec. 2.2; HipExtract, Algorithm 5's two passes over the selected
+// rows), written for one GPU:
+//
+//   Identify.  The columns of J become either
+//     * a rank map (JRank): one 64-bit word per 32 columns holding the membership bits
+//       of J and the number of members in the words before it, plus jpos[r] = the
+//       position in J of the r-th smallest member.  A column c is kept when its bit is
+//       set; its new column is jpos[rank(c)].  The tables take n/4 + 4|J| bytes (16 MB +
+//       128 MB for n = 2^26, |J| = 2^25) instead of the 4n of a dense inverse map, and
+//       need no O(n) clearing beyond the n/4 bytes of words;
+//     * or J sorted once with its positions (JSorted), searched by binary search per
+//       stored entry: Algorithm 5's search, for small |J|.
+//   Count (k_xcount).  A warp takes 32 selected rows ("a block"): lane l resolves row
+//     i0 + l (I[i], range check, the row-pointer pair), so 32 index chains are in flight,
+//     and records the row's source start and length for the fill.  The warp then loads
+//     the columns of XC_ROWS rows at once (two per lane), tests each against J's bitmap
+//     and counts the members (ballot + popc).
+//   Fill (k_xfill).  A warp again takes 32 rows; for XF_ROWS rows at once it loads the
+//     columns and values, relabels the kept entries (rank word + position), compacts them
+//     (ballot slots) into a per-warp shared buffer and ranks each among its row's new
+//     columns, so a row of at most XFAST source entries is written once, sorted, at its
+//     final place.  Longer rows are written in source order and queued for the row sort.
+//   Random lookups, not HBM bytes, bound both passes: one 4-byte lookup per SM cycle
+//   while its table is L2-resident (~300 G/s on GB300), fewer for tables above ~100 MB.
+#pragma once
+
+#include "kernels.cuh"
+#include "rowsort.cuh"
+
+namespace sp {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int XFAST = 64;     // rows of at most this many source entries: masks, warp sort
+constexpr int XC_ROWS = 8;    // rows whose columns a counting warp loads together
+constexpr int XF_ROWS = 4;    // rows whose kept entries a filling warp loads together
+constexpr int XB = 256;       // threads per CTA of the count / fill
+constexpr unsigned kDropped = 0xFFFFFFFFu;  // padding key: never below a key
+
+// ---- identify ------------------------------------------------------------------------
+// Membership only (the count): the bitmap of J.
+struct JBits {
+  const uint32_t* bits;
+  long long n;
+  __device__ __forceinline__ bool test(long long c) const {
+    return c >= 0 && c < n && ((ld_map(bits + (c >> 5)) >> (c & 31)) & 1u);
+  }
+};
+
+// Rank map: word w = bits of columns [32w, 32w + 32) (low half) | members before 32w (high).
+template <class IX>
+struct JRank {
+  const unsigned long long* meta;
+  const IX* jpos;
+  long long n;
+  __device__ __forceinline__ bool test(long long c) const {
+    if (c < 0 || c >= n) return false;
+    const unsigned long long w = (unsigned long long)ld_map(reinterpret_cast<const long long*>(meta) + (c >> 5));
+    return (uint32_t(w) >> (c & 31)) & 1u;
+  }
+  __device__ __forceinline__ bool map(long long c, uint32_t& key) const {
+    if (c < 0 || c >= n) return false;
+    const unsigned long long w = (unsigned long long)ld_map(reinterpret_cast<const long long*>(meta) + (c >> 5));
+    const uint32_t bits = uint32_t(w), b = 1u << (c & 31);
+    if (!(bits & b)) return false;
+    const uint32_t r = uint32_t(w >> 32) + __popc(bits & (b - 1u));
+    key = uint32_t((long long)ld_plain(jpos + r));  // |J| words: larger than L2 at scale
+    return true;
+  }
+};
+
+// Sorted J: jk ascending (the values of J), jp[r] = position in J of jk[r].
+struct JSorted {
+  const uint32_t* jk;
+  const uint32_t* jp;
+  long long nJ;
+  __device__ __forceinline__ long long find(long long c) const {
+    if (c < 0 || c > 0xFFFFFFFFll) return -1;
+    long long lo = 0, hi = nJ;
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if ((long long)ld_map(jk + mid) < c) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo < nJ && (long long)ld_map(jk + lo) == c ? lo : -1;
+  }
+  __device__ __forceinline__ bool test(long long c) const { return find(c) >= 0; }
+  __device__ __forceinline__ bool map(long long c, uint32_t& key) const {
+    const long long r = find(c);
+    if (r < 0) return false;
+    key = ld_map(jp + r);
+    return true;
+  }
+};
+
+// Scan input / output of the rank words: popcount of each bitmap word, and the word
+// written with its exclusive prefix.
+struct LoadPopc {
+  const uint32_t* bits;
+  __device__ long long operator()(long long w) const { return __popc(bits[w]); }
+};
+struct StoreRank {
+  const uint32_t* bits;
+  unsigned long long* meta;
+  long long nw;
+  __device__ void operator()(long long w, long long v) const {
+    if (w < nw) meta[w] = (unsigned long long)bits[w] | ((unsigned long long)v << 32);
+  }
+};
+
+// jpos[rank(J[k])] = k
+template <class IX>
+__global__ void k_jrank_pos(const IX* __restrict__ J, long long nJ, long long n,
+                            const unsigned long long* __restrict__ meta, IX* __restrict__ jpos) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nJ;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long c = (long long)J[k];
+    if (c < 0 || c >= n) continue;  // reported by the bitmap pass
+    const unsigned long long w = meta[c >> 5];
+    const uint32_t b = 1u << (c & 31);
+    jpos[uint32_t(w >> 32) + __popc(uint32_t(w) & (b - 1u))] = IX(k);
+  }
+}
+
+// the sorted identify's input: J's values as 32-bit keys, positions as values
+template <class IX>
+__global__ void k_jsorted_init(const IX* __restrict__ J, long long nJ, uint32_t* __restrict__ jk,
+                               uint32_t* __restrict__ jp) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nJ;
+       k += (long long)gridDim.x * blockDim.x) {
+    jk[k] = uint32_t((long long)J[k]);  // in range (checked by the bitmap pass)
+    jp[k] = uint32_t(k);
+  }
+}
+
+// ---- count ---------------------------------------------------------------------------
+// cnt[i] = kept entries of selected row i (rows of more than SRC_LONG source entries are
+// listed for k_count_long instead); rs0 / rsn = source start / length of every row;
+// *n_slow += rows of more than XFAST source entries (the fill queues their sort).
+template <class RP, class CI, class IX, class Test>
+__global__ void __launch_bounds__(XB, 4) k_xcount(const RP* __restrict__ rowptr, const CI* __restrict__ col,
+                                                 const IX* __restrict__ I, long long nI, long long m, long long nnz,
+                                                 Test test, long long* __restrict__ cnt, long long* __restrict__ rs0,
+                                                 long long* __restrict__ rsn, long long* __restrict__ cl_rows,
+                                                 unsigned* n_cl, long long cl_cap, unsigned* n_slow, DevStatus* st) {
+  constexpr int R = XC_ROWS;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i0 = w0 * 32; i0 < nI; i0 += nw * 32) {
+    const long long i = i0 + lane;
+    long long s = 0, L = 0;
+    if (i < nI) {
+      const long long r = (long long)I[i];
+      if (r < 0 || r >= m) {
+        dev_fail(st, SP_ERR_INDEX_RANGE, i);
+      } else {
+        const long long a = (long long)rowptr[r], b = (long long)rowptr[r + 1];
+        if (a >= 0 && b >= a && b <= nnz) {
+          s = a;
+          L = b - a;
+        }
+      }
+      rs0[i] = s;
+      rsn[i] = L;
+    }
+    const unsigned slow = __ballot_sync(kFull, L > XFAST);
+    if (lane == 0 && slow) atomicAdd(n_slow, unsigned(__popc(slow)));
+    if (L > SRC_LONG) push_row(cl_rows, n_cl, cl_cap, i, st);
+    long long mine = 0;
+    const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
+    for (int g = 0; g < nr; g += R) {
+      long long ss[R];
+      int LL[R];
+      CI c0[R], c1[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
+        const long long l = __shfl_sync(kFull, L, (g + u) & 31);
+        LL[u] = (g + u < nr && l <= SRC_LONG) ? int(l) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        c0[u] = lane < LL[u] ? ld_stream(col + ss[u] + lane) : CI(0);
+        c1[u] = lane + 32 < LL[u] ? ld_stream(col + ss[u] + 32 + lane) : CI(0);
+      }
+      bool k0[R], k1[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        k0[u] = lane < LL[u] && test.test((long long)c0[u]);
+        k1[u] = lane + 32 < LL[u] && test.test((long long)c1[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        long long c = __popc(__ballot_sync(kFull, k0[u])) + __popc(__ballot_sync(kFull, k1[u]));
+        // rows of XFAST < L <= SRC_LONG entries: the rest in batches of LOAD_U x 32
+        for (int e0 = 64; e0 < LL[u]; e0 += 32 * LOAD_U) {
+          CI cc[LOAD_U];
+#pragma unroll
+          for (int v = 0; v < LOAD_U; ++v) {
+            const int e = e0 + v * 32 + lane;
+            cc[v] = e < LL[u] ? ld_stream(col + ss[u] + e) : CI(0);
+          }
+#pragma unroll
+          for (int v = 0; v < LOAD_U; ++v) {
+            const int e = e0 + v * 32 + lane;
+            c += __popc(__ballot_sync(kFull, e < LL[u] && test.test((long long)cc[v])));
+          }
+        }
+        if (lane == g + u) mine = c;
+      }
+    }
+    if (i < nI && L <= SRC_LONG) cnt[i] = mine;
+  }
+}
+
+// ---- fill ----------------------------------------------------------------------------
+template <class CI, class VT>
+__device__ __forceinline__ void x_put(CI* out_col, VT* out_val, long long pos, long long end, uint32_t key,
+                                      const VT& v, DevStatus* st) {
+  if (pos < end) {
+    st_stream(out_col + pos, CI(key));
+    st_stream(out_val + pos, v);
+  } else {
+    dev_fail(st, SP_ERR_INTERNAL, -26);
+  }
+}
+
+// Sort job of a row the warp path did not sort (k kept entries at output offset o).
+__device__ __forceinline__ void x_queue(long long o, long long k, int key_bits, FinalEntry* fin, unsigned* fin_n,
+                                        long long fin_cap, HugeEntry* huge, unsigned* huge_n, long long huge_cap,
+                                        DevStatus* st) {
+  if (k <= 1) return;
+  if (k <= SS_RUN_MAX) {
+    const unsigned q = atomicAdd(fin_n, 1u);
+    if (q < fin_cap) fin[q] = FinalEntry{o, k, BUF_OUT, 0};
+    else dev_fail(st, SP_ERR_INTERNAL, -27);
+  } else {
+    const unsigned q = atomicAdd(huge_n, 1u);
+    if (q < huge_cap) huge[q] = HugeEntry{o, k, 0u, key_bits, BUF_OUT, 0};
+    else dev_fail(st, SP_ERR_INTERNAL, -28);
+  }
+}
+
+// kSorted: the relabelling keeps the source order (ascending J), so slots are ranks and
+// no row is queued.
+template <class CI, class VT, class Rel, bool kSorted>
+__global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, const VT* __restrict__ val, Rel rel,
+                                                long long nI, const long long* __restrict__ rs0,
+                                                const long long* __restrict__ rsn, const long long* __restrict__ vp,
+                                                CI* __restrict__ out_col, VT* __restrict__ out_val, FinalEntry* fin,
+                                                unsigned* fin_n, long long fin_cap, HugeEntry* huge, unsigned* huge_n,
+                                                long long huge_cap, int key_bits, DevStatus* st) {
+  constexpr int R = XF_ROWS, NWB = XB / 32, KW = XFAST + 4;
+  __shared__ __align__(16) uint32_t s_key[NWB][KW];  // a row's kept keys (+ padding for 4-wide loads)
+  __shared__ VT s_val[NWB][XFAST];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t* wk = s_key[wid];
+  VT* wv = s_val[wid];
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i0 = w0 * 32; i0 < nI; i0 += nw * 32) {
+    const long long i = i0 + lane;
+    long long s = 0, L = 0, o = 0, oe = 0;
+    if (i < nI) {
+      s = rs0[i];
+      L = rsn[i];
+      o = vp[i];
+      oe = vp[i + 1];
+    }
+    if (!kSorted && L > XFAST) x_queue(o, oe - o, key_bits, fin, fin_n, fin_cap, huge, huge_n, huge_cap, st);
+    const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
+    for (int g = 0; g < nr; g += R) {
+      long long ss[R];
+      int LL[R];
+      CI c0[R], c1[R];
+      VT v0[R], v1[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
+        const long long l = __shfl_sync(kFull, L, (g + u) & 31);
+        LL[u] = (g + u < nr && l <= XFAST) ? int(l) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        c0[u] = lane < LL[u] ? ld_stream(col + ss[u] + lane) : CI(0);
+        c1[u] = lane + 32 < LL[u] ? ld_stream(col + ss[u] + 32 + lane) : CI(0);
+      }
+      // values of dropped entries are loaded too: they share sectors with kept ones
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        if (lane < LL[u]) v0[u] = ld_stream(val + ss[u] + lane);
+        if (lane + 32 < LL[u]) v1[u] = ld_stream(val + ss[u] + 32 + lane);
+      }
+      uint32_t k0[R], k1[R];
+      bool p0[R], p1[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        p0[u] = lane < LL[u] && rel.map((long long)c0[u], k0[u]);
+        p1[u] = lane + 32 < LL[u] && rel.map((long long)c1[u], k1[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        if (LL[u] == 0) continue;  // warp-uniform: empty, long or beyond the block
+        const long long ou = __shfl_sync(kFull, o, (g + u) & 31);
+        const long long eu = __shfl_sync(kFull, oe, (g + u) & 31);
+        const unsigned b0 = __ballot_sync(kFull, p0[u]), b1 = __ballot_sync(kFull, p1[u]);
+        const int n0 = __popc(b0), nk = n0 + __popc(b1);
+        if (nk != eu - ou) {  // the count disagrees with the fill (a library bug)
+          if (lane == 0) dev_fail(st, SP_ERR_INTERNAL, -29);
+          continue;
+        }
+        if (kSorted) {
+          if (p0[u]) x_put(out_col, out_val, ou + __popc(b0 & lt), eu, k0[u], v0[u], st);
+          if (p1[u]) x_put(out_col, out_val, ou + n0 + __popc(b1 & lt), eu, k1[u], v1[u], st);
+          continue;
+        }
+        // compact the kept entries into the warp's buffer, then rank each among the row
+        if (p0[u]) {
+          wk[__popc(b0 & lt)] = k0[u];
+          wv[__popc(b0 & lt)] = v0[u];
+        }
+        if (p1[u]) {
+          wk[n0 + __popc(b1 & lt)] = k1[u];
+          wv[n0 + __popc(b1 & lt)] = v1[u];
+        }
+        if (lane < 4) wk[nk + lane] = kDropped;  // padding: never below a key
+        __syncwarp();
+        const uint4* w4 = reinterpret_cast<const uint4*>(wk);
+        const int nq = (nk + 3) >> 2;
+        const uint32_t a = lane < nk ? wk[lane] : kDropped;
+        int ra = 0;
+        if (nk <= 32) {
+          for (int q = 0; q < nq; ++q) {
+            const uint4 x = w4[q];
+            ra += int(x.x < a) + int(x.y < a) + int(x.z < a) + int(x.w < a);
+          }
+          VT va;
+          if (lane < nk) va = wv[lane];
+          __syncwarp();
+          if (lane < nk) x_put(out_col, out_val, ou + ra, eu, a, va, st);
+        } else {
+          const uint32_t b = lane + 32 < nk ? wk[lane + 32] : kDropped;
+          int rb = 0;
+          for (int q = 0; q < nq; ++q) {
+            const uint4 x = w4[q];
+            ra += int(x.x < a) + int(x.y < a) + int(x.z < a) + int(x.w < a);
+            rb += int(x.x < b) + int(x.y < b) + int(x.z < b) + int(x.w < b);
+          }
+          const VT va = wv[lane];
+          VT vb;
+          if (lane + 32 < nk) vb = wv[lane + 32];
+          __syncwarp();
+          x_put(out_col, out_val, ou + ra, eu, a, va, st);
+          if (lane + 32 < nk) x_put(out_col, out_val, ou + rb, eu, b, vb, st);
+        }
+      }
+    }
+    // rows of XFAST < L <= SRC_LONG source entries: kept entries in source order (ballot
+    // slots); their sort was queued above
+    unsigned mid = __ballot_sync(kFull, L > XFAST && L <= SRC_LONG);
+    while (mid) {
+      const int k = __ffs(mid) - 1;
+      mid &= mid - 1;
+      const long long sk = __shfl_sync(kFull, s, k), Lk = __shfl_sync(kFull, L, k);
+      long long ok = __shfl_sync(kFull, o, k);
+      const long long ek = __shfl_sync(kFull, oe, k);
+      for (long long e0 = 0; e0 < Lk; e0 += 32 * LOAD_U) {
+        CI cc[LOAD_U];
+        VT vv[LOAD_U];
+        uint32_t kk[LOAD_U];
+        bool pp[LOAD_U];
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const long long e = e0 + v * 32 + lane;
+          cc[v] = e < Lk ? ld_stream(col + sk + e) : CI(0);
+          if (e < Lk) vv[v] = ld_stream(val + sk + e);
+        }
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const long long e = e0 + v * 32 + lane;
+          pp[v] = e < Lk && rel.map((long long)cc[v], kk[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < LOAD_U; ++v) {
+          const unsigned b = __ballot_sync(kFull, pp[v]);
+          if (pp[v]) x_put(out_col, out_val, ok + __popc(b & lt), ek, kk[v], vv[v], st);
+          ok += __popc(b);
+        }
+      }
+    }
+  }
+}
+
+// Loader view (loaders.cuh) of the recorded rows for the CTA-per-row count and fill of
+// rows longer than SRC_LONG.
+template <class CIt, class VTt, class Rel>
+struct XLongRows {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr bool kAllKept = false;
+  static constexpr bool kLoadVals = true;
+  static constexpr bool kEagerVals = true;
+  static constexpr bool kRowCtx = false;
+  const CI* col;
+  const VT* val;
+  Rel rel;
+  const long long* rs0;
+  const long long* rsn;
+  __device__ RowSrc row(long long i) const { return RowSrc{rs0[i], 0, rsn[i], 0}; }
+  __device__ const CI* cols(int) const { return col; }
+  __device__ const VT* vals(int) const { return val; }
+  __device__ bool test(int, long long c) const { return rel.test(c); }
+  // instantiated only by the fill (the count calls test alone)
+  __device__ bool map(int, long long c, uint32_t& key) const { return rel.map(c, key); }
+};
+
+}  // namespace sp

@@ -40,7 +40,7 @@ struct sp_ctx {
   // kernel shapes: the context's options, the tuning table, and the values in force for
   // the call being issued (options overridden by the table entry that covers the call)
   struct Shapes {
-    int tile_shape = 0, heavy = 128, count_rows = 4, fill_rows = 2, batch_rows = 1;
+    int tile_shape = 0, heavy = 128, count_rows = 4, fill_rows = 2, batch_rows = 1, identify = 0;
   };
   Shapes opt, cur;
   std::vector<sp_tune_entry> tuning;
@@ -146,6 +146,7 @@ inline void ctx_begin_call(sp_ctx* ctx, int op, long long size) {
   if (e.count_rows >= 0) ctx->cur.count_rows = e.count_rows;
   if (e.fill_rows >= 0) ctx->cur.fill_rows = e.fill_rows;
   if (e.batch_rows >= 0) ctx->cur.batch_rows = e.batch_rows;
+  if (e.identify >= 0) ctx->cur.identify = e.identify;
 }
 
 }  // namespace sp

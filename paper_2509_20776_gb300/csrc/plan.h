@@ -38,8 +38,16 @@ struct sp_plan {
   uint32_t* jcnt = nullptr;
   long long* jptr = nullptr;
   void* jpos = nullptr;
+  // extraction, general / ascending J: identify tables (rank map words + member
+  // positions, or J sorted with its positions), and the rows the fill queues for sorting
+  int identify = 0;
+  unsigned long long* jmeta = nullptr;
+  void* jrpos = nullptr;
+  uint32_t* jsk = nullptr;
+  uint32_t* jsp = nullptr;
+  long long n_slow = 0;
   long long list_cap = 0;
-  unsigned* counters = nullptr;  // [0] n_cl [3] count ticket
+  unsigned* counters = nullptr;  // [0] n_cl [3] count ticket [4] rows of more than XFAST entries
   long long* h_tail = nullptr;   // pinned host: totals read back by the count call
 };
 

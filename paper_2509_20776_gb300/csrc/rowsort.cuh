@@ -990,10 +990,11 @@ struct RowsWs {
 
 constexpr int kRowsSlots = 12;
 
-inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
+// extra_fin: runs a caller queues itself (beyond the partition's and the split's)
+inline void rows_caps(long long nrows, long long nnz, RowsWs* w, long long extra_fin = 0) {
   w->ntiles_cap = (nnz + SS_ROW_W * nrows) / SS_TILE_MAX + 1;
   w->nchunks = (nnz + GC_CH - 1) / GC_CH;
-  w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / SS_RUN_MAX + 16) + nnz / SS_TILE_MAX + 1;
+  w->fin_cap = 2 * (3 * (nnz / GROUP_CAP) + nnz / SS_RUN_MAX + 16) + nnz / SS_TILE_MAX + 1 + extra_fin;
   w->huge_cap = nnz / SS_RUN_MAX + 1;
   w->nxt_cap = nnz / SS_RUN_MAX + 1;
   w->hv_cap = nnz / (SS_HEAVY + 1) + 1;  // heavy buckets are disjoint runs of > SS_HEAVY
@@ -1001,9 +1002,9 @@ inline void rows_caps(long long nrows, long long nnz, RowsWs* w) {
 
 // Workspace of run_rows; `sort` = false reserves only what the gather needs.
 inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbytes, size_t* off,
-                         bool sort = true) {
+                         bool sort = true, long long extra_fin = 0) {
   RowsWs w;
-  rows_caps(nrows, nnz, &w);
+  rows_caps(nrows, nnz, &w, extra_fin);
   if (!sort) w.fin_cap = w.huge_cap = w.nxt_cap = w.hv_cap = 0;
   const bool need_temp = sort && nnz > SS_RUN_MAX;
   off[0] = cv.reserve(size_t(w.ntiles_cap + 1) * 8);
@@ -1021,9 +1022,9 @@ inline void rows_reserve(Carver& cv, long long nrows, long long nnz, size_t vbyt
 }
 
 inline RowsWs rows_bind(const Carver& cv, long long nrows, long long nnz, const size_t* off,
-                        bool sort = true) {
+                        bool sort = true, long long extra_fin = 0) {
   RowsWs w;
-  rows_caps(nrows, nnz, &w);
+  rows_caps(nrows, nnz, &w, extra_fin);
   if (!sort) w.fin_cap = w.huge_cap = w.nxt_cap = w.hv_cap = 0;
   w.tile_first = cv.at<long long>(off[0]);
   w.chunk_first = cv.at<long long>(off[1]);
@@ -1051,6 +1052,76 @@ struct NoGather {
   __device__ VT val(long long) const { return VT(0); }
 };
 
+// Key-range split of the rows queued in w.huge (counter 1) into runs queued in w.fin.
+template <class CI, class VT>
+sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col, VT* out_val) {
+  const int nsm = ctx->num_sms;
+  VT* tval = static_cast<VT*>(w.tval);
+  constexpr size_t csm = split_smem_bytes<SplitCoarse, VT>(), fsm = split_smem_bytes<SplitFine, VT>();
+  static bool once_h = (set_smem(k_split<SplitCoarse, CI, VT>, csm), set_smem(k_split<SplitFine, CI, VT>, fsm), true);
+  (void)once_h;
+  {
+    SP_PHASE(SP_PHASE_HUGE);
+    k_split<SplitCoarse, CI, VT><<<SplitCoarse::MINB * nsm, SplitCoarse::B, csm, s>>>(
+        w.huge, w.counters + 1, w.huge_cap, w.counters + 3, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
+        w.fin_cap, w.nxt, w.counters + 2, w.nxt_cap, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  // the fine split: the coarse buckets that hold more than SS_RUN_MAX entries (skewed keys
+  // or very long rows); an empty list costs one short launch
+  {
+    SP_PHASE(SP_PHASE_HUGE);
+    k_split<SplitFine, CI, VT><<<SplitFine::MINB * nsm, SplitFine::B, fsm, s>>>(
+        w.nxt, w.counters + 2, w.nxt_cap, w.counters + 4, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
+        w.fin_cap, w.nxt, w.counters + 5, 0, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  return SP_OK;
+}
+
+// Sorts the runs queued in w.fin (counter 0), then the heavy buckets queued by any sort
+// pass (counters 6, 7), in place.
+template <class CI, class VT>
+sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, CI* out_col, VT* out_val) {
+  const int nsm = ctx->num_sms;
+  const int heavy = ctx->cur.heavy;
+  VT* tval = static_cast<VT*>(w.tval);
+  const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
+  using SsRun = SsRunT<VT>;
+  constexpr size_t rsm = ss_smem_bytes<SsRun, VT>();
+  static bool once_r = (set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
+  (void)once_r;
+  {
+    SP_PHASE(SP_PHASE_LONG);
+    k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
+        nullptr, nullptr, no_tiles, w.fin, w.counters + 0, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
+        w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  // heavy buckets: runs over their own key range; the last pass ranks every bucket
+  for (int pass = 0; pass < SS_PASSES; ++pass) {
+    const int a = pass & 1, b = a ^ 1;
+    const bool last = pass == SS_PASSES - 1;
+    SP_CUDA(cudaMemsetAsync(w.counters + 6 + b, 0, 4, s));
+    {
+      SP_PHASE(SP_PHASE_LONG);
+      k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
+          nullptr, nullptr, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
+          last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, heavy, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  return SP_OK;
+}
+
+// Sorts in place the rows a caller queued itself in w.fin / w.huge (counters 0 and 1,
+// zeroed with the rest of w.counters before the caller queued them).
+template <class CI, class VT>
+sp_status sort_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, CI* out_col, VT* out_val) {
+  SP_TRY((split_queued<CI, VT>(ctx, s, w, out_col, out_val)));
+  return sort_runs<CI, VT>(ctx, s, w, key_bits, out_col, out_val);
+}
+
 // Partition the output rows (row pointer vp, nnz entries), gather them with `gs`
 // (when given) and sort every row in place (when `sort`).
 template <class CI, class VT, class Gs>
@@ -1061,7 +1132,6 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   const int nsm = ctx->num_sms;
   unsigned* fin_n = w.counters + 0;
   unsigned* huge_n = w.counters + 1;
-  unsigned* nxt_n = w.counters + 2;
   // kernel shapes of this call (context options or the tuning table)
   const bool large_tiles = ctx->cur.tile_shape == 1;
   const long long tmax = large_tiles ? SsTileL::CP : SsTile::CP;
@@ -1082,37 +1152,13 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     SP_CUDA(cudaGetLastError());
   }
   if (!sort) return SP_OK;
-  VT* tval = static_cast<VT*>(w.tval);
-  if (nnz > SS_RUN_MAX) {
-    constexpr size_t csm = split_smem_bytes<SplitCoarse, VT>(), fsm = split_smem_bytes<SplitFine, VT>();
-    static bool once_h = (set_smem(k_split<SplitCoarse, CI, VT>, csm), set_smem(k_split<SplitFine, CI, VT>, fsm), true);
-    (void)once_h;
-    {
-      SP_PHASE(SP_PHASE_HUGE);
-      k_split<SplitCoarse, CI, VT><<<SplitCoarse::MINB * nsm, SplitCoarse::B, csm, s>>>(
-          w.huge, huge_n, w.huge_cap, w.counters + 3, w.tkey, tval, out_col, out_val, w.fin, fin_n, w.fin_cap,
-          w.nxt, nxt_n, w.nxt_cap, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-    // the fine split: the coarse buckets that hold more than SS_RUN_MAX entries (skewed keys
-    // or very long rows); an empty list costs one short launch
-    {
-      SP_PHASE(SP_PHASE_HUGE);
-      k_split<SplitFine, CI, VT><<<SplitFine::MINB * nsm, SplitFine::B, fsm, s>>>(
-          w.nxt, nxt_n, w.nxt_cap, w.counters + 4, w.tkey, tval, out_col, out_val, w.fin, fin_n, w.fin_cap,
-          w.nxt, w.counters + 5, 0, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-  }
+  if (nnz > SS_RUN_MAX) SP_TRY((split_queued<CI, VT>(ctx, s, w, out_col, out_val)));
   // tiles, then the runs, then the heavy buckets queued by either
-  const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   const unsigned* no_runs = w.counters + 8;
-  using SsRun = SsRunT<VT>;
-  constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), lsm = ss_smem_bytes<SsTileL, VT>(),
-                   rsm = ss_smem_bytes<SsRun, VT>();
-  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsTileL, CI, VT>, lsm),
-                        set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
+  constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), lsm = ss_smem_bytes<SsTileL, VT>();
+  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsTileL, CI, VT>, lsm), true);
   (void)once_s;
+  VT* tval = static_cast<VT*>(w.tval);
   {
     SP_PHASE(SP_PHASE_TILE);
     if (large_tiles)
@@ -1125,27 +1171,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
           w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
-  {
-    SP_PHASE(SP_PHASE_LONG);
-    k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
-        vp, w.tile_first, no_tiles, w.fin, fin_n, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
-        w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
-  // heavy buckets: runs over their own key range; the last pass ranks every bucket
-  for (int pass = 0; pass < SS_PASSES; ++pass) {
-    const int a = pass & 1, b = a ^ 1;
-    const bool last = pass == SS_PASSES - 1;
-    SP_CUDA(cudaMemsetAsync(w.counters + 6 + b, 0, 4, s));
-    {
-      SP_PHASE(SP_PHASE_LONG);
-      k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
-          vp, w.tile_first, no_tiles, w.hv[a], w.counters + 6 + a, w.hv_cap, w.tkey, tval, out_col, out_val,
-          last ? nullptr : w.hv[b], w.counters + 6 + b, w.hv_cap, key_bits, heavy, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-  }
-  return SP_OK;
+  return sort_runs<CI, VT>(ctx, s, w, key_bits, out_col, out_val);
 }
 
 }  // namespace sp

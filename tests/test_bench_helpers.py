@@ -23,22 +23,31 @@ def test_roofline_of_dominant_phase():
     classes = {"tile": (400, 10), "long": (300, 2), "huge": (300, 1)}
     m, n = 100, 100
     stats = {"gather": (6.0, 6), "tile": (3.0, 6), "long": (5.0, 24), "scan": (0.5, 12), "other": (9.0, 3)}
-    r = bench.roofline_permute(stats, classes, m, n, ops_per_step=3, steps=2, peak_gbs=1000.0, scale=7)
+    lk = {"g_per_s": 100.0, "table_bytes": 400, "probe": "x"}
+    r = bench.roofline_permute(stats, classes, m, n, ops_per_step=3, steps=2, peak_gbs=1000.0, lookup_peak=lk)
     assert r["phase"] == "gather" and r["kernel"] == "k_gather_chunks"  # "other" has no byte model
-    alg = 20 * 1000 + 16 * m
+    alg = 16 * 1000 + 16 * m  # the scope's 16 B per entry, plus the per-row pointers
     assert r["alg_bytes_per_launch"] == alg
     assert abs(r["achieved"] - alg * 6 / 6e-3 / 1e9) < 0.1
     assert r["frac"] == round(r["achieved"] / 1000.0, 4)
-    assert r["traffic"] is None  # no capture at this scale
+    # the relabel lookup (4 B per entry) only in the separately named fraction
+    assert abs(r["frac_incl_lookup"] - (alg + 4 * 1000) * 6 / 6e-3 / 1e9 / 1000.0) < 1e-3
     assert r["avg_launch_ms"] == 1.0
+    # lookups: one per entry of each of the 6 launches in 6 ms
+    assert r["lookup_roofline"]["achieved"] == round(1000 * 6 / 6e-3 / 1e9, 2)
+    assert abs(r["lookup_roofline"]["frac"] - 1000 * 6 / 6e-3 / 1e9 / 100.0) < 1e-4
 
 
 def test_traffic_only_from_captures():
-    for (scale, phase), v in bench.NCU_TRAFFIC.items():
-        assert scale == 25 and phase in ("gather", "tile", "huge", "long") and v > 0
     classes = {"tile": (10, 5), "long": (0, 0), "huge": (0, 0)}
-    r = bench.roofline_permute({"gather": (1.0, 3)}, classes, 5, 5, 3, 1, 100.0, 25)
-    assert r["traffic"] == bench.NCU_TRAFFIC[(25, "gather")]
+    r = bench.roofline_permute({"gather": (1.0, 3)}, classes, 5, 5, 3, 1, 100.0, None)
+    if bench.GATHER_DRAM_BYTES_PER_ENTRY is None:
+        assert r["traffic"] is None
+    else:  # a per-entry figure from a capture, scaled by the entries one launch moves
+        assert r["traffic"] == int(bench.GATHER_DRAM_BYTES_PER_ENTRY * 10)
+    assert "lookup_roofline" not in r
+    r = bench.roofline_permute({"tile": (1.0, 3)}, classes, 5, 5, 3, 1, 100.0, None)
+    assert r["traffic"] is None and "frac_incl_lookup" not in r
 
 
 def test_workload_name_follows_scale():

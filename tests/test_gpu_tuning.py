@@ -24,7 +24,7 @@ def ctx():
     c = Context(0)
     yield c
     c.set_tuning(None)
-    c.set_shapes(tile_shape=-1, heavy=-1, count_rows=-1, fill_rows=-1, batch_rows=-1)
+    c.set_shapes(tile_shape=-1, heavy=-1, count_rows=-1, fill_rows=-1, batch_rows=-1, identify=-1)
     c.close()
 
 
@@ -54,18 +54,41 @@ def test_permute_every_shape(ctx, rmat, tile_shape, heavy, order):
     assert_same(B, _want[order], f"shape {tile_shape}/{heavy} {order}")
 
 
-@pytest.mark.parametrize("count_rows,fill_rows", [(1, 1), (2, 2), (3, 1), (4, 2)])
-def test_extract_every_rows_per_warp(ctx, rmat, count_rows, fill_rows):
+@pytest.mark.parametrize("identify", [0, 1])
+@pytest.mark.parametrize("jorder", ["random", "ascending"])
+def test_extract_every_identify(ctx, rmat, identify, jorder):
+    """Both identifies (rank map, sorted-J binary search), with general and ascending J
+    (the fill that needs no sort), on a matrix with hub rows (the queued row sorts and
+    the CTA-per-row count / fill)."""
     n = rmat.nrows
     g = torch.Generator().manual_seed(11)
     I = torch.randint(0, n, (n // 3,), generator=g).to(torch.int32)  # repeats allowed
     J = torch.randperm(n, generator=g)[: n // 2].to(torch.int32)
-    ctx.set_shapes(count_rows=count_rows, fill_rows=fill_rows, tile_shape=count_rows % 2)
+    if jorder == "ascending":
+        J = torch.sort(J).values
+    ctx.set_shapes(identify=identify, tile_shape=identify)
     try:
         B = ctx.sp_extract(to_dev(rmat), I.cuda(), J.cuda())
     finally:
+        ctx.set_shapes(identify=-1, tile_shape=-1)
+    assert_same(B, oracle.extract(to_oracle(rmat), I.numpy(), J.numpy()), f"identify {identify} {jorder}")
+
+
+@pytest.mark.parametrize("count_rows,fill_rows", [(1, 1), (2, 2), (3, 1), (4, 2)])
+def test_assign_every_rows_per_warp(ctx, rmat, count_rows, fill_rows):
+    n = rmat.nrows
+    g = torch.Generator().manual_seed(12)
+    I = torch.randperm(n, generator=g)[: n // 4].to(torch.int32)
+    J = torch.randperm(n, generator=g)[: n // 4].to(torch.int32)
+    Bm = synth.er_csr(n // 4, n // 4, 6, seed=13, value_kind="f32u01", rowptr_dtype=torch.int64,
+                      colidx_dtype=torch.int32)
+    ctx.set_shapes(count_rows=count_rows, fill_rows=fill_rows, tile_shape=count_rows % 2)
+    try:
+        Ap = ctx.sp_assign(to_dev(rmat), I.cuda(), J.cuda(), to_dev(Bm))
+    finally:
         ctx.set_shapes(count_rows=-1, fill_rows=-1, tile_shape=-1)
-    assert_same(B, oracle.extract(to_oracle(rmat), I.numpy(), J.numpy()), f"rows {count_rows}/{fill_rows}")
+    want = oracle.assign(to_oracle(rmat), I.numpy(), J.numpy(), to_oracle(Bm))
+    assert_same(Ap, want, f"rows {count_rows}/{fill_rows}")
 
 
 def _batch(n_req, seed):
@@ -112,7 +135,8 @@ def test_tuning_table_per_call(ctx, rmat):
     table = {"format": "sp-tuning-1", "entries": [
         {"op": "permute", "size_max": 10_000, "tile_shape": 1, "heavy": 256},
         {"op": "permute", "size_max": 1 << 62, "tile_shape": 0, "heavy": 512},
-        {"op": "extract", "size_max": 1 << 62, "count_rows": 2, "fill_rows": 1},
+        {"op": "extract", "size_max": 10_000, "identify": 1},
+        {"op": "extract", "size_max": 1 << 62, "identify": 0, "tile_shape": 1},
         {"op": "batch", "size_max": 1 << 62, "batch_rows": 4}]}
     ctx.set_tuning(table)
     try:
@@ -124,6 +148,9 @@ def test_tuning_table_per_call(ctx, rmat):
         I = torch.arange(0, rmat.nrows, 3, dtype=torch.int32)
         B = ctx.sp_extract(to_dev(rmat), I.cuda(), I.cuda())
         assert_same(B, oracle.extract(to_oracle(rmat), I.numpy(), I.numpy()), "tuned extract")
+        Is = torch.randperm(300, generator=torch.Generator().manual_seed(4))[:100].to(torch.int32)
+        B = ctx.sp_extract(to_dev(small), Is.cuda(), Is.flip(0).contiguous().cuda())
+        assert_same(B, oracle.extract(to_oracle(small), Is.numpy(), Is.flip(0).numpy()), "tuned small extract")
     finally:
         ctx.set_tuning(None)
     with pytest.raises(ValueError):

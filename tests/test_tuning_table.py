@@ -19,7 +19,8 @@ def test_entries_validated_and_ordered():
     assert rows[0]["heavy"] == 256 and rows[0]["tile_shape"] == -1
     assert rows[2]["batch_rows"] == 8 and rows[2]["count_rows"] == -1
     for bad in ({"op": "sort", "size_max": 1}, {"op": "permute", "size_max": 1, "heavy": 100},
-                {"op": "extract", "size_max": 1, "fill_rows": 3}, {"op": "batch", "size_max": 1, "batch_rows": 16}):
+                {"op": "extract", "size_max": 1, "fill_rows": 3}, {"op": "batch", "size_max": 1, "batch_rows": 16},
+                {"op": "extract", "size_max": 1, "identify": 2}):
         with pytest.raises(ValueError):
             b.tune_entries([bad])
 
@@ -33,8 +34,8 @@ def test_numbers_match_header():
     assert {k.lower(): v for k, v in ops.items()} == b.OPS
     # the ctypes entry mirrors the C struct's field order and widths
     assert [f for f, _ in b.sp_tune_entry._fields_] == ["op", "tile_shape", "heavy", "count_rows", "fill_rows",
-                                                        "batch_rows", "size_max"]
-    assert b.sp_tune_entry.size_max.offset == 24
+                                                        "batch_rows", "identify", "size_max"]
+    assert b.sp_tune_entry.size_max.offset == 32
 
 
 def test_autotune_compare_and_files(tmp_path):
