@@ -64,6 +64,8 @@ def parse():
                     help="comma list of the extra sections to run (extract, assign, batch, serve)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--lookup-sweep", action="store_true",
+                    help="print the measured rate of uniform random 4-byte lookups per table size and exit")
     ap.add_argument("--rows-limit", type=int, default=0,
                     help="profiling case: the headline matrix's first R rows (all columns), one "
                          "permutation with independent random p, q; prints its line and exits")
@@ -246,31 +248,30 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup
     return out
 
 
-def lookup_probe(table_elems, device, n_lookups=1 << 28):
-    """Measured rate of random 4-byte lookups into an int32 table of `table_elems` entries
-    (PyTorch's gather of uniformly random indices, best of 3 after a warm-up; each lookup
-    also streams its 4-byte index in and its result out): the ceiling of a relabel step
-    whose map has that size."""
+def lookup_probe(table_elems, cols, device):
+    """Measured rate of the relabel lookups alone: PyTorch's gather of an int32 map of
+    `table_elems` entries at the workload's own column indices `cols` (the same lookups,
+    in the same order, that the gather makes; the index stream is read and the result
+    written as well), best of 3 after a warm-up.  The gather cannot relabel faster than
+    this, so its lookup rate over this one is its fraction of the lookup ceiling."""
     import torch
     t = torch.arange(table_elems, dtype=torch.int32, device=device)
-    g = torch.Generator(device=device).manual_seed(7)
-    idx = torch.randint(0, table_elems, (n_lookups,), generator=g, device=device, dtype=torch.int64).to(torch.int32)
-    out = torch.empty(n_lookups, dtype=torch.int32, device=device)
-    torch.index_select(t, 0, idx, out=out)
+    out = torch.empty(cols.numel(), dtype=torch.int32, device=device)
+    torch.index_select(t, 0, cols, out=out)
     torch.cuda.synchronize()
     best = 1e9
     for _ in range(3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        torch.index_select(t, 0, idx, out=out)
+        torch.index_select(t, 0, cols, out=out)
         b.record()
         torch.cuda.synchronize()
         best = min(best, a.elapsed_time(b))
-    del t, idx, out
+    del t, out
     torch.cuda.empty_cache()
-    return {"g_per_s": round(n_lookups / (best * 1e-3) / 1e9, 2), "table_bytes": table_elems * 4,
-            "probe": f"torch.index_select of {n_lookups} uniform random int32 indices (index read and "
-                     "result write included), best of 3"}
+    return {"g_per_s": round(cols.numel() / (best * 1e-3) / 1e9, 2), "table_bytes": table_elems * 4,
+            "probe": f"torch.index_select of an int32 map of {table_elems} entries at the workload's "
+                     f"{cols.numel()} column indices (index read and result write included), best of 3"}
 
 
 def time_steps(fn, steps, warmup, ws):
@@ -390,7 +391,7 @@ def run_ours(args, ws, rank, local):
     ms = max_over_ranks(ms, ws)
     out_per_step = nnz * len(ops)
     value = out_per_step * args.steps * ws / (ms * 1e-3)
-    lk = lookup_probe(A.ncols, dev)
+    lk = lookup_probe(A.ncols, A.colidx, dev)
     roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, lk)
     # whole op: read and write col + val per entry, p and rowptr pair per row, q and qinv
     alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols
@@ -439,6 +440,8 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
         log("cpu baseline done")
+        result["cpu_baseline_mt"] = cpu_baseline_mt(A, ops[0][1])
+        log("multithreaded cpu baseline done")
     ctx.close()
     if rank == 0:
         log_summary(result)
@@ -809,10 +812,11 @@ def bench_batch_tuned(ctx, dms, reqs, nnz, steps, ws):
             "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1)}
 
 
-def bench_serve(ctx, args, dev, nreq=10000):
+def bench_serve(ctx, args, dev, nreq=100000, nreq_overload=10000):
     """Poisson stream of mixed requests (60 % P A P^T, 30 % extraction, 10 % assignment)
-    over the batching workload's 64 matrices, at 0.8 x the plain path's measured capacity;
-    continuous batching against one synchronous call per request."""
+    over the batching workload's 64 matrices: `nreq` requests at 0.8 x the plain path's
+    measured capacity and the first `nreq_overload` at 2 x; continuous batching against
+    one synchronous call per request."""
     import torch
     import synth
     from paper_2509_20776_gb300 import CSR
@@ -847,20 +851,20 @@ def bench_serve(ctx, args, dev, nreq=10000):
     sample = make([0.0] * nreq)[:ns]
     run_plain(ctx, dms, sample)
     cap = ns / max(max(r.done for r in sample), 1e-9)
-    res = {"workload": f"{nreq} requests (60/30/10 % permute/extract/assign) on the batching "
-                       f"workload's {len(mats)} matrices, Poisson arrivals",
+    res = {"workload": f"{nreq} requests at 0.8x, {nreq_overload} at 2x (60/30/10 % permute/extract/assign) "
+                       f"on the batching workload's {len(mats)} matrices, Poisson arrivals",
            "plain_capacity_per_s": round(cap, 1), "unit": UNIT}
     srv = Server(dms, slots=4)
-    for load in (0.8, 2.0):  # below and above the plain path's capacity
+    for load, nr in ((0.8, nreq), (2.0, nreq_overload)):  # below and above the plain path's capacity
         rate = load * cap
         gaps = torch.empty(nreq, dtype=torch.float64).exponential_(rate, generator=g)
         arrivals = torch.cumsum(gaps, 0).tolist()
-        plain = run_plain(ctx, dms, make(arrivals))
-        served = srv.run(make(arrivals))
+        plain = run_plain(ctx, dms, make(arrivals)[:nr])
+        served = srv.run(make(arrivals)[:nr])
         nnz_p = sum(r.nnz_out for r in plain)
         nnz_s = sum(r.nnz_out for r in served)
         sp, ss = latency_stats(plain), latency_stats(served)
-        res[f"load_{load}x"] = {"rate_per_s": round(rate, 1),
+        res[f"load_{load}x"] = {"rate_per_s": round(rate, 1), "requests": nr,
                                 "plain": {**sp, "value": round(nnz_p / sp["span_s"], 1)},
                                 "served": {**ss, "value": round(nnz_s / ss["span_s"], 1)},
                                 "same_nnz": nnz_p == nnz_s}
@@ -904,6 +908,48 @@ def cpu_baseline(args):
                       f"{O.nnz} nnz), one P A P^T with a random p, {dt:.1f} s"}
 
 
+def _mem_available() -> int:
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_mt(A, p):
+    """The multithreaded CPU restatement of Algorithm 2 (oracle/cpu_mt.cpp: count, scan,
+    fill, per-row sort; OpenMP on every host thread) on the headline matrix itself, one
+    P A P^T with the workload's random p.  Skipped when the host lacks the memory."""
+    import numpy as np
+    from oracle import cpu_mt
+    need = A.nnz * 8 * 2 + A.nrows * 8 * 3 + A.ncols * 4
+    avail = _mem_available()
+    if avail < 1.5 * need:
+        return {"skipped": f"host memory: {avail >> 30} GiB available, {int(1.5 * need) >> 30} GiB wanted"}
+    rp, ci, vv = A.rowptr.cpu().numpy(), A.colidx.cpu().numpy(), A.values.cpu().numpy()
+    pn = p.cpu().numpy().astype(np.int64)
+    t = time.perf_counter()
+    cpu_mt.permute(A.nrows, A.ncols, rp, ci, vv, pn)
+    dt = time.perf_counter() - t
+    return {"value": round(A.nnz / dt, 1), "unit": UNIT, "cores": cpu_mt.threads(), "nproc": os.cpu_count(),
+            "cpu_model": _cpu_model(), "kind": "openmp restatement of Algorithm 2 (count, scan, fill, per-row sort)",
+            "sample": f"the headline matrix ({A.nnz} entries), one P A P^T with the random p, {dt:.2f} s"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on a bounded sample per step (scale-18 R-MAT)."""
     import oracle
@@ -937,8 +983,40 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def lookup_sweep():
+    """Rate of uniform random 4-byte lookups (torch.index_select, 2^28 lookups, index read
+    and result write included) into int32 tables of 8 MB to 1 GB: where a relabel map stops
+    being L2-resident."""
+    import torch
+    dev = torch.device("cuda", 0)
+    rows = []
+    for mb in (8, 16, 32, 64, 96, 112, 128, 160, 256, 1024):
+        n = mb * (1 << 20) // 4
+        t = torch.arange(n, dtype=torch.int32, device=dev)
+        g = torch.Generator(device=dev).manual_seed(mb)
+        idx = torch.randint(0, n, (1 << 28,), generator=g, device=dev, dtype=torch.int32)
+        out = torch.empty(1 << 28, dtype=torch.int32, device=dev)
+        torch.index_select(t, 0, idx, out=out)
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            torch.index_select(t, 0, idx, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        rows.append({"table_mb": mb, "ms": round(best, 3), "g_lookups_per_s": round((1 << 28) / best / 1e6, 1)})
+        del t, idx, out
+        torch.cuda.empty_cache()
+    return {"lookup_sweep": rows}
+
+
 def main():
     args = parse()
+    if args.lookup_sweep:
+        print(json.dumps(lookup_sweep()), flush=True)
+        return
     ws, rank, local = dist_init()
     if args.impl == "reference":
         if rank == 0:

@@ -88,6 +88,29 @@ def tune_array(table):
     return arr, len(rows)
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class sp_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """Device memory for a context from PyTorch's caching allocator (the sp_allocator hook
+    of include/sp.h): ``alloc(nbytes, stream)`` returns a device address or 0, ``free(ptr,
+    nbytes, stream)`` returns it.  Subclasses may refuse allocations (failure injection)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+
+    def alloc(self, nbytes: int, stream: int) -> int:
+        return torch.cuda.caching_allocator_alloc(max(1, nbytes), self.device, stream or 0)
+
+    def free(self, ptr: int, nbytes: int, stream: int) -> None:
+        torch.cuda.caching_allocator_delete(ptr)
+
+
 class sp_extract_req(ctypes.Structure):
     _fields_ = [("mat", ctypes.c_int64), ("nI", ctypes.c_int64), ("nJ", ctypes.c_int64),
                 ("I", ctypes.c_void_p), ("J", ctypes.c_void_p)]
@@ -210,13 +233,31 @@ class CSR:
 class Context:
     """Owns an ``sp_ctx`` (workspace, device error record) for one CUDA device."""
 
-    def __init__(self, device: int | None = None):
+    def __init__(self, device: int | None = None, allocator=None):
+        """``allocator``: an object with ``alloc(nbytes, stream) -> int`` and ``free(ptr,
+        nbytes, stream)`` (e.g. ``TorchAllocator``) through which the library takes its
+        workspace, plans and library-allocated outputs; None = stream-ordered cudaMallocAsync."""
         self.lib = load_library()
         if device is None:
             device = torch.cuda.current_device()
         self.device = device
+        self._allocator_c = None
+        if allocator is not None:
+            def _a(user, nbytes, stream):
+                try:
+                    return allocator.alloc(int(nbytes), int(stream or 0)) or None
+                except Exception:  # noqa: BLE001  (a failed allocation is reported as NULL)
+                    return None
+
+            def _f(user, ptr, nbytes, stream):
+                if ptr:
+                    allocator.free(int(ptr), int(nbytes), int(stream or 0))
+
+            self._allocator_c = sp_allocator(_ALLOC_FN(_a), _FREE_FN(_f), None)  # kept alive with the context
         h = ctypes.c_void_p()
-        self._check(self.lib.sp_ctx_create(ctypes.byref(h), device, None), "sp_ctx_create")
+        self._check(self.lib.sp_ctx_create(ctypes.byref(h), device,
+                                           ctypes.byref(self._allocator_c) if self._allocator_c is not None else None),
+                    "sp_ctx_create")
         self.handle = h
 
     def _check(self, code: int, where: str):

@@ -634,9 +634,10 @@ extern "C" sp_status sp_assign_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, sp_str
   Ap->nnz = pl->nnz_out;
   Ap->colidx_type = pl->A.colidx_type;
   Ap->value_type = pl->A.value_type;
+  const bool owned = lib_allocates(Ap);
   SP_TRY(alloc_csr(ctx, Ap, s));
   const sp_csr& A = pl->A;
-  return dispatch_i(A.rowptr_type, [&](auto rp) {
+  const sp_status st_ = dispatch_i(A.rowptr_type, [&](auto rp) {
     using RP = decltype(rp);
     return dispatch_i(A.colidx_type, [&](auto ci) {
       using CI = decltype(ci);
@@ -649,6 +650,7 @@ extern "C" sp_status sp_assign_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, sp_str
       });
     });
   });
+  return release_on_error(ctx, Ap, owned, s, st_);
 }
 
 extern "C" sp_status sp_assign(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,
@@ -678,8 +680,9 @@ extern "C" sp_status sp_assign_permute_fill(sp_ctx* ctx, sp_plan* pl, const void
   out->nnz = pl->nnz_out;
   out->colidx_type = A.colidx_type;
   out->value_type = A.value_type;
+  const bool owned = lib_allocates(out);
   SP_TRY(alloc_csr(ctx, out, s));
-  return dispatch_i(A.rowptr_type, [&](auto rp) {
+  const sp_status st_ = dispatch_i(A.rowptr_type, [&](auto rp) {
     using RP = decltype(rp);
     return dispatch_i(A.colidx_type, [&](auto ci) {
       using CI = decltype(ci);
@@ -693,6 +696,7 @@ extern "C" sp_status sp_assign_permute_fill(sp_ctx* ctx, sp_plan* pl, const void
       });
     });
   });
+  return release_on_error(ctx, out, owned, s, st_);
 }
 
 extern "C" sp_status sp_assign_permute(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,

@@ -539,9 +539,10 @@ extern "C" sp_status sp_extract_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* B, sp_str
   B->nnz = pl->nnz_out;
   B->colidx_type = pl->A.colidx_type;
   B->value_type = pl->A.value_type;
+  const bool owned = lib_allocates(B);
   SP_TRY(alloc_csr(ctx, B, s));
   const sp_csr& A = pl->A;
-  return dispatch_i(A.rowptr_type, [&](auto rp) {
+  const sp_status st_ = dispatch_i(A.rowptr_type, [&](auto rp) {
     using RP = decltype(rp);
     return dispatch_i(A.colidx_type, [&](auto ci) {
       using CI = decltype(ci);
@@ -554,6 +555,7 @@ extern "C" sp_status sp_extract_fill(sp_ctx* ctx, sp_plan* pl, sp_csr* B, sp_str
       });
     });
   });
+  return release_on_error(ctx, B, owned, s, st_);
 }
 
 extern "C" sp_status sp_extract(sp_ctx* ctx, const sp_csr* A, const void* I, int64_t nI,

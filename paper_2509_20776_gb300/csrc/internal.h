@@ -132,6 +132,18 @@ struct PhaseScope {
 // Allocate B's arrays through the context allocator when all three are NULL.
 sp_status alloc_csr(sp_ctx* ctx, sp_csr* B, cudaStream_t s);
 
+// A call that allocated its output (`owned`) and then failed releases it (stream-ordered
+// after the work already queued on s) and zeroes the pointers; returns st.
+inline sp_status release_on_error(sp_ctx* ctx, sp_csr* B, bool owned, cudaStream_t s, sp_status st) {
+  if (st == SP_OK || !owned) return st;
+  ctx_free(ctx, B->rowptr, 0, s);
+  ctx_free(ctx, B->colidx, 0, s);
+  ctx_free(ctx, B->values, 0, s);
+  B->rowptr = B->colidx = B->values = nullptr;
+  return st;
+}
+inline bool lib_allocates(const sp_csr* B) { return !B->rowptr && !B->colidx && !B->values; }
+
 // With SP_OPT_VALIDATE set, check A is canonical (synchronises); else SP_OK.
 sp_status validate_if_asked(sp_ctx* ctx, const sp_csr* A, cudaStream_t s);
 

@@ -161,8 +161,9 @@ extern "C" sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, con
   B->nnz = A->nnz;
   B->colidx_type = A->colidx_type;
   B->value_type = A->value_type;
+  const bool owned = lib_allocates(B);
   SP_TRY(alloc_csr(ctx, B, s));
-  return dispatch_i(A->rowptr_type, [&](auto rp) {
+  const sp_status st_ = dispatch_i(A->rowptr_type, [&](auto rp) {
     using RP = decltype(rp);
     return dispatch_i(A->colidx_type, [&](auto ci) {
       using CI = decltype(ci);
@@ -176,4 +177,5 @@ extern "C" sp_status sp_permute(sp_ctx* ctx, const sp_csr* A, const void* p, con
       });
     });
   });
+  return release_on_error(ctx, B, owned, s, st_);
 }

@@ -5,11 +5,13 @@ time.  Every scheduling round the server
   * retires the requests whose work has finished on the device (latency = completion
     time seen by the host - arrival time);
   * admits the requests that have arrived, in arrival order, while their output bound
-    fits the device-memory budget (permutation: nnz(A); assignment: nnz(A) + nnz(B);
-    extraction: the batch's exact count);
-  * runs all admitted extractions as one batch (``ExtractBatch``: one count, one fill for
-    the whole round) and issues the permutations and assignments round-robin on several
-    stream slots, each with its own library context, so their work overlaps on the GPU.
+    fits the device-memory budget (permutation: nnz(A); assignment: nnz(A) + nnz(B));
+  * counts the round's extractions as one batch (``ExtractBatch``: one count for the
+    whole round) and admits the batch by the exact output bytes that count returns: a
+    batch that does not fit is held, counted but not filled, until retiring work frees
+    enough memory (later extractions wait behind it, in order);
+  * fills admitted batches and issues the permutations and assignments round-robin on
+    several stream slots, each with its own library context, so their work overlaps.
 Requests that arrive while others are on the GPU join the next round: slots and memory
 free up as earlier work retires.  ``run_plain`` serves the same stream one synchronous
 call per request, for comparison.  Every kernel is the library's; this module only
@@ -53,10 +55,12 @@ class Server:
     device: int = 0
     _ctx: list = field(default_factory=list)
     _streams: list = field(default_factory=list)
+    stats: dict = field(default_factory=dict)
 
     def __post_init__(self):
         self._ctx = [Context(self.device) for _ in range(self.slots)]
         self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
+        self.stats = {"rounds": 0, "batches": 0, "held_rounds": 0, "peak_used": 0}
 
     def close(self):
         for c in self._ctx:
@@ -68,16 +72,22 @@ class Server:
             return _bytes(a)
         if r.kind == "assign":
             return _bytes(a) + _bytes(r.B)
-        return 0  # extractions are admitted by their exact count (below)
+        return 0  # extractions are admitted by their batch's exact count (below)
+
+    @staticmethod
+    def _batch_bytes(bt: ExtractBatch) -> int:
+        like = bt.mats[0]
+        return bt.nnz * (like.colidx.element_size() + like.values.element_size()) + (bt.rows + 1) * 8
 
     def run(self, reqs: list[Request]) -> list[Request]:
         """Serve ``reqs`` (sorted by arrival); fills ``done`` / ``nnz_out`` of each."""
         t0 = time.perf_counter()
         i, n = 0, len(reqs)
         inflight: list[tuple[list[Request], torch.cuda.Event, int, object]] = []
+        held = None  # (requests, counted batch, slot, bytes): waiting for memory
         used = 0
         turn = 0
-        while i < n or inflight:
+        while i < n or inflight or held:
             now = time.perf_counter() - t0
             # retire finished work (in issue order is not required)
             still = []
@@ -97,24 +107,20 @@ class Server:
             inflight = still
             # admit what has arrived
             ex, other = [], []
-            while i < n and reqs[i].arrival <= now and len(ex) < self.max_batch:
+            while i < n and reqs[i].arrival <= now:
                 r = reqs[i]
-                b = self._bound(r)
-                if b and used + b > self.mem_budget and (inflight or ex or other):
-                    break  # wait for memory to free up
                 if r.kind == "extract":
+                    if held is not None or len(ex) >= self.max_batch:
+                        break  # extractions stay in order behind a held batch
                     ex.append(r)
-                else:
-                    other.append(r)
-                    used += b
-                i += 1
-            if not ex and not other:
-                if inflight:
+                    i += 1
                     continue
-                if i < n:  # idle until the next arrival
-                    while time.perf_counter() - t0 < reqs[i].arrival:
-                        pass
-                continue
+                b = self._bound(r)
+                if used + b > self.mem_budget and (inflight or ex or other or held):
+                    break  # wait for memory to free up
+                other.append(r)
+                used += b
+                i += 1
             for r in other:
                 k = turn % self.slots
                 turn += 1
@@ -131,23 +137,37 @@ class Server:
                     ev = torch.cuda.Event()
                     ev.record(st)
                 inflight.append(([r], ev, self._bound(r), out))
-            if ex:
+            if ex:  # count the round's extractions as one batch
                 k = turn % self.slots
                 turn += 1
                 ctx, st = self._ctx[k], self._streams[k]
                 with torch.cuda.stream(st):
                     bt = ExtractBatch(ctx, self.mats, [(r.mat, r.I, r.J) for r in ex], stream=st)
-                    out = bt.alloc()
-                    nbytes = _bytes(out)
-                    bt.fill(out, st)
-                    offs = bt.row_offsets()
-                    if self.keep_results:
-                        for j, r in enumerate(ex):
-                            r.result = (out, offs[j], offs[j + 1])
-                    ev = torch.cuda.Event()
-                    ev.record(st)
-                used += nbytes
-                inflight.append((ex, ev, nbytes, (bt, out, offs)))
+                held = (ex, bt, k, self._batch_bytes(bt))
+                self.stats["batches"] += 1
+            if held is not None:
+                ex_h, bt, k, nbytes = held
+                if used + nbytes <= self.mem_budget or not inflight:
+                    ctx, st = self._ctx[k], self._streams[k]
+                    with torch.cuda.stream(st):
+                        out = bt.alloc()
+                        bt.fill(out, st)
+                        offs = bt.row_offsets()
+                        if self.keep_results:
+                            for j, r in enumerate(ex_h):
+                                r.result = (out, offs[j], offs[j + 1])
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                    used += nbytes
+                    inflight.append((ex_h, ev, nbytes, (bt, out, offs)))
+                    held = None
+                else:
+                    self.stats["held_rounds"] += 1
+            self.stats["peak_used"] = max(self.stats["peak_used"], used)
+            self.stats["rounds"] += 1
+            if not other and not ex and held is None and not inflight and i < n:
+                while time.perf_counter() - t0 < reqs[i].arrival:  # idle until the next arrival
+                    pass
         torch.cuda.synchronize()
         for c in self._ctx:
             c.sync()

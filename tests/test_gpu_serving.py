@@ -87,3 +87,35 @@ def test_served_equals_plain():
     assert st["p99_ms"] >= st["p50_ms"] >= 0
     srv.close()
     ctx.close()
+
+
+def test_extractions_held_by_memory():
+    """A budget smaller than any output: every counted extraction batch waits, counted but
+    not filled, until the work in flight retires; every result still equals the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_20776_gb300 import build
+    build.build()
+    from paper_2509_20776_gb300.serving import Server
+    mats = [to_dev(synth.rmat_csr(s, 6, seed=s + 1, symmetrize=True, value_kind="f32u01",
+                                  rowptr_dtype=torch.int64, colidx_dtype=torch.int32)) for s in (9, 11)]
+    reqs = _stream(mats, 80, 5, 1e9)  # everything arrives at once
+    srv = Server(mats, slots=2, mem_budget=1, keep_results=True)
+    srv.run(reqs)
+    assert srv.stats["held_rounds"] > 0 and srv.stats["batches"] > 0
+    hosts = [to_oracle(m) for m in mats]
+    for k, r in enumerate(reqs):
+        A = hosts[r.mat]
+        if r.kind == "permute":
+            assert_same(r.result, oracle.permute(A, r.p.cpu().numpy(), r.p.cpu().numpy()), f"request {k}")
+        elif r.kind == "assign":
+            assert_same(r.result, oracle.assign(A, r.I.cpu().numpy(), r.J.cpu().numpy(), to_oracle(r.B)),
+                        f"request {k}")
+        else:
+            ref = oracle.extract(A, r.I.cpu().numpy(), r.J.cpu().numpy())
+            out, r0, r1 = r.result
+            base, end = int(out.rowptr[r0]), int(out.rowptr[r1])
+            assert np.array_equal((out.rowptr[r0:r1 + 1] - base).cpu().numpy().astype(np.int64), ref.rowptr)
+            assert np.array_equal(out.colidx[base:end].cpu().numpy().astype(np.int64), ref.colidx)
+            assert np.array_equal(bits(out.values[base:end].cpu().numpy()), bits(ref.values))
+    srv.close()
