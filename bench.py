@@ -39,11 +39,11 @@ WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16
 # DRAM bytes (read + write) per output entry of one k_gather_chunks launch on the
 # first P A P^T (random p), from a one-kernel ncu capture of only
 # dram__bytes_read.sum + dram__bytes_write.sum on the rows-limited instance of the same
-# workload (bench.py --rows-limit 2097152: the first 2^21 rows, all 2^25 columns, so
-# the relabel map keeps its full-size L2 pressure); scaled to a full launch by the
-# entries it moves (profiles/gather_dram_rmat25_rows2m.md).  Only valid for the kernel
+# workload (bench.py --rows-limit 2097152: 2^21 random rows, all 2^25 columns, so the
+# relabel map keeps its full-size L2 pressure); scaled to a full launch by the entries
+# it moves (profiles/gather_dram_rmat25_rows2m.md).  Only valid for the kernel
 # as captured: retake the capture when it changes.
-GATHER_DRAM_BYTES_PER_ENTRY = None
+GATHER_DRAM_BYTES_PER_ENTRY = 24.87  # 1 642 645 248 B over 66 045 976 entries
 
 _T0 = time.time()
 
@@ -67,8 +67,8 @@ def parse():
     ap.add_argument("--lookup-sweep", action="store_true",
                     help="print the measured rate of uniform random 4-byte lookups per table size and exit")
     ap.add_argument("--rows-limit", type=int, default=0,
-                    help="profiling case: the headline matrix's first R rows (all columns), one "
-                         "permutation with independent random p, q; prints its line and exits")
+                    help="profiling case: R random rows of the headline matrix (all columns), "
+                         "one permutation with independent random p, q; prints its line and exits")
     return ap.parse_args()
 
 
@@ -292,25 +292,33 @@ def time_steps(fn, steps, warmup, ws):
     return ev[0].elapsed_time(ev[1])
 
 
-def run_rows_limited(args, ctx, A, dev):
-    """Profiling case (--rows-limit R): the first R rows of the headline matrix with all
-    its columns, B = P A Q^T with independent random p (R) and q (all columns): the
-    kernels see the full-size column maps at a few GB on the device."""
+def run_rows_limited(args, ctx, holder, dev):
+    """Profiling case (--rows-limit R): R random rows of the headline matrix (seeded, so
+    the row-length mix is the workload's) with all its columns, and
+    B = P A Q^T with independent random p (R) and q (all columns): the kernels see the
+    full-size column map (the relabel's L2 pressure) at a few GB on the device.  The full
+    matrix is released before the measured operation."""
     import torch
     import synth
     from paper_2509_20776_gb300 import CSR
-    R = min(args.rows_limit, A.nrows)
-    nz = int(A.rowptr[R])
-    Ar = CSR(R, A.ncols, A.rowptr[:R + 1].clone(), A.colidx[:nz].clone(), A.values[:nz].clone())
-    del A
+    A0 = holder.pop()
+    A = CSR(A0.nrows, A0.ncols, A0.rowptr, A0.colidx, A0.values)
+    del A0
+    step = max(1, A.nrows // max(1, args.rows_limit))
+    # a random subset (evenly spaced rows would favour R-MAT's heavy low-numbered rows)
+    I = synth.random_subset(A.nrows, A.nrows // step, 9, 0, device=dev)
+    Jall = torch.arange(0, A.ncols, dtype=torch.int32, device=dev)
+    Ar = ctx.sp_extract(A, I, Jall)  # consecutive J: rows copied as they are
+    del A, I, Jall
     torch.cuda.empty_cache()
+    R = Ar.nrows
     p = synth.random_permutation(R, 1, 0, device=dev)
     q = synth.random_permutation(Ar.ncols, 1, 1, device=dev)
     B = ctx.sp_permute(Ar, p, q)
     ms = time_steps(lambda: ctx.sp_permute(Ar, p, q, sync=False, out=B), max(1, args.steps), args.warmup, 1)
     ctx.sync()
-    return {"rows_limit": R, "ncols": Ar.ncols, "nnz": nz, "ms_per_op": round(ms / max(1, args.steps), 4),
-            "workload": "first R rows of the headline matrix, P A Q^T with random p, q"}
+    return {"rows_limit": R, "ncols": Ar.ncols, "nnz": Ar.nnz, "ms_per_op": round(ms / max(1, args.steps), 4),
+            "workload": "R random rows of the headline matrix, all columns; P A Q^T with random p, q"}
 
 
 def log_summary(res):
@@ -364,7 +372,9 @@ def run_ours(args, ws, rank, local):
     log(f"generated: {A.nrows} rows, {A.nnz} entries")
     if args.rows_limit:
         del ops
-        return run_rows_limited(args, ctx, A, dev)
+        holder = [A]
+        del A
+        return run_rows_limited(args, ctx, holder, dev)
     Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
     nnz, m = A.nnz, A.nrows
     outs = [ctx.sp_permute(Ad, p, q, sync=True) for _, p, q in ops]  # also validates
@@ -468,9 +478,12 @@ def e2e_permute(ctx, A, ops, args, ws):
     d2h = len(ops) * (out_rp.numel() * 8 + out_ci.numel() * 4 + out_v.numel() * 4)
 
     # Copies of large arrays are cut into NCOPY pieces on NCOPY streams per direction.
-    # Results go back on their own streams, so each one's device-to-host copy overlaps
-    # the next permutation and the next step's host-to-device copy of A.
-    NCOPY = 8
+    # Steps overlap: the result copies of step k (device -> host) run while step k+1
+    # copies its inputs in (host -> device, the link carries both directions at once) and
+    # permutes; step k+1 overwrites the device copy of A only after step k's last
+    # permutation has read it, and the copy streams keep every result copy in issue
+    # order.  The timed region ends after the last result copy of the last step.
+    NCOPY = 4
     cps_in = [torch.cuda.Stream(device=dev) for _ in range(NCOPY)]   # host -> device
     cps = [torch.cuda.Stream(device=dev) for _ in range(NCOPY)]      # device -> host
 
@@ -505,16 +518,34 @@ def e2e_permute(ctx, A, ops, args, ws):
                     t.record_stream(st)  # keep B's memory until its copies are done
         done[0] = torch.cuda.Event()
         done[0].record(main)
+
+    def drain():
+        main = torch.cuda.current_stream()
         for st in cps:
-            main.wait_stream(st)  # the step ends when every result is on the host
+            main.wait_stream(st)
 
     steps = max(1, args.steps // 2)
-    ms = time_steps(step, steps, 1, ws)
+    step()  # warm-up
+    drain()
+    torch.cuda.synchronize()
+    barrier(ws)
+    main = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(main)
+    for _ in range(steps):
+        step()
+    drain()
+    ev[1].record(main)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = ev[0].elapsed_time(ev[1])
     ctx.sync()
     ms = max_over_ranks(ms, ws)
     value = A.nnz * len(ops) * steps * ws / (ms * 1e-3)
     return {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(ms / steps, 3)}
+            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "schedule": "steps overlap: result copies of a step run with the next step's input copy and "
+                        "permutations; the timed region ends after the last result copy"}
 
 
 def bench_extract(ctx, args, dev, hbm, ws):
