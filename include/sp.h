@@ -144,11 +144,13 @@ SP_API int64_t sp_ctx_error_detail(const sp_ctx* ctx);
  *   SP_OPT_BATCH_ROWS      rows a warp serves at once in the batched extraction's count
  *                          and fill (32 / rows lanes per row): 1 (default), 2, 4 or 8;
  *   SP_OPT_IDENTIFY        how an extraction identifies the kept columns (general or
- *                          ascending J): 0 = rank map over the columns (a membership bit
- *                          and a rank per column, one position per member of J: n/4 +
- *                          |J| * idx bytes, two lookups per entry; default); 1 = J sorted
- *                          once, binary search per stored entry (Algorithm 5's search:
- *                          |J| log |J| set-up, no column-sized table). */
+ *                          ascending J, and every request of a batch): 0 = rank map over
+ *                          the columns (a membership bit and a rank per column, one
+ *                          position per member of J: n/4 + |J| * idx bytes, two lookups
+ *                          per entry; default; a batch whose maps would exceed 16 GB uses
+ *                          1); 1 = J sorted once, binary search per stored entry
+ *                          (Algorithm 5's search: |J| log |J| set-up, no column-sized
+ *                          table). */
 typedef enum sp_option {
   SP_OPT_SPIN_LIMIT = 0,
   SP_OPT_SCAN_HOLD_TILE = 1,

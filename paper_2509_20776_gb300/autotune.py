@@ -29,7 +29,7 @@ KNOBS = {
     "permute": ("tile_shape", "heavy"),
     "extract": ("identify", "tile_shape", "heavy"),
     "assign": ("count_rows", "fill_rows", "tile_shape", "heavy"),
-    "batch": ("batch_rows", "tile_shape", "heavy"),
+    "batch": ("identify", "batch_rows", "tile_shape", "heavy"),
 }
 SEARCH = {"tile_shape": (0, 1), "heavy": (128, 256, 512), "count_rows": (1, 2, 4), "fill_rows": (1, 2),
           "batch_rows": (1, 2, 4, 8), "identify": (0, 1)}

@@ -1,17 +1,24 @@
 // Batched extraction: B_k = A_{m_k}(I_k, J_k) for thousands of small requests in a fixed
 // number of launches over the whole batch (the batching pattern of the serving path).
 //
-// Identification uses each request's J sorted once (positions carried as values): a
-// stored column c of a selected row is looked up by binary search in the request's
-// sorted J -- the per-(i, j) search of Algorithm 5, which suits small |J| where a dense
-// inverse map per request would cost O(ncols).  Every step runs once for the batch:
-//   J gather -> segmented sort of the J's -> duplicate check -> per-row kept counts ->
-//   scan -> fill -> segmented sort of the output rows.
+// Identification, per request, by one of (SP_OPT_IDENTIFY):
+//   0 (default) a rank map per request: the request's slice of one batch-wide array of
+//     64-bit words, one per 32 columns of its matrix (membership bits | members before the
+//     word, counted over the whole batch), and the members' positions in J stored in that
+//     global rank order; a stored column is tested and relabelled with two lookups.  The
+//     slices take ncols/32 words per request; a batch whose slices would exceed
+//     kBatchMapBytes falls back to
+//   1 each request's J sorted once (positions carried as values), a stored column looked
+//     up by binary search in it: the per-(i, j) search of Algorithm 5.
+// Every step runs once for the batch: identify (bitmaps, scan, positions; or J gather,
+// segmented sort, duplicate check) -> per-row kept counts -> scan -> fill -> segmented
+// sort of the output rows.
 // The count call synchronises once (the batch's output size); the fill call allocates
 // nothing and never synchronises, so it can be captured in a CUDA graph and replayed.
 #include <vector>
 
 #include "dispatch.h"
+#include "extract_rows.cuh"
 #include "kernels.cuh"
 #include "rowsort.cuh"
 
@@ -24,12 +31,25 @@ struct BatchMat {  // a matrix of the batch (device arrays)
   long long nrows, ncols, nnz;
 };
 
-struct BatchReq {  // a request, with its offsets in the batch's J and output rows
+struct BatchReq {  // a request, with its offsets in the batch's J, output rows and map words
   long long mat, nI, nJ;
   const void* I;
   const void* J;
   long long roff, joff;
+  long long moff;  // first word of the request's rank-map slice (identify 0)
 };
+
+constexpr long long kBatchMapBytes = 16ll << 30;  // largest rank map a batch builds
+
+// What a batched row needs from its request: the matrix's arrays and the request's
+// rank-map slice (built on the host, one per request).
+struct ReqView {
+  const void* col;
+  const void* val;
+  const unsigned long long* meta;  // the request's slice of the batch's rank words
+  long long ncol;
+};
+
 
 }  // namespace sp
 
@@ -47,6 +67,17 @@ struct sp_batch {
   long long* djoff = nullptr;   // nreq + 1
   void* jkey = nullptr;         // jtot entries of idx_type: every J, sorted per request
   uint32_t* jpos = nullptr;     // jtot: position of each sorted J entry in its request
+  int identify = 1;             // 0: rank map, 1: sorted J
+  long long nwords = 0;         // rank-map words of the whole batch
+  uint32_t* jbits = nullptr;    // nwords membership words
+  unsigned long long* jmeta = nullptr;  // nwords: bits | members before the word (batch-wide)
+  uint32_t* jrp = nullptr;      // jtot: position in its request's J, in batch-wide rank order
+  long long* rs0 = nullptr;     // rank map: source start, length and request of every output row
+  long long* rsn = nullptr;
+  int* rreq = nullptr;
+  sp::ReqView* rv = nullptr;    // rank map: every request's arrays and slice
+  std::vector<sp::ReqView> hviews;  // host copy (kept: the copy to rv is asynchronous)
+  long long n_slow = 0;         // rank map: output rows of more than XFAST source entries
   long long* vp = nullptr;      // rows + 1: counts, then the output row pointer
   size_t ws_bytes = 0;          // workspace the fill needs (reserved by the count)
   cudaStream_t stream = nullptr;
@@ -82,6 +113,111 @@ __global__ void k_batch_gather_j(const BatchReq* __restrict__ reqs, const BatchM
     }
   }
 }
+
+// rank map: every request's J marked in its slice of the bitmap (a repeat is an error)
+template <class IX>
+__global__ void k_batch_mark(const BatchReq* __restrict__ reqs, const BatchMat* __restrict__ mats, long long nreq,
+                             uint32_t* __restrict__ bits, DevStatus* st) {
+  for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
+    const BatchReq q = reqs[k];
+    const long long n = mats[q.mat].ncols;
+    const IX* J = static_cast<const IX*>(q.J);
+    for (long long b = threadIdx.x; b < q.nJ; b += blockDim.x) {
+      const long long c = (long long)J[b];
+      if (c < 0 || c >= n) {
+        dev_fail(st, SP_ERR_INDEX_RANGE, q.joff + b);
+        continue;
+      }
+      const uint32_t m = 1u << (c & 31);
+      if (atomicOr(bits + q.moff + (c >> 5), m) & m) dev_fail(st, SP_ERR_DUPLICATE_INDEX, q.joff + b);
+    }
+  }
+}
+
+// rank map: jrp[rank(J_k[b])] = b, ranks counted over the whole batch
+template <class IX>
+__global__ void k_batch_jrank(const BatchReq* __restrict__ reqs, const BatchMat* __restrict__ mats, long long nreq,
+                              const unsigned long long* __restrict__ meta, uint32_t* __restrict__ jrp) {
+  for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
+    const BatchReq q = reqs[k];
+    const long long n = mats[q.mat].ncols;
+    const IX* J = static_cast<const IX*>(q.J);
+    for (long long b = threadIdx.x; b < q.nJ; b += blockDim.x) {
+      const long long c = (long long)J[b];
+      if (c < 0 || c >= n) continue;  // reported by k_batch_mark
+      const unsigned long long w = meta[q.moff + (c >> 5)];
+      const uint32_t bit = 1u << (c & 31);
+      jrp[uint32_t(w >> 32) + __popc(uint32_t(w) & (bit - 1u))] = uint32_t(b);
+    }
+  }
+}
+
+// rank map: source start, length and request of every output row (one CTA per request
+// at a time, its rows in parallel)
+template <class RP, class IX>
+__global__ void k_batch_rowinfo(const BatchReq* __restrict__ reqs, const BatchMat* __restrict__ mats, long long nreq,
+                                long long* __restrict__ rs0, long long* __restrict__ rsn, int* __restrict__ rreq,
+                                DevStatus* st) {
+  for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
+    const BatchReq q = reqs[k];
+    const BatchMat a = mats[q.mat];
+    const IX* I = static_cast<const IX*>(q.I);
+    const RP* rp = static_cast<const RP*>(a.rowptr);
+    for (long long t = threadIdx.x; t < q.nI; t += blockDim.x) {
+      const long long r = q.roff + t, src = (long long)I[t];
+      long long s = 0, L = 0;
+      if (src < 0 || src >= a.nrows) {
+        dev_fail(st, SP_ERR_INDEX_RANGE, r);
+      } else {
+        const long long b = (long long)rp[src], e = (long long)rp[src + 1];
+        if (b >= 0 && e >= b && e <= a.nnz) {
+          s = b;
+          L = e - b;
+        }
+      }
+      rs0[r] = s;
+      rsn[r] = L;
+      rreq[r] = int(k);
+    }
+  }
+}
+
+// Row source of the batched count and fill (extract_rows.cuh): output row r reads the
+// matrix of its request and tests / relabels through the request's rank-map slice.  The
+// per-row handle is the request's index; its view is read through the read-only cache.
+template <class CIt, class VTt>
+struct XBatchSrc {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr bool kLongCta = false;  // a warp takes every row, however long
+  struct H {
+    int k;
+  };
+  const int* rreq;
+  const ReqView* rv;
+  const uint32_t* jrp;
+  __device__ __forceinline__ H handle(long long r) const { return H{rreq[r]}; }
+  __device__ static __forceinline__ H shfl(const H& h, int k) { return H{__shfl_sync(kFull, h.k, k)}; }
+  __device__ __forceinline__ const CI* cols(const H& h) const { return static_cast<const CI*>(rv[h.k].col); }
+  __device__ __forceinline__ const VT* vals(const H& h) const { return static_cast<const VT*>(rv[h.k].val); }
+  __device__ __forceinline__ bool test(const H& h, long long c) const {
+    const long long n = __ldg(&rv[h.k].ncol);
+    if (c < 0 || c >= n) return false;
+    const unsigned long long* meta = rv[h.k].meta;
+    const unsigned long long w = (unsigned long long)ld_map(reinterpret_cast<const long long*>(meta) + (c >> 5));
+    return (uint32_t(w) >> (c & 31)) & 1u;
+  }
+  __device__ __forceinline__ bool map(const H& h, long long c, uint32_t& key) const {
+    const long long n = __ldg(&rv[h.k].ncol);
+    if (c < 0 || c >= n) return false;
+    const unsigned long long* meta = rv[h.k].meta;
+    const unsigned long long w = (unsigned long long)ld_map(reinterpret_cast<const long long*>(meta) + (c >> 5));
+    const uint32_t bits = uint32_t(w), b = 1u << (c & 31);
+    if (!(bits & b)) return false;
+    key = ld_plain(jrp + (uint32_t(w >> 32) + __popc(bits & (b - 1u))));
+    return true;
+  }
+};
 
 // J must be distinct within a request: equal neighbours in the sorted J of one request
 template <class IX>
@@ -167,16 +303,26 @@ __global__ void k_batch_rows(const BatchReq* __restrict__ reqs, const BatchMat* 
 template <class RP, class CI, class VT, class IX>
 sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>& hm,
                            const std::vector<BatchReq>& hr, cudaStream_t s) {
-  const long long nreq = b->nreq, rows = b->rows, jtot = b->jtot;
+  const long long nreq = b->nreq, rows = b->rows, jtot = b->jtot, nw = b->nwords;
+  // the rank map unless its slices are too large (or the batch's J too long for 32-bit ranks)
+  b->identify = (ctx->cur.identify == 0 && nw * 12 <= kBatchMapBytes && jtot < (1ll << 32)) ? 0 : 1;
+  const bool rank = b->identify == 0;
   Carver cv;
   const size_t o_m = cv.reserve(hm.size() * sizeof(BatchMat));
   const size_t o_r = cv.reserve(hr.size() * sizeof(BatchReq));
   const size_t o_ro = cv.reserve(size_t(nreq + 1) * 8);
   const size_t o_jo = cv.reserve(size_t(nreq + 1) * 8);
-  const size_t o_jk = cv.reserve(size_t(jtot) * sizeof(IX));
+  const size_t o_jk = cv.reserve(rank ? 0 : size_t(jtot) * sizeof(IX));
   const size_t o_jp = cv.reserve(size_t(jtot) * 4);
+  const size_t o_jb = cv.reserve(rank ? size_t(nw) * 4 : 0);
+  const size_t o_jm = cv.reserve(rank ? size_t(nw) * 8 : 0);
   const size_t o_vp = cv.reserve(size_t(rows + 1) * 8);
-  const size_t o_sc = cv.reserve(scan_ws_bytes(rows));
+  const size_t o_sc = cv.reserve(scan_ws_bytes(rows > nw ? rows : nw));
+  const size_t o_rs = cv.reserve(rank ? size_t(rows) * 8 : 0);
+  const size_t o_rn = cv.reserve(rank ? size_t(rows) * 8 : 0);
+  const size_t o_rq = cv.reserve(rank ? size_t(rows) * 4 : 0);
+  const size_t o_rv = cv.reserve(rank ? size_t(nreq) * sizeof(ReqView) : 0);
+  const size_t o_ct = cv.reserve(64);
   b->buf = static_cast<char*>(ctx_alloc(ctx, cv.total(), s));
   if (!b->buf) return SP_ERR_OOM;
   b->buf_bytes = cv.total();
@@ -185,9 +331,25 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   b->reqs = cv.at<BatchReq>(o_r);
   b->droff = cv.at<long long>(o_ro);
   b->djoff = cv.at<long long>(o_jo);
-  b->jkey = cv.at<void>(o_jk);
-  b->jpos = cv.at<uint32_t>(o_jp);
+  b->jkey = rank ? nullptr : cv.at<void>(o_jk);
+  b->jpos = rank ? nullptr : cv.at<uint32_t>(o_jp);
+  b->jrp = rank ? cv.at<uint32_t>(o_jp) : nullptr;
+  b->jbits = rank ? cv.at<uint32_t>(o_jb) : nullptr;
+  b->jmeta = rank ? cv.at<unsigned long long>(o_jm) : nullptr;
   b->vp = cv.at<long long>(o_vp);
+  b->rs0 = rank ? cv.at<long long>(o_rs) : nullptr;
+  b->rsn = rank ? cv.at<long long>(o_rn) : nullptr;
+  b->rreq = rank ? cv.at<int>(o_rq) : nullptr;
+  b->rv = rank ? cv.at<ReqView>(o_rv) : nullptr;
+  unsigned* counters = cv.at<unsigned>(o_ct);
+  if (rank && nreq > 0) {
+    b->hviews.resize(size_t(nreq));
+    for (long long k = 0; k < nreq; ++k) {
+      const BatchMat& a = hm[size_t(hr[size_t(k)].mat)];
+      b->hviews[size_t(k)] = ReqView{a.colidx, a.values, b->jmeta + hr[size_t(k)].moff, a.ncols};
+    }
+    SP_CUDA(cudaMemcpyAsync(b->rv, b->hviews.data(), size_t(nreq) * sizeof(ReqView), cudaMemcpyHostToDevice, s));
+  }
   std::vector<long long> joff(nreq + 1);
   for (long long k = 0; k <= nreq; ++k) joff[k] = k < nreq ? hr[k].joff : jtot;
   SP_CUDA(cudaMemcpyAsync(b->mats, hm.data(), hm.size() * sizeof(BatchMat), cudaMemcpyHostToDevice, s));
@@ -196,7 +358,28 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   SP_CUDA(cudaMemcpyAsync(b->djoff, joff.data(), size_t(nreq + 1) * 8, cudaMemcpyHostToDevice, s));
   const int nsm = ctx->num_sms;
   IX* jkey = static_cast<IX*>(b->jkey);
-  if (jtot > 0) {
+  if (rank) {
+    // every request's slice: bits (repeats reported), batch-wide ranks, positions
+    SP_CUDA(cudaMemsetAsync(b->jbits, 0, size_t(nw) * 4, s));
+    if (jtot > 0) {
+      {
+        SP_PHASE(SP_PHASE_MAP);
+        k_batch_mark<IX><<<unsigned(nreq < 65535 ? nreq : 65535), 256, 0, s>>>(b->reqs, b->mats, nreq, b->jbits,
+                                                                            ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+    }
+    SP_TRY(launch_scan(ctx, s, LoadPopc{b->jbits}, StoreRank{b->jbits, b->jmeta, nw}, nw, cv.at<char>(o_sc),
+                       SP_PHASE_MAP));
+    if (jtot > 0) {
+      {
+        SP_PHASE(SP_PHASE_MAP);
+        k_batch_jrank<IX><<<unsigned(nreq < 65535 ? nreq : 65535), 256, 0, s>>>(b->reqs, b->mats, nreq, b->jmeta,
+                                                                             b->jrp);
+      }
+      SP_CUDA(cudaGetLastError());
+    }
+  } else if (jtot > 0) {
     {
       SP_PHASE(SP_PHASE_MAP);
       k_batch_gather_j<IX><<<unsigned(nreq < 65535 ? nreq : 65535), 256, 0, s>>>(b->reqs, b->mats, nreq, jkey,
@@ -219,28 +402,47 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
     }
     SP_CUDA(cudaGetLastError());
   }
-  if (rows > 0) {
+  SP_CUDA(cudaMemsetAsync(counters, 0, 64, s));
+  if (rows > 0 && rank) {
+    // every output row's source, then the count of k_xcount (lane-per-row, grouped loads)
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_batch_rowinfo<RP, IX><<<unsigned(nreq < 65535 ? nreq : 65535), 256, 0, s>>>(
+          b->reqs, b->mats, nreq, b->rs0, b->rsn, b->rreq, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      const XBatchSrc<CI, uint32_t> src{b->rreq, b->rv, b->jrp};
+      k_xcount<<<grid_for((rows + 31) / 32 * 32, XB, nsm * 8), XB, 0, s>>>(
+          src, XResolveRecorded{b->rs0, b->rsn}, rows, b->vp, nullptr, counters, 0, counters + 1, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  } else if (rows > 0) {
     {
       SP_PHASE(SP_PHASE_COUNT);
       const int rpw = ctx->cur.batch_rows;
-      k_batch_rows<0, RP, CI, VT, IX><<<grid_for((rows + rpw - 1) / rpw * 32, 256, nsm * 16), 256, 0, s>>>(
-          b->reqs, b->mats, b->droff, nreq, rows, jkey, b->jpos, b->vp, nullptr, nullptr, rpw, ctx->dstatus);
+      const int g = grid_for((rows + rpw - 1) / rpw * 32, 256, nsm * 16);
+      k_batch_rows<0, RP, CI, VT, IX><<<g, 256, 0, s>>>(b->reqs, b->mats, b->droff, nreq, rows, jkey, b->jpos, b->vp,
+                                                        nullptr, nullptr, rpw, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
   }
   SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp}, StoreDual<long long>{b->vp, nullptr, ctx->dstatus},
                      rows, cv.at<char>(o_sc)));
   long long* h = nullptr;
-  SP_CUDA(cudaMallocHost(&h, 8));
+  SP_CUDA(cudaMallocHost(&h, 16));
   cudaMemcpyAsync(h, b->vp + rows, 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h + 1, counters + 1, 4, cudaMemcpyDeviceToHost, s);
   const sp_status st = ctx_collect(ctx, s);
-  b->nnz = *h;
+  b->nnz = h[0];
+  b->n_slow = rank ? (long long)*reinterpret_cast<const unsigned*>(h + 1) : 0;
   cudaFreeHost(h);
   SP_TRY(st);
   // reserve now the workspace the fill's row sort needs, so the fill allocates nothing
   Carver cf;
   size_t rf[kRowsSlots];
-  rows_reserve(cf, rows, b->nnz, sizeof(VT), rf);
+  rows_reserve(cf, rows, b->nnz, sizeof(VT), rf, true, b->n_slow);
   b->ws_bytes = cf.total();
   char* base;
   SP_TRY(ctx_workspace(ctx, b->ws_bytes, s, &base));
@@ -254,7 +456,7 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
   // a failure leaves the output untouched
   Carver cf;
   size_t rf[kRowsSlots];
-  rows_reserve(cf, rows, nnz, sizeof(VT), rf);
+  rows_reserve(cf, rows, nnz, sizeof(VT), rf, true, b->n_slow);
   if (nnz > 0 && cf.total() > ctx->ws_cap) return SP_ERR_INTERNAL;
   // the int64 row pointer is the batch's own; an int32 output gets a narrowed copy
   if (out->rowptr_type == SP_I64) {
@@ -268,19 +470,38 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
   if (nnz == 0) return SP_OK;
   CI* oc = static_cast<CI*>(out->colidx);
   VT* ov = static_cast<VT*>(out->values);
+  const int kb = ceil_log2_u64(uint64_t(b->max_nj > 1 ? b->max_nj : 1));
+  if (b->identify == 0) {
+    // k_xfill: short rows relabelled, ranked and written once; longer rows in source
+    // order, queued for the row sort
+    char* base;
+    SP_TRY(ctx_workspace(ctx, cf.total(), s, &base));
+    cf.bind(base);
+    const RowsWs w = rows_bind(cf, rows, nnz, rf, true, b->n_slow);
+    SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      const XBatchSrc<CI, VT> src{b->rreq, b->rv, b->jrp};
+      k_xfill<XBatchSrc<CI, VT>, false><<<grid_for((rows + 31) / 32 * 32, XB, ctx->num_sms * 8), XB, 0, s>>>(
+          src, rows, b->rs0, b->rsn, b->vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+          w.huge_cap, kb, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    return sort_queued<CI, VT>(ctx, s, w, kb, oc, ov);
+  }
   {
     SP_PHASE(SP_PHASE_GATHER);
     const int rpw = ctx->cur.batch_rows;
-    k_batch_rows<1, RP, CI, VT, IX><<<grid_for((rows + rpw - 1) / rpw * 32, 256, ctx->num_sms * 16), 256, 0, s>>>(
-        b->reqs, b->mats, b->droff, b->nreq, rows, static_cast<const IX*>(b->jkey), b->jpos, b->vp, oc, ov, rpw,
-        ctx->dstatus);
+    const int g = grid_for((rows + rpw - 1) / rpw * 32, 256, ctx->num_sms * 16);
+    k_batch_rows<1, RP, CI, VT, IX><<<g, 256, 0, s>>>(b->reqs, b->mats, b->droff, b->nreq, rows,
+                                                      static_cast<const IX*>(b->jkey), b->jpos, b->vp, oc, ov, rpw,
+                                                      ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   char* base;
   SP_TRY(ctx_workspace(ctx, cf.total(), s, &base));
   cf.bind(base);
-  const RowsWs w = rows_bind(cf, rows, nnz, rf);
-  const int kb = ceil_log2_u64(uint64_t(b->max_nj > 1 ? b->max_nj : 1));
+  const RowsWs w = rows_bind(cf, rows, nnz, rf, true, b->n_slow);
   return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, b->vp, rows, nnz, kb, w, nullptr, true, oc, ov);
 }
 
@@ -327,7 +548,8 @@ extern "C" sp_status sp_extract_batch_count(sp_ctx* ctx, const sp_csr* mats, int
       return q.mat < 0 || q.mat >= nmats || (q.nI > 0 && !q.I) || (q.nJ > 0 && !q.J) ? SP_ERR_INVALID_ARG
                                                                                      : SP_ERR_SHAPE;
     }
-    hr[k] = BatchReq{q.mat, q.nI, q.nJ, q.I, q.J, b->rows, b->jtot};
+    hr[k] = BatchReq{q.mat, q.nI, q.nJ, q.I, q.J, b->rows, b->jtot, b->nwords};
+    b->nwords += (mats[q.mat].ncols + 31) / 32;
     b->roff[k] = b->rows;
     b->rows += q.nI;
     b->jtot += q.nJ;

@@ -345,9 +345,10 @@ sp_status extract_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
       using Test = decltype(test);
       {
         SP_PHASE(SP_PHASE_COUNT);
-        k_xcount<RP, CI, IX, Test><<<g, XB, 0, s>>>(rp, ci, I, nI, m, nnz, test, pl->vp, pl->sstart, pl->slen,
-                                                    pl->cl_rows, pl->counters + 0, pl->list_cap, pl->counters + 4,
-                                                    ctx->dstatus);
+        const XOne<CI, uint32_t, Test> src{ci, nullptr, test};
+        const XResolveI<RP, IX> res{rp, I, m, nnz, pl->sstart, pl->slen, ctx->dstatus};
+        k_xcount<<<g, XB, 0, s>>>(src, res, nI, pl->vp, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->counters + 4,
+                                  ctx->dstatus);
       }
       SP_CUDA(cudaGetLastError());
       const XLongRows<CI, uint32_t, Test> lr{ci, nullptr, test, pl->sstart, pl->slen};
@@ -430,14 +431,15 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
     using Rel = decltype(rel);
     {
       SP_PHASE(SP_PHASE_GATHER);
+      const XOne<CI, VT, Rel> src{ci, vv, rel};
       if (sorted)
-        k_xfill<CI, VT, Rel, true><<<g, XB, 0, s>>>(ci, vv, rel, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
-                                                    w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap, kb,
-                                                    ctx->dstatus);
+        k_xfill<XOne<CI, VT, Rel>, true><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
+                                                          w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+                                                          w.huge_cap, kb, ctx->dstatus);
       else
-        k_xfill<CI, VT, Rel, false><<<g, XB, 0, s>>>(ci, vv, rel, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
-                                                     w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap,
-                                                     kb, ctx->dstatus);
+        k_xfill<XOne<CI, VT, Rel>, false><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
+                                                           w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+                                                           w.huge_cap, kb, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
     // rows of more than SRC_LONG source entries: one CTA each, kept entries in source order

@@ -24,6 +24,8 @@
 //   while its table is L2-resident (~300 G/s on GB300), fewer for tables above ~100 MB.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "rowsort.cuh"
 
@@ -31,7 +33,7 @@ namespace sp {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int XFAST = 64;     // rows of at most this many source entries: masks, warp sort
-constexpr int XC_ROWS = 8;    // rows whose columns a counting warp loads together
+constexpr int XC_ROWS = 6;    // rows whose columns a counting warp loads together
 constexpr int XF_ROWS = 4;    // rows whose kept entries a filling warp loads together
 constexpr int XB = 256;       // threads per CTA of the count / fill
 constexpr unsigned kDropped = 0xFFFFFFFFu;  // padding key: never below a key
@@ -132,84 +134,151 @@ __global__ void k_jsorted_init(const IX* __restrict__ J, long long nJ, uint32_t*
   }
 }
 
+// ---- row sources ---------------------------------------------------------------------
+// Where listed row i's entries are and how a stored column is tested / relabelled:
+//   using CI, VT;  using H = ...;            per-row handle (the arrays of the row's matrix)
+//   H handle(long long i) const;             the handle of listed row i (lane-per-row)
+//   static H shfl(const H& h, int lane);     another lane's handle
+//   const CI* cols(const H&); const VT* vals(const H&);
+//   bool test(const H&, long long c);  bool map(const H&, long long c, uint32_t& key);
+//   kLongCta: rows of more than SRC_LONG entries go to the CTA-per-row kernels
+// One matrix and one identify for every row:
+template <class CIt, class VTt, class Rel>
+struct XOne {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr bool kLongCta = true;
+  struct H {};
+  const CI* col;
+  const VT* val;
+  Rel rel;
+  __device__ __forceinline__ H handle(long long) const { return H{}; }
+  __device__ static __forceinline__ H shfl(const H& h, int) { return h; }
+  __device__ __forceinline__ const CI* cols(const H&) const { return col; }
+  __device__ __forceinline__ const VT* vals(const H&) const { return val; }
+  __device__ __forceinline__ bool test(const H&, long long c) const { return rel.test(c); }
+  __device__ __forceinline__ bool map(const H&, long long c, uint32_t& key) const { return rel.map(c, key); }
+};
+
+// Row resolvers of the count: listed row i -> (source start, length).
+struct XSpan {
+  long long s, L;
+};
+// From the index vector and the row pointer (range-checked; the pair is recorded):
+template <class RP, class IX>
+struct XResolveI {
+  const RP* rowptr;
+  const IX* I;
+  long long m, nnz;
+  long long* rs0;
+  long long* rsn;
+  DevStatus* st;
+  __device__ __forceinline__ XSpan operator()(long long i) const {
+    XSpan sp{0, 0};
+    const long long r = (long long)I[i];
+    if (r < 0 || r >= m) {
+      dev_fail(st, SP_ERR_INDEX_RANGE, i);
+    } else {
+      const long long a = (long long)rowptr[r], b = (long long)rowptr[r + 1];
+      if (a >= 0 && b >= a && b <= nnz) sp = XSpan{a, b - a};
+    }
+    rs0[i] = sp.s;
+    rsn[i] = sp.L;
+    return sp;
+  }
+};
+// From a table recorded earlier:
+struct XResolveRecorded {
+  const long long* rs0;
+  const long long* rsn;
+  __device__ __forceinline__ XSpan operator()(long long i) const { return XSpan{rs0[i], rsn[i]}; }
+};
+
 // ---- count ---------------------------------------------------------------------------
-// cnt[i] = kept entries of selected row i (rows of more than SRC_LONG source entries are
-// listed for k_count_long instead); rs0 / rsn = source start / length of every row;
-// *n_slow += rows of more than XFAST source entries (the fill queues their sort).
-template <class RP, class CI, class IX, class Test>
-__global__ void __launch_bounds__(XB, 4) k_xcount(const RP* __restrict__ rowptr, const CI* __restrict__ col,
-                                                 const IX* __restrict__ I, long long nI, long long m, long long nnz,
-                                                 Test test, long long* __restrict__ cnt, long long* __restrict__ rs0,
-                                                 long long* __restrict__ rsn, long long* __restrict__ cl_rows,
-                                                 unsigned* n_cl, long long cl_cap, unsigned* n_slow, DevStatus* st) {
+// cnt[i] = kept entries of listed row i (with Src::kLongCta, rows of more than SRC_LONG
+// source entries are listed for k_count_long instead); *n_slow += rows of more than XFAST
+// source entries (the fill queues their sort).
+template <class Src, class Res>
+__global__ void __launch_bounds__(XB, 4) k_xcount(Src src, Res res, long long nI, long long* __restrict__ cnt,
+                                                 long long* __restrict__ cl_rows, unsigned* n_cl, long long cl_cap,
+                                                 unsigned* n_slow, DevStatus* st) {
+  using CI = typename Src::CI;
+  using H = typename Src::H;
   constexpr int R = XC_ROWS;
+  constexpr long long kLong = Src::kLongCta ? SRC_LONG : (1ll << 62);
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i0 = w0 * 32; i0 < nI; i0 += nw * 32) {
     const long long i = i0 + lane;
     long long s = 0, L = 0;
+    H h{};
     if (i < nI) {
-      const long long r = (long long)I[i];
-      if (r < 0 || r >= m) {
-        dev_fail(st, SP_ERR_INDEX_RANGE, i);
-      } else {
-        const long long a = (long long)rowptr[r], b = (long long)rowptr[r + 1];
-        if (a >= 0 && b >= a && b <= nnz) {
-          s = a;
-          L = b - a;
-        }
-      }
-      rs0[i] = s;
-      rsn[i] = L;
+      const XSpan sp = res(i);
+      s = sp.s;
+      L = sp.L;
+      h = src.handle(i);
     }
     const unsigned slow = __ballot_sync(kFull, L > XFAST);
     if (lane == 0 && slow) atomicAdd(n_slow, unsigned(__popc(slow)));
-    if (L > SRC_LONG) push_row(cl_rows, n_cl, cl_cap, i, st);
+    if (L > kLong) push_row(cl_rows, n_cl, cl_cap, i, st);
     long long mine = 0;
     const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
     for (int g = 0; g < nr; g += R) {
       long long ss[R];
-      int LL[R];
+      int LL[R];  // the row's length, capped (the loop over a longer row re-reads it)
       CI c0[R], c1[R];
+      // the handle of row g + u (nothing for a single matrix; one shuffle for a batch)
+      auto hof = [&](int u) { return Src::shfl(h, (g + u) & 31); };
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
         const long long l = __shfl_sync(kFull, L, (g + u) & 31);
-        LL[u] = (g + u < nr && l <= SRC_LONG) ? int(l) : 0;
+        if constexpr (Src::kLongCta) LL[u] = (g + u < nr && l <= kLong) ? int(l) : 0;
+        else LL[u] = g + u < nr ? int(l < (1 << 30) ? l : (1 << 30)) : 0;
       }
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        c0[u] = lane < LL[u] ? ld_stream(col + ss[u] + lane) : CI(0);
-        c1[u] = lane + 32 < LL[u] ? ld_stream(col + ss[u] + 32 + lane) : CI(0);
+        const CI* cp = src.cols(hof(u));
+        c0[u] = lane < LL[u] ? ld_stream(cp + ss[u] + lane) : CI(0);
+        c1[u] = lane + 32 < LL[u] ? ld_stream(cp + ss[u] + 32 + lane) : CI(0);
       }
       bool k0[R], k1[R];
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        k0[u] = lane < LL[u] && test.test((long long)c0[u]);
-        k1[u] = lane + 32 < LL[u] && test.test((long long)c1[u]);
+        const H hu = hof(u);
+        k0[u] = lane < LL[u] && src.test(hu, (long long)c0[u]);
+        k1[u] = lane + 32 < LL[u] && src.test(hu, (long long)c1[u]);
       }
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         long long c = __popc(__ballot_sync(kFull, k0[u])) + __popc(__ballot_sync(kFull, k1[u]));
-        // rows of XFAST < L <= SRC_LONG entries: the rest in batches of LOAD_U x 32
-        for (int e0 = 64; e0 < LL[u]; e0 += 32 * LOAD_U) {
+        // rows of more than XFAST entries: the rest in batches of LOAD_U x 32
+        const H hu = hof(u);
+        const CI* cp = src.cols(hu);
+        // (single matrix: LL is the length itself; batched rows re-read a capped length)
+        using LT = std::conditional_t<Src::kLongCta, int, long long>;
+        LT Lu = LT(LL[u]);
+        if constexpr (!Src::kLongCta) {
+          if (LL[u] > 64) Lu = __shfl_sync(kFull, L, (g + u) & 31);
+        }
+        for (LT e0 = 64; e0 < Lu; e0 += 32 * LOAD_U) {
           CI cc[LOAD_U];
 #pragma unroll
           for (int v = 0; v < LOAD_U; ++v) {
-            const int e = e0 + v * 32 + lane;
-            cc[v] = e < LL[u] ? ld_stream(col + ss[u] + e) : CI(0);
+            const LT e = e0 + v * 32 + lane;
+            cc[v] = e < Lu ? ld_stream(cp + ss[u] + e) : CI(0);
           }
 #pragma unroll
           for (int v = 0; v < LOAD_U; ++v) {
-            const int e = e0 + v * 32 + lane;
-            c += __popc(__ballot_sync(kFull, e < LL[u] && test.test((long long)cc[v])));
+            const LT e = e0 + v * 32 + lane;
+            c += __popc(__ballot_sync(kFull, e < Lu && src.test(hu, (long long)cc[v])));
           }
         }
         if (lane == g + u) mine = c;
       }
     }
-    if (i < nI && L <= SRC_LONG) cnt[i] = mine;
+    if (i < nI && L <= kLong) cnt[i] = mine;
   }
 }
 
@@ -243,14 +312,18 @@ __device__ __forceinline__ void x_queue(long long o, long long k, int key_bits, 
 
 // kSorted: the relabelling keeps the source order (ascending J), so slots are ranks and
 // no row is queued.
-template <class CI, class VT, class Rel, bool kSorted>
-__global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, const VT* __restrict__ val, Rel rel,
-                                                long long nI, const long long* __restrict__ rs0,
+template <class Src, bool kSorted>
+__global__ void __launch_bounds__(XB, 3) k_xfill(Src src, long long nI, const long long* __restrict__ rs0,
                                                 const long long* __restrict__ rsn, const long long* __restrict__ vp,
-                                                CI* __restrict__ out_col, VT* __restrict__ out_val, FinalEntry* fin,
+                                                typename Src::CI* __restrict__ out_col,
+                                                typename Src::VT* __restrict__ out_val, FinalEntry* fin,
                                                 unsigned* fin_n, long long fin_cap, HugeEntry* huge, unsigned* huge_n,
                                                 long long huge_cap, int key_bits, DevStatus* st) {
+  using CI = typename Src::CI;
+  using VT = typename Src::VT;
+  using H = typename Src::H;
   constexpr int R = XF_ROWS, NWB = XB / 32, KW = XFAST + 4;
+  constexpr long long kLong = Src::kLongCta ? SRC_LONG : (1ll << 62);
   __shared__ __align__(16) uint32_t s_key[NWB][KW];  // a row's kept keys (+ padding for 4-wide loads)
   __shared__ VT s_val[NWB][XFAST];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -262,17 +335,20 @@ __global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, con
   for (long long i0 = w0 * 32; i0 < nI; i0 += nw * 32) {
     const long long i = i0 + lane;
     long long s = 0, L = 0, o = 0, oe = 0;
+    H h{};
     if (i < nI) {
       s = rs0[i];
       L = rsn[i];
       o = vp[i];
       oe = vp[i + 1];
+      h = src.handle(i);
     }
     if (!kSorted && L > XFAST) x_queue(o, oe - o, key_bits, fin, fin_n, fin_cap, huge, huge_n, huge_cap, st);
     const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
     for (int g = 0; g < nr; g += R) {
       long long ss[R];
       int LL[R];
+      H hh[R];
       CI c0[R], c1[R];
       VT v0[R], v1[R];
 #pragma unroll
@@ -280,24 +356,27 @@ __global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, con
         ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
         const long long l = __shfl_sync(kFull, L, (g + u) & 31);
         LL[u] = (g + u < nr && l <= XFAST) ? int(l) : 0;
+        hh[u] = Src::shfl(h, (g + u) & 31);
       }
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        c0[u] = lane < LL[u] ? ld_stream(col + ss[u] + lane) : CI(0);
-        c1[u] = lane + 32 < LL[u] ? ld_stream(col + ss[u] + 32 + lane) : CI(0);
+        const CI* cp = src.cols(hh[u]);
+        c0[u] = lane < LL[u] ? ld_stream(cp + ss[u] + lane) : CI(0);
+        c1[u] = lane + 32 < LL[u] ? ld_stream(cp + ss[u] + 32 + lane) : CI(0);
       }
       // values of dropped entries are loaded too: they share sectors with kept ones
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        if (lane < LL[u]) v0[u] = ld_stream(val + ss[u] + lane);
-        if (lane + 32 < LL[u]) v1[u] = ld_stream(val + ss[u] + 32 + lane);
+        const VT* vq = src.vals(hh[u]);
+        if (lane < LL[u]) v0[u] = ld_stream(vq + ss[u] + lane);
+        if (lane + 32 < LL[u]) v1[u] = ld_stream(vq + ss[u] + 32 + lane);
       }
       uint32_t k0[R], k1[R];
       bool p0[R], p1[R];
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        p0[u] = lane < LL[u] && rel.map((long long)c0[u], k0[u]);
-        p1[u] = lane + 32 < LL[u] && rel.map((long long)c1[u], k1[u]);
+        p0[u] = lane < LL[u] && src.map(hh[u], (long long)c0[u], k0[u]);
+        p1[u] = lane + 32 < LL[u] && src.map(hh[u], (long long)c1[u], k1[u]);
       }
 #pragma unroll
       for (int u = 0; u < R; ++u) {
@@ -356,13 +435,16 @@ __global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, con
         }
       }
     }
-    // rows of XFAST < L <= SRC_LONG source entries: kept entries in source order (ballot
-    // slots); their sort was queued above
-    unsigned mid = __ballot_sync(kFull, L > XFAST && L <= SRC_LONG);
+    // rows of more than XFAST source entries (up to SRC_LONG with Src::kLongCta): kept
+    // entries in source order (ballot slots); their sort was queued above
+    unsigned mid = __ballot_sync(kFull, L > XFAST && L <= kLong);
     while (mid) {
       const int k = __ffs(mid) - 1;
       mid &= mid - 1;
       const long long sk = __shfl_sync(kFull, s, k), Lk = __shfl_sync(kFull, L, k);
+      const H hk = Src::shfl(h, k);
+      const CI* cp = src.cols(hk);
+      const VT* vq = src.vals(hk);
       long long ok = __shfl_sync(kFull, o, k);
       const long long ek = __shfl_sync(kFull, oe, k);
       for (long long e0 = 0; e0 < Lk; e0 += 32 * LOAD_U) {
@@ -373,13 +455,13 @@ __global__ void __launch_bounds__(XB, 3) k_xfill(const CI* __restrict__ col, con
 #pragma unroll
         for (int v = 0; v < LOAD_U; ++v) {
           const long long e = e0 + v * 32 + lane;
-          cc[v] = e < Lk ? ld_stream(col + sk + e) : CI(0);
-          if (e < Lk) vv[v] = ld_stream(val + sk + e);
+          cc[v] = e < Lk ? ld_stream(cp + sk + e) : CI(0);
+          if (e < Lk) vv[v] = ld_stream(vq + sk + e);
         }
 #pragma unroll
         for (int v = 0; v < LOAD_U; ++v) {
           const long long e = e0 + v * 32 + lane;
-          pp[v] = e < Lk && rel.map((long long)cc[v], kk[v]);
+          pp[v] = e < Lk && src.map(hk, (long long)cc[v], kk[v]);
         }
 #pragma unroll
         for (int v = 0; v < LOAD_U; ++v) {

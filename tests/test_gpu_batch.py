@@ -1,5 +1,6 @@
 """Batched extraction (one count + one capturable fill for thousands of requests) against
-the oracle, request by request, bit-exact; the same results alone and in the batch; CUDA
+the oracle, request by request, bit-exact, with either identify (per-request rank maps,
+or each request's J sorted and searched); the same results alone and in the batch; CUDA
 graph capture and replay of the fill."""
 import numpy as np
 import pytest
@@ -67,13 +68,18 @@ def _check(out, offs, ms, reqs, what):
         assert np.array_equal(vv[sl].view(np.uint32), want.values.view(np.uint32)), f"{what}: request {k} values"
 
 
-def test_batch_matches_oracle(ctx):
+@pytest.mark.parametrize("identify", [0, 1])
+def test_batch_matches_oracle(ctx, identify):
     ms = _mats()
     dms = [to_dev(m) for m in ms]
     reqs = _requests(ms, 300, 1)
     dreqs = [(mi, I.cuda(), J.cuda()) for mi, I, J in reqs]
-    out, offs = ctx.sp_extract_batch(dms, dreqs)
-    _check(out, offs, ms, reqs, "batch")
+    ctx.set_shapes(identify=identify)
+    try:
+        out, offs = ctx.sp_extract_batch(dms, dreqs)
+    finally:
+        ctx.set_shapes(identify=-1)
+    _check(out, offs, ms, reqs, f"batch, identify {identify}")
 
 
 def test_batch_same_alone_and_in_the_mix(ctx):
@@ -118,17 +124,26 @@ def test_batch_graph_replay(ctx):
     bt.close()
 
 
-def test_batch_errors(ctx):
+@pytest.mark.parametrize("identify", [0, 1])
+def test_batch_errors(ctx, identify):
     from paper_2509_20776_gb300 import SpError
     ms = _mats()
     dms = [to_dev(m) for m in ms]
     I = torch.tensor([0, 1], dtype=torch.int32).cuda()
-    with pytest.raises(SpError) as e:
-        ctx.sp_extract_batch(dms, [(0, I, torch.tensor([5, 7, 5], dtype=torch.int32).cuda())])
-    assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
-    with pytest.raises(SpError) as e:
-        ctx.sp_extract_batch(dms, [(0, I, torch.tensor([5, 1 << 20], dtype=torch.int32).cuda())])
-    assert e.value.name == "SP_ERR_INDEX_RANGE"
+    ctx.set_shapes(identify=identify)
+    try:
+        with pytest.raises(SpError) as e:
+            ctx.sp_extract_batch(dms, [(0, I, torch.tensor([5, 7, 5], dtype=torch.int32).cuda())])
+        assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
+        with pytest.raises(SpError) as e:
+            ctx.sp_extract_batch(dms, [(0, I, torch.tensor([5, 1 << 20], dtype=torch.int32).cuda())])
+        assert e.value.name == "SP_ERR_INDEX_RANGE"
+        # the same J in two requests is fine (repeats are per request)
+        J = torch.tensor([5, 7], dtype=torch.int32).cuda()
+        out, offs = ctx.sp_extract_batch(dms, [(0, I, J), (0, I, J)])
+        assert offs == [0, 2, 4]
+    finally:
+        ctx.set_shapes(identify=-1)
     with pytest.raises(SpError) as e:
         ctx.sp_extract_batch(dms, [(9, I, I)])
     assert e.value.name == "SP_ERR_INVALID_ARG"
