@@ -322,6 +322,53 @@ SP_API int64_t sp_batch_row_offset(const sp_batch* batch, int64_t k);
 /* Release a batch (stream-ordered on the stream of its count).  NULL is a no-op. */
 SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
 
+/* ------------------------------------------------------------------------------
+ * Batched permutation (the same batching pattern; no counterpart in the paper)
+ *   B_k = P_k A_{mat} Q_k^T, B_k[i, j] = A_{mat}[p_k[i], q_k[j]] (Sec. 2.1) for nreq
+ *   requests over nmats device-resident matrices of one type combination; p_k (nrows
+ *   entries) and q_k (ncols entries) of idx_type, device pointers, NULL = identity.
+ *   Every input matrix must be canonical CSR (columns ascending and distinct within a
+ *   row): a row of at most 64 entries is ranked in one warp, which assumes distinct
+ *   keys.
+ * sp_permute_batch_plan: host only, no device synchronisation.  Lays out the batch
+ *   (a permutation keeps every entry, so the output size is known: *nnz_total = the
+ *   sum of the matrices' nnz over the requests) and allocates one device buffer
+ *   (inverse column maps, row bitmaps, the row table, the row pointer, the row-sort
+ *   workspace), whose request tables it copies on `stream`: a fill on another stream
+ *   must be ordered after it.  *plan borrows the matrices and p_k, q_k until
+ *   destroyed; the fill reads p_k and q_k when it runs, so a replayed graph picks up
+ *   new permutations written into the same buffers.
+ * sp_permute_batch_fill: runs the whole batch on `stream` (per request the inverse
+ *   column map and the row bitmap, which validate q_k and p_k; the row table; the row
+ *   pointer; the fill; the sort of rows of more than 64 entries) into one CSR `out`:
+ *   request k owns rows [sp_pbatch_row_offset(k), sp_pbatch_row_offset(k+1)) and its
+ *   columns keep their meaning; out has the sum of nrows rows and the largest ncols as
+ *   its column count.  out's arrays are caller-allocated (nnz_total entries, the
+ *   matrices' colidx / value types, any rowptr type).  Never synchronises and allocates
+ *   nothing, so the whole batch can be captured in a CUDA graph and replayed while the
+ *   inputs keep their addresses.
+ *   Errors: SP_ERR_INVALID_ARG, SP_ERR_OVERFLOW (int32 indices or rowptr too narrow,
+ *   more than 2^31 - 1 requests); from the device (sp_ctx_sync) SP_ERR_NOT_PERMUTATION,
+ *   SP_ERR_INDEX_RANGE (a stored column outside [0, ncols)), SP_ERR_NOT_CANONICAL (row
+ *   lengths that do not add up to a matrix's nnz); on a device error the output is not
+ *   the permutation but no write leaves its arrays.
+ * ------------------------------------------------------------------------------ */
+typedef struct sp_permute_req {
+  int64_t mat;   /* index of the matrix in mats */
+  const void* p; /* device, nrows entries (new row -> old row) or NULL */
+  const void* q; /* device, ncols entries (new column -> old column) or NULL */
+} sp_permute_req;
+typedef struct sp_pbatch sp_pbatch;
+
+SP_API sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int64_t nmats,
+                                       const sp_permute_req* reqs, int64_t nreq, sp_itype idx_type,
+                                       sp_pbatch** plan, int64_t* nnz_total, sp_stream_t stream);
+SP_API sp_status sp_permute_batch_fill(sp_ctx* ctx, sp_pbatch* plan, sp_csr* out, sp_stream_t stream);
+/* First output row of request k (k = nreq gives the total); -1 for a bad k. */
+SP_API int64_t sp_pbatch_row_offset(const sp_pbatch* plan, int64_t k);
+/* Release a batch plan (stream-ordered on the stream of its plan call).  NULL is a no-op. */
+SP_API sp_status sp_pbatch_destroy(sp_ctx* ctx, sp_pbatch* plan);
+
 /* Release a plan (stream-ordered on the stream of its last call).  NULL is a no-op. */
 SP_API sp_status sp_plan_destroy(sp_ctx* ctx, sp_plan* plan);
 

@@ -116,11 +116,16 @@ class sp_extract_req(ctypes.Structure):
                 ("I", ctypes.c_void_p), ("J", ctypes.c_void_p)]
 
 
+class sp_permute_req(ctypes.Structure):
+    _fields_ = [("mat", ctypes.c_int64), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
 _PCSR = ctypes.POINTER(sp_csr)
 _PREQ = ctypes.POINTER(sp_extract_req)
+_PPREQ = ctypes.POINTER(sp_permute_req)
 SIGNATURES = {
     "sp_status_str": (ctypes.c_char_p, [_int]),
     "sp_version": (_int, []),
@@ -147,6 +152,10 @@ SIGNATURES = {
     "sp_extract_batch_fill": (_int, [_vp, _vp, _PCSR, _vp]),
     "sp_batch_row_offset": (_i64, [_vp, _i64]),
     "sp_batch_destroy": (_int, [_vp, _vp]),
+    "sp_permute_batch_plan": (_int, [_vp, _PCSR, _i64, _PPREQ, _i64, _int, _vp, _vp, _vp]),
+    "sp_permute_batch_fill": (_int, [_vp, _vp, _PCSR, _vp]),
+    "sp_pbatch_row_offset": (_i64, [_vp, _i64]),
+    "sp_pbatch_destroy": (_int, [_vp, _vp]),
     "sp_plan_destroy": (_int, [_vp, _vp]),
     "sp_csr_free": (_int, [_vp, _PCSR]),
     "sp_inverse_map": (_int, [_vp, _vp, _i64, _i64, _int, _vp, _int, _vp]),
@@ -418,6 +427,24 @@ class Context:
         finally:
             bt.close()
 
+    def permute_batch(self, mats, requests, stream=None) -> "PermuteBatch":
+        """Plan a batch of permutations B_k = P_k mats[m_k] Q_k^T; ``requests`` holds
+        (m_k, p_k, q_k) with device index tensors of one dtype (or None for the identity).
+        Host only: the output size is the sum of the matrices' nnz."""
+        return PermuteBatch(self, mats, requests, stream)
+
+    def sp_permute_batch(self, mats, requests, rowptr_dtype=torch.int64, stream=None):
+        """All results of a batch of permutations in one CSR plus the first row of every
+        request."""
+        bt = self.permute_batch(mats, requests, stream)
+        try:
+            out = bt.alloc(rowptr_dtype)
+            bt.fill(out, stream)
+            self.sync(stream)
+            return out, bt.row_offsets()
+        finally:
+            bt.close()
+
     def _alloc(self, nrows, ncols, nnz, rowptr_dtype, like: CSR) -> CSR:
         dev = like.colidx.device
         return CSR(nrows, ncols, torch.empty(nrows + 1, dtype=rowptr_dtype, device=dev),
@@ -519,6 +546,71 @@ class ExtractBatch:
     def close(self):
         if self.handle:
             self.ctx.lib.sp_batch_destroy(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PermuteBatch:
+    """A planned batch of permutations (``sp_permute_batch_plan``): ``fill`` launches the
+    whole batch, its validation included, without synchronising (capturable in a CUDA
+    graph)."""
+
+    def __init__(self, ctx: Context, mats, requests, stream=None):
+        self.ctx = ctx
+        self.mats = list(mats)
+        self.requests = list(requests)
+        self.handle = None
+        if not self.mats:
+            raise ValueError("a batch needs at least one matrix")
+        dts = {t.dtype for _, p, q in self.requests for t in (p, q) if t is not None}
+        if len(dts) > 1:
+            raise TypeError("all index tensors of a batch share one dtype")
+        idx_t = _itype(dts.pop() if dts else torch.int32)
+        self._descs = (sp_csr * len(self.mats))(*[m.desc() for m in self.mats])
+        self._reqs = (sp_permute_req * max(1, len(self.requests)))()
+        for k, (mi, p, q) in enumerate(self.requests):
+            a = self.mats[int(mi)] if 0 <= int(mi) < len(self.mats) else None
+            if a is not None and ((p is not None and p.numel() != a.nrows) or
+                                  (q is not None and q.numel() != a.ncols)):
+                raise ValueError(f"request {k}: p needs nrows and q ncols entries")
+            self._reqs[k] = sp_permute_req(int(mi), p.data_ptr() if p is not None and p.numel() else None,
+                                           q.data_ptr() if q is not None and q.numel() else None)
+        h = ctypes.c_void_p()
+        nnz = ctypes.c_int64()
+        ctx._check(ctx.lib.sp_permute_batch_plan(ctx.handle, self._descs, len(self.mats), self._reqs,
+                                                 len(self.requests), idx_t, ctypes.byref(h),
+                                                 ctypes.byref(nnz), _stream(stream)),
+                   "sp_permute_batch_plan")
+        self.handle = h
+        self.nnz = nnz.value
+        self.rows = int(ctx.lib.sp_pbatch_row_offset(h, len(self.requests)))
+        self.ncols = max([self.mats[int(mi)].ncols for mi, _, _ in self.requests] + [0])
+
+    def row_offsets(self):
+        return [int(self.ctx.lib.sp_pbatch_row_offset(self.handle, k))
+                for k in range(len(self.requests) + 1)]
+
+    def alloc(self, rowptr_dtype=torch.int64) -> CSR:
+        like = self.mats[0]
+        dev = like.colidx.device
+        return CSR(self.rows, self.ncols, torch.empty(self.rows + 1, dtype=rowptr_dtype, device=dev),
+                   torch.empty(self.nnz, dtype=like.colidx.dtype, device=dev),
+                   torch.empty(self.nnz, dtype=like.values.dtype, device=dev))
+
+    def fill(self, out: CSR, stream=None):
+        self._out_desc = out.desc()  # kept alive: a captured graph replays with these pointers
+        self.ctx._check(self.ctx.lib.sp_permute_batch_fill(self.ctx.handle, self.handle,
+                                                           ctypes.byref(self._out_desc), _stream(stream)),
+                        "sp_permute_batch_fill")
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.sp_pbatch_destroy(self.ctx.handle, self.handle)
             self.handle = None
 
     def __del__(self):

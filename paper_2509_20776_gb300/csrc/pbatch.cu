@@ -1,0 +1,372 @@
+// Batched permutation: B_k = P_k A_{m_k} Q_k^T (Sec. 2.1; HipPerm) for many requests over
+// device-resident matrices, in a fixed number of launches for the whole batch (the
+// batching pattern of the serving path; the paper has no batched form).
+//
+// The output size of a permutation is the input's, so the plan (host only: request and
+// matrix tables, buffer layout) knows every row pointer's extent and the batch's nnz
+// without touching the device; the fill then runs everything on one stream with no
+// synchronisation and no allocation, so the whole batch can be captured in a CUDA graph:
+//   per request: inverse column map qinv_k (validates q_k) and a bitmap of p_k
+//   (validates p_k) -> a table of every output row's source (start, length, request) ->
+//   exclusive scan of the lengths (the row pointer) -> the fill of extract_rows.cuh
+//   (every entry kept, relabelled through its request's qinv; rows of at most XFAST
+//   entries ranked and written once, longer rows queued) -> the row sort of the queue.
+#include <vector>
+
+#include "dispatch.h"
+#include "extract_rows.cuh"
+#include "kernels.cuh"
+#include "rowsort.cuh"
+
+namespace sp {
+
+struct PermReq {  // a request with its offsets in the batch's rows, map words and bitmaps
+  long long mat, nrows, ncols;
+  const void* p;  // new row -> old row (null: identity)
+  const void* q;  // new column -> old column (null: identity)
+  long long roff;  // first output row
+  long long qoff;  // first entry of the request's qinv
+  long long boff;  // first word of the request's row bitmap
+};
+
+struct PermView {  // what an output row needs from its request
+  const void* col;
+  const void* val;
+  const void* qinv;  // the request's inverse column map (null: identity)
+  long long ncol;
+};
+
+// per request: qinv[q[j]] = j (a repeat or an index out of range is not a permutation)
+// and the bitmap of p
+template <class IX>
+__global__ void k_pbatch_maps(const PermReq* __restrict__ reqs, long long nreq, IX* __restrict__ qinv,
+                              uint32_t* __restrict__ pbits, DevStatus* st) {
+  for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
+    const PermReq r = reqs[k];
+    const IX* q = static_cast<const IX*>(r.q);
+    const IX* p = static_cast<const IX*>(r.p);
+    if (q) {
+      for (long long j = threadIdx.x; j < r.ncols; j += blockDim.x) {
+        const long long c = (long long)q[j];
+        if (c < 0 || c >= r.ncols) {
+          dev_fail(st, SP_ERR_NOT_PERMUTATION, j);
+          continue;
+        }
+        IX* slot = qinv + r.qoff + c;
+        if constexpr (sizeof(IX) == 4) {
+          if (atomicCAS(reinterpret_cast<int*>(slot), -1, int(j)) != -1) dev_fail(st, SP_ERR_NOT_PERMUTATION, j);
+        } else {
+          if (atomicCAS(reinterpret_cast<unsigned long long*>(slot), ~0ull, (unsigned long long)j) != ~0ull)
+            dev_fail(st, SP_ERR_NOT_PERMUTATION, j);
+        }
+      }
+    }
+    if (p) {
+      for (long long i = threadIdx.x; i < r.nrows; i += blockDim.x) {
+        const long long v = (long long)p[i];
+        if (v < 0 || v >= r.nrows) {
+          dev_fail(st, SP_ERR_NOT_PERMUTATION, i);
+          continue;
+        }
+        const uint32_t m = 1u << (v & 31);
+        if (atomicOr(pbits + r.boff + (v >> 5), m) & m) dev_fail(st, SP_ERR_NOT_PERMUTATION, i);
+      }
+    }
+  }
+}
+
+// every output row's source start, length and request
+template <class RP, class IX>
+__global__ void k_pbatch_rowinfo(const PermReq* __restrict__ reqs, const sp_csr* __restrict__ mats, long long nreq,
+                                 long long* __restrict__ rs0, long long* __restrict__ rsn, int* __restrict__ rreq) {
+  for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
+    const PermReq r = reqs[k];
+    const sp_csr a = mats[r.mat];
+    const IX* p = static_cast<const IX*>(r.p);
+    const RP* rp = static_cast<const RP*>(a.rowptr);
+    for (long long i = threadIdx.x; i < r.nrows; i += blockDim.x) {
+      const long long src = p ? (long long)p[i] : i;
+      long long s = 0, L = 0;
+      if (src >= 0 && src < r.nrows) {  // else reported by k_pbatch_maps
+        const long long b = (long long)rp[src], e = (long long)rp[src + 1];
+        if (b >= 0 && e >= b && e <= a.nnz) {
+          s = b;
+          L = e - b;
+        }
+      }
+      rs0[r.roff + i] = s;
+      rsn[r.roff + i] = L;
+      rreq[r.roff + i] = int(k);
+    }
+  }
+}
+
+// Row source of the fill (extract_rows.cuh): every stored entry is kept; its column is
+// relabelled through the request's qinv.  The per-row handle is the request's index.  A
+// stored column outside [0, ncols) is reported (SP_ERR_INDEX_RANGE) and not written.
+template <class CIt, class VTt, class IX>
+struct XPermBatchSrc {
+  using CI = CIt;
+  using VT = VTt;
+  static constexpr bool kLongCta = false;  // a warp takes every row, however long
+  struct H {
+    int k;
+  };
+  const int* rreq;
+  const PermView* pv;
+  DevStatus* st;
+  __device__ __forceinline__ H handle(long long r) const { return H{rreq[r]}; }
+  __device__ static __forceinline__ H shfl(const H& h, int k) { return H{__shfl_sync(kFull, h.k, k)}; }
+  __device__ __forceinline__ const CI* cols(const H& h) const { return static_cast<const CI*>(pv[h.k].col); }
+  __device__ __forceinline__ const VT* vals(const H& h) const { return static_cast<const VT*>(pv[h.k].val); }
+  __device__ __forceinline__ bool map(const H& h, long long c, uint32_t& key) const {
+    const PermView& v = pv[h.k];
+    if (c < 0 || c >= v.ncol) {
+      dev_fail(st, SP_ERR_INDEX_RANGE, c);
+      return false;
+    }
+    key = v.qinv ? uint32_t((long long)ld_map(static_cast<const IX*>(v.qinv) + c)) : uint32_t(c);
+    return true;
+  }
+};
+
+// Scan output of the batch's row pointer, clamped to the output's nnz so that no row
+// reaches past the output arrays: the lengths of a valid batch add up to exactly its nnz
+// (each source row taken once); a repeated row of p is reported by k_pbatch_maps, a row
+// pointer whose lengths do not add up to nnz here (SP_ERR_NOT_CANONICAL).
+template <class T>
+struct StoreCapped {
+  long long* vp;
+  T* out;  // may be null
+  long long n, cap;
+  DevStatus* st;
+  __device__ void operator()(long long i, long long v) const {
+    if (v > cap || (i == n && v != cap)) {
+      dev_fail(st, SP_ERR_NOT_CANONICAL, i);
+      if (v > cap) v = cap;
+    }
+    vp[i] = v;
+    if (out) out[i] = T(v);
+  }
+};
+
+}  // namespace sp
+
+struct sp_pbatch {
+  long long nreq = 0, nmats = 0, rows = 0, nnz = 0, qtot = 0, btot = 0, max_cols = 0;
+  sp_itype idx_type = SP_I32, rowptr_type = SP_I64, colidx_type = SP_I32;
+  sp_vtype value_type = SP_F32;
+  std::vector<long long> roff;  // host: first output row of every request (+ total)
+  std::vector<sp::PermReq> hreq;
+  std::vector<sp::PermView> hview;
+  std::vector<sp_csr> hmats;
+  char* buf = nullptr;  // device: tables, maps, row table, row pointer, scan and sort workspace
+  size_t buf_bytes = 0;
+  cudaStream_t stream = nullptr;
+  size_t o_req = 0, o_view = 0, o_mat = 0, o_qinv = 0, o_bits = 0, o_rs0 = 0, o_rsn = 0, o_rreq = 0, o_vp = 0,
+         o_scan = 0;
+  size_t ro[sp::kRowsSlots] = {};
+  long long fin_extra = 0;  // rows the fill may queue (more than XFAST entries)
+};
+
+namespace sp {
+
+template <class RP, class CI, class VT, class IX>
+sp_status pbatch_fill_impl(sp_ctx* ctx, sp_pbatch* b, sp_csr* out, cudaStream_t s) {
+  const long long nreq = b->nreq, rows = b->rows, nnz = b->nnz;
+  Carver cv;  // the plan's layout, rebuilt to bind the pointers
+  cv.bind(b->buf);
+  PermReq* reqs = cv.at<PermReq>(b->o_req);
+  PermView* views = cv.at<PermView>(b->o_view);
+  sp_csr* mats = cv.at<sp_csr>(b->o_mat);
+  IX* qinv = cv.at<IX>(b->o_qinv);
+  uint32_t* pbits = cv.at<uint32_t>(b->o_bits);
+  long long* rs0 = cv.at<long long>(b->o_rs0);
+  long long* rsn = cv.at<long long>(b->o_rsn);
+  int* rreq = cv.at<int>(b->o_rreq);
+  long long* vp = cv.at<long long>(b->o_vp);
+  const int nsm = ctx->num_sms;
+  const unsigned gq = unsigned(nreq < 65535 ? nreq : 65535);
+  if (b->qtot > 0) SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(b->qtot) * sizeof(IX), s));
+  if (b->btot > 0) SP_CUDA(cudaMemsetAsync(pbits, 0, size_t(b->btot) * 4, s));
+  if (nreq > 0) {
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_pbatch_maps<IX><<<gq, 256, 0, s>>>(reqs, nreq, qinv, pbits, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_pbatch_rowinfo<RP, IX><<<gq, 256, 0, s>>>(reqs, mats, nreq, rs0, rsn, rreq);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  // row pointer of the batch: scan of the row lengths, mirrored into the output's type
+  if (out->rowptr_type == SP_I64) {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{rsn},
+                       StoreCapped<long long>{vp, static_cast<long long*>(out->rowptr), rows, nnz, ctx->dstatus},
+                       rows, cv.at<char>(b->o_scan)));
+  } else {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{rsn},
+                       StoreCapped<int32_t>{vp, static_cast<int32_t*>(out->rowptr), rows, nnz, ctx->dstatus},
+                       rows, cv.at<char>(b->o_scan)));
+  }
+  if (nnz == 0 || rows == 0) return SP_OK;
+  CI* oc = static_cast<CI*>(out->colidx);
+  VT* ov = static_cast<VT*>(out->values);
+  const RowsWs w = rows_bind(cv, rows, nnz, b->ro, true, b->fin_extra);
+  SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
+  const int kb = ceil_log2_u64(uint64_t(b->max_cols > 1 ? b->max_cols : 1));
+  {
+    SP_PHASE(SP_PHASE_GATHER);
+    const XPermBatchSrc<CI, VT, IX> src{rreq, views, ctx->dstatus};
+    k_xfill<XPermBatchSrc<CI, VT, IX>, false><<<grid_for((rows + 31) / 32 * 32, XB, nsm * 8), XB, 0, s>>>(
+        src, rows, rs0, rsn, vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap, kb,
+        ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  return sort_queued<CI, VT>(ctx, s, w, kb, oc, ov);
+}
+
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int64_t nmats, const sp_permute_req* reqs,
+                                           int64_t nreq, sp_itype idx_type, sp_pbatch** plan, int64_t* nnz_total,
+                                           sp_stream_t stream) {
+  if (!ctx || !plan || !nnz_total || nmats < 0 || nreq < 0) return SP_ERR_INVALID_ARG;
+  if ((nmats > 0 && !mats) || (nreq > 0 && !reqs)) return SP_ERR_INVALID_ARG;
+  if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (nmats == 0 && nreq > 0) return SP_ERR_INVALID_ARG;
+  if (nreq > INT32_MAX) return SP_ERR_OVERFLOW;  // a row's request is an int
+  for (int64_t t = 0; t < nmats; ++t) {
+    SP_TRY(check_csr(&mats[t]));
+    if (mats[t].rowptr_type != mats[0].rowptr_type || mats[t].colidx_type != mats[0].colidx_type ||
+        mats[t].value_type != mats[0].value_type)
+      return SP_ERR_INVALID_ARG;  // one type combination per batch
+    if (mats[t].ncols > (int64_t(1) << 32)) return SP_ERR_OVERFLOW;  // 32-bit sort keys
+    if (idx_type == SP_I32 && (mats[t].nrows > INT32_MAX || mats[t].ncols > INT32_MAX)) return SP_ERR_OVERFLOW;
+  }
+  sp_pbatch* b = new sp_pbatch();
+  b->nreq = nreq;
+  b->nmats = nmats;
+  b->idx_type = idx_type;
+  if (nmats > 0) {
+    b->rowptr_type = mats[0].rowptr_type;
+    b->colidx_type = mats[0].colidx_type;
+    b->value_type = mats[0].value_type;
+  }
+  b->hmats.assign(mats, mats + nmats);
+  b->hreq.resize(size_t(nreq));
+  b->roff.assign(size_t(nreq + 1), 0);
+  for (int64_t k = 0; k < nreq; ++k) {
+    const sp_permute_req& q = reqs[k];
+    if (q.mat < 0 || q.mat >= nmats) {
+      delete b;
+      return SP_ERR_INVALID_ARG;
+    }
+    const sp_csr& a = mats[q.mat];
+    b->hreq[size_t(k)] = PermReq{q.mat, a.nrows, a.ncols, q.p, q.q, b->rows, q.q ? b->qtot : 0, q.p ? b->btot : 0};
+    b->roff[size_t(k)] = b->rows;
+    b->rows += a.nrows;
+    b->nnz += a.nnz;
+    if (q.q) b->qtot += a.ncols;
+    if (q.p) b->btot += (a.nrows + 31) / 32;
+    if (a.ncols > b->max_cols) b->max_cols = a.ncols;
+    b->fin_extra += a.nnz / (XFAST + 1) + 1;  // rows of more than XFAST entries
+  }
+  b->roff[size_t(nreq)] = b->rows;
+  const size_t is = itype_size(idx_type), vs = nmats > 0 ? vtype_size(b->value_type) : 4;
+  Carver cv;
+  b->o_req = cv.reserve(size_t(nreq) * sizeof(PermReq));
+  b->o_view = cv.reserve(size_t(nreq) * sizeof(PermView));
+  b->o_mat = cv.reserve(size_t(nmats) * sizeof(sp_csr));
+  b->o_qinv = cv.reserve(size_t(b->qtot) * is);
+  b->o_bits = cv.reserve(size_t(b->btot) * 4);
+  b->o_rs0 = cv.reserve(size_t(b->rows) * 8);
+  b->o_rsn = cv.reserve(size_t(b->rows) * 8);
+  b->o_rreq = cv.reserve(size_t(b->rows) * 4);
+  b->o_vp = cv.reserve(size_t(b->rows + 1) * 8);
+  b->o_scan = cv.reserve(scan_ws_bytes(b->rows));
+  rows_reserve(cv, b->rows, b->nnz, vs, b->ro, true, b->fin_extra);
+  cudaStream_t s = (cudaStream_t)stream;
+  b->stream = s;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    delete b;
+    return SP_ERR_CUDA;
+  }
+  ctx_begin_call(ctx, SP_OP_BATCH, b->rows);
+  b->buf = static_cast<char*>(ctx_alloc(ctx, cv.total(), s));
+  if (!b->buf) {
+    delete b;
+    return SP_ERR_OOM;
+  }
+  b->buf_bytes = cv.total();
+  cv.bind(b->buf);
+  b->hview.resize(size_t(nreq));
+  {
+    char* qbase = cv.at<char>(b->o_qinv);
+    for (int64_t k = 0; k < nreq; ++k) {
+      const PermReq& r = b->hreq[size_t(k)];
+      const sp_csr& a = mats[r.mat];
+      b->hview[size_t(k)] = PermView{a.colidx, a.values, r.q ? qbase + size_t(r.qoff) * is : nullptr, a.ncols};
+    }
+  }
+  sp_status st = SP_OK;
+  auto copy = [&](size_t off, const void* src, size_t bytes) {
+    if (st == SP_OK && bytes && cudaMemcpyAsync(cv.at<char>(off), src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      st = SP_ERR_CUDA;
+  };
+  copy(b->o_req, b->hreq.data(), size_t(nreq) * sizeof(PermReq));
+  copy(b->o_view, b->hview.data(), size_t(nreq) * sizeof(PermView));
+  copy(b->o_mat, b->hmats.data(), size_t(nmats) * sizeof(sp_csr));
+  if (st != SP_OK) {
+    sp_pbatch_destroy(ctx, b);
+    return st;
+  }
+  *plan = b;
+  *nnz_total = b->nnz;
+  return SP_OK;
+}
+
+extern "C" sp_status sp_permute_batch_fill(sp_ctx* ctx, sp_pbatch* b, sp_csr* out, sp_stream_t stream) {
+  if (!ctx || !b || !out) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type != SP_I32 && out->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type == SP_I32 && b->nnz > INT32_MAX) return SP_ERR_OVERFLOW;
+  if (!out->rowptr || (b->nnz > 0 && (!out->colidx || !out->values))) return SP_ERR_INVALID_ARG;
+  if (b->nmats > 0 && (out->colidx_type != b->colidx_type || out->value_type != b->value_type))
+    return SP_ERR_INVALID_ARG;
+  out->nrows = b->rows;
+  out->ncols = b->max_cols;
+  out->nnz = b->nnz;
+  cudaStream_t s = (cudaStream_t)stream;
+  SP_CUDA(cudaSetDevice(ctx->device));
+  ctx_begin_call(ctx, SP_OP_BATCH, b->rows);
+  return dispatch_i(b->rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(b->colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(b->value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(b->idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return pbatch_fill_impl<RP, CI, VT, IX>(ctx, b, out, s);
+        });
+      });
+    });
+  });
+}
+
+extern "C" int64_t sp_pbatch_row_offset(const sp_pbatch* b, int64_t k) {
+  if (!b || k < 0 || k > b->nreq) return -1;
+  return b->roff[size_t(k)];
+}
+
+extern "C" sp_status sp_pbatch_destroy(sp_ctx* ctx, sp_pbatch* b) {
+  if (!b) return SP_OK;
+  if (b->buf && ctx) ctx_free(ctx, b->buf, b->buf_bytes, b->stream);
+  delete b;
+  return SP_OK;
+}
