@@ -327,9 +327,6 @@ SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
  *   B_k = P_k A_{mat} Q_k^T, B_k[i, j] = A_{mat}[p_k[i], q_k[j]] (Sec. 2.1) for nreq
  *   requests over nmats device-resident matrices of one type combination; p_k (nrows
  *   entries) and q_k (ncols entries) of idx_type, device pointers, NULL = identity.
- *   Every input matrix must be canonical CSR (columns ascending and distinct within a
- *   row): a row of at most 64 entries is ranked in one warp, which assumes distinct
- *   keys.
  * sp_permute_batch_plan: host only, no device synchronisation.  Lays out the batch
  *   (a permutation keeps every entry, so the output size is known: *nnz_total = the
  *   sum of the matrices' nnz over the requests) and allocates one device buffer
@@ -340,7 +337,8 @@ SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
  *   new permutations written into the same buffers.
  * sp_permute_batch_fill: runs the whole batch on `stream` (per request the inverse
  *   column map and the row bitmap, which validate q_k and p_k; the row table; the row
- *   pointer; the fill; the sort of rows of more than 64 entries) into one CSR `out`:
+ *   pointer; the partition, gather and row sort of sp_permute over the whole batch)
+ *   into one CSR `out`:
  *   request k owns rows [sp_pbatch_row_offset(k), sp_pbatch_row_offset(k+1)) and its
  *   columns keep their meaning; out has the sum of nrows rows and the largest ncols as
  *   its column count.  out's arrays are caller-allocated (nnz_total entries, the
@@ -348,10 +346,11 @@ SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
  *   nothing, so the whole batch can be captured in a CUDA graph and replayed while the
  *   inputs keep their addresses.
  *   Errors: SP_ERR_INVALID_ARG, SP_ERR_OVERFLOW (int32 indices or rowptr too narrow,
- *   more than 2^31 - 1 requests); from the device (sp_ctx_sync) SP_ERR_NOT_PERMUTATION,
- *   SP_ERR_INDEX_RANGE (a stored column outside [0, ncols)), SP_ERR_NOT_CANONICAL (row
- *   lengths that do not add up to a matrix's nnz); on a device error the output is not
- *   the permutation but no write leaves its arrays.
+ *   more than 2^23 requests, a matrix of 2^40 entries or more); from the device
+ *   (sp_ctx_sync) SP_ERR_NOT_PERMUTATION, SP_ERR_INDEX_RANGE (under a column map, a
+ *   stored column outside [0, ncols)), SP_ERR_NOT_CANONICAL (row lengths that do not
+ *   add up to a matrix's nnz); on a device error the output is not the permutation but
+ *   no write leaves its arrays.
  * ------------------------------------------------------------------------------ */
 typedef struct sp_permute_req {
   int64_t mat;   /* index of the matrix in mats */

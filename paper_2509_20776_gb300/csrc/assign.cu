@@ -492,7 +492,7 @@ struct FusedGs {
     }
     return (pos >= 0 && pos < nnzA) ? ld_stream(valA + pos) : VT(0);
   }
-  __device__ CI map(CI c) const {
+  __device__ CI map(long long, CI c) const {
     if (!qinv) return c;
     const long long cl = (long long)c;
     if (cl < 0 || cl >= n) return CI(-1);  // reported as SP_ERR_INDEX_RANGE by the sort

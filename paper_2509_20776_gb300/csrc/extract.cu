@@ -54,7 +54,7 @@ struct ExtractRangeGs {
   __device__ long long src(long long i) const { return sstart[i]; }
   __device__ CI col(long long pos) const { return ld_stream(c_ + pos); }
   __device__ VT val(long long pos) const { return ld_stream(v_ + pos); }
-  __device__ CI map(CI c) const { return CI((long long)c - j0); }
+  __device__ CI map(long long, CI c) const { return CI((long long)c - j0); }
 };
 
 // Repeated J (Sec. 2.2 allows repeats): column c of A feeds every position b with

@@ -7,14 +7,14 @@
 // without touching the device; the fill then runs everything on one stream with no
 // synchronisation and no allocation, so the whole batch can be captured in a CUDA graph:
 //   per request: inverse column map qinv_k (validates q_k) and a bitmap of p_k
-//   (validates p_k) -> a table of every output row's source (start, length, request) ->
-//   exclusive scan of the lengths (the row pointer) -> the fill of extract_rows.cuh
-//   (every entry kept, relabelled through its request's qinv; rows of at most XFAST
-//   entries ranked and written once, longer rows queued) -> the row sort of the queue.
+//   (validates p_k) -> every output row's source (request k and start s packed as
+//   k * 2^40 + s) and length -> exclusive scan of the lengths (the row pointer) -> the
+//   two-phase path of the single permutation over the whole batch: partition of the
+//   output rows, load-balanced chunk gather with the relabelling through each row's
+//   request, in-place row sort.
 #include <vector>
 
 #include "dispatch.h"
-#include "extract_rows.cuh"
 #include "kernels.cuh"
 #include "rowsort.cuh"
 
@@ -29,12 +29,17 @@ struct PermReq {  // a request with its offsets in the batch's rows, map words a
   long long boff;  // first word of the request's row bitmap
 };
 
-struct PermView {  // what an output row needs from its request
-  const void* col;
-  const void* val;
-  const void* qinv;  // the request's inverse column map (null: identity)
+// what an output row needs from its request (read through the read-only cache)
+struct PermView {
+  unsigned long long col;   // const CI*
+  unsigned long long val;   // const VT*
+  unsigned long long qinv;  // const IX*: the request's inverse column map (0: identity)
   long long ncol;
 };
+
+constexpr int kReqShift = 40;  // source position = request * 2^40 + entry of its matrix
+constexpr long long kEntryMask = (1ll << kReqShift) - 1;
+constexpr long long kMaxReqs = 1ll << 23;
 
 // per request: qinv[q[j]] = j (a repeat or an index out of range is not a permutation)
 // and the bitmap of p
@@ -75,10 +80,10 @@ __global__ void k_pbatch_maps(const PermReq* __restrict__ reqs, long long nreq, 
   }
 }
 
-// every output row's source start, length and request
+// every output row's source (request and start, packed) and length
 template <class RP, class IX>
 __global__ void k_pbatch_rowinfo(const PermReq* __restrict__ reqs, const sp_csr* __restrict__ mats, long long nreq,
-                                 long long* __restrict__ rs0, long long* __restrict__ rsn, int* __restrict__ rreq) {
+                                 long long* __restrict__ rsrc, long long* __restrict__ rsn) {
   for (long long k = blockIdx.x; k < nreq; k += gridDim.x) {
     const PermReq r = reqs[k];
     const sp_csr a = mats[r.mat];
@@ -94,39 +99,38 @@ __global__ void k_pbatch_rowinfo(const PermReq* __restrict__ reqs, const sp_csr*
           L = e - b;
         }
       }
-      rs0[r.roff + i] = s;
+      rsrc[r.roff + i] = (k << kReqShift) | s;
       rsn[r.roff + i] = L;
-      rreq[r.roff + i] = int(k);
     }
   }
 }
 
-// Row source of the fill (extract_rows.cuh): every stored entry is kept; its column is
-// relabelled through the request's qinv.  The per-row handle is the request's index.  A
-// stored column outside [0, ncols) is reported (SP_ERR_INDEX_RANGE) and not written.
+// Phase-1 gather (rowsort.cuh) of the batch: output row r reads its request's matrix at
+// the packed source position; every column is relabelled through the request's qinv
+// (identity without one).  Under a column map a column outside [0, ncols) becomes the
+// key 0xFFFFFFFF, which the sort reports as SP_ERR_INDEX_RANGE.
 template <class CIt, class VTt, class IX>
-struct XPermBatchSrc {
+struct PermBatchGs {
   using CI = CIt;
   using VT = VTt;
-  static constexpr bool kLongCta = false;  // a warp takes every row, however long
-  struct H {
-    int k;
-  };
-  const int* rreq;
   const PermView* pv;
-  DevStatus* st;
-  __device__ __forceinline__ H handle(long long r) const { return H{rreq[r]}; }
-  __device__ static __forceinline__ H shfl(const H& h, int k) { return H{__shfl_sync(kFull, h.k, k)}; }
-  __device__ __forceinline__ const CI* cols(const H& h) const { return static_cast<const CI*>(pv[h.k].col); }
-  __device__ __forceinline__ const VT* vals(const H& h) const { return static_cast<const VT*>(pv[h.k].val); }
-  __device__ __forceinline__ bool map(const H& h, long long c, uint32_t& key) const {
-    const PermView& v = pv[h.k];
-    if (c < 0 || c >= v.ncol) {
-      dev_fail(st, SP_ERR_INDEX_RANGE, c);
-      return false;
-    }
-    key = v.qinv ? uint32_t((long long)ld_map(static_cast<const IX*>(v.qinv) + c)) : uint32_t(c);
-    return true;
+  const long long* rsrc;
+  __device__ long long src(long long r) const { return rsrc[r]; }
+  __device__ CI col(long long pos) const {
+    const CI* c = reinterpret_cast<const CI*>(__ldg(&pv[pos >> kReqShift].col));
+    return ld_stream(c + (pos & kEntryMask));
+  }
+  __device__ VT val(long long pos) const {
+    const VT* v = reinterpret_cast<const VT*>(__ldg(&pv[pos >> kReqShift].val));
+    return ld_stream(v + (pos & kEntryMask));
+  }
+  __device__ CI map(long long pos, CI c) const {
+    const PermView* v = pv + (pos >> kReqShift);
+    const IX* qinv = reinterpret_cast<const IX*>(__ldg(&v->qinv));
+    if (!qinv) return c;
+    const long long cl = (long long)c;
+    if (cl < 0 || cl >= __ldg(&v->ncol)) return CI(-1);
+    return CI(ld_map(qinv + cl));
   }
 };
 
@@ -163,10 +167,9 @@ struct sp_pbatch {
   char* buf = nullptr;  // device: tables, maps, row table, row pointer, scan and sort workspace
   size_t buf_bytes = 0;
   cudaStream_t stream = nullptr;
-  size_t o_req = 0, o_view = 0, o_mat = 0, o_qinv = 0, o_bits = 0, o_rs0 = 0, o_rsn = 0, o_rreq = 0, o_vp = 0,
+  size_t o_req = 0, o_view = 0, o_mat = 0, o_qinv = 0, o_bits = 0, o_rsrc = 0, o_rsn = 0, o_vp = 0,
          o_scan = 0;
   size_t ro[sp::kRowsSlots] = {};
-  long long fin_extra = 0;  // rows the fill may queue (more than XFAST entries)
 };
 
 namespace sp {
@@ -181,11 +184,9 @@ sp_status pbatch_fill_impl(sp_ctx* ctx, sp_pbatch* b, sp_csr* out, cudaStream_t 
   sp_csr* mats = cv.at<sp_csr>(b->o_mat);
   IX* qinv = cv.at<IX>(b->o_qinv);
   uint32_t* pbits = cv.at<uint32_t>(b->o_bits);
-  long long* rs0 = cv.at<long long>(b->o_rs0);
+  long long* rsrc = cv.at<long long>(b->o_rsrc);
   long long* rsn = cv.at<long long>(b->o_rsn);
-  int* rreq = cv.at<int>(b->o_rreq);
   long long* vp = cv.at<long long>(b->o_vp);
-  const int nsm = ctx->num_sms;
   const unsigned gq = unsigned(nreq < 65535 ? nreq : 65535);
   if (b->qtot > 0) SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(b->qtot) * sizeof(IX), s));
   if (b->btot > 0) SP_CUDA(cudaMemsetAsync(pbits, 0, size_t(b->btot) * 4, s));
@@ -197,7 +198,7 @@ sp_status pbatch_fill_impl(sp_ctx* ctx, sp_pbatch* b, sp_csr* out, cudaStream_t 
     SP_CUDA(cudaGetLastError());
     {
       SP_PHASE(SP_PHASE_COUNT);
-      k_pbatch_rowinfo<RP, IX><<<gq, 256, 0, s>>>(reqs, mats, nreq, rs0, rsn, rreq);
+      k_pbatch_rowinfo<RP, IX><<<gq, 256, 0, s>>>(reqs, mats, nreq, rsrc, rsn);
     }
     SP_CUDA(cudaGetLastError());
   }
@@ -214,18 +215,11 @@ sp_status pbatch_fill_impl(sp_ctx* ctx, sp_pbatch* b, sp_csr* out, cudaStream_t 
   if (nnz == 0 || rows == 0) return SP_OK;
   CI* oc = static_cast<CI*>(out->colidx);
   VT* ov = static_cast<VT*>(out->values);
-  const RowsWs w = rows_bind(cv, rows, nnz, b->ro, true, b->fin_extra);
-  SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
+  // phase 1: gather + relabel over the whole batch; phase 2 (any column map): row sort
+  const RowsWs w = rows_bind(cv, rows, nnz, b->ro);
   const int kb = ceil_log2_u64(uint64_t(b->max_cols > 1 ? b->max_cols : 1));
-  {
-    SP_PHASE(SP_PHASE_GATHER);
-    const XPermBatchSrc<CI, VT, IX> src{rreq, views, ctx->dstatus};
-    k_xfill<XPermBatchSrc<CI, VT, IX>, false><<<grid_for((rows + 31) / 32 * 32, XB, nsm * 8), XB, 0, s>>>(
-        src, rows, rs0, rsn, vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.counters + 1, w.huge_cap, kb,
-        ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
-  return sort_queued<CI, VT>(ctx, s, w, kb, oc, ov);
+  const PermBatchGs<CI, VT, IX> g{views, rsrc};
+  return run_rows(ctx, s, vp, rows, nnz, kb, w, &g, b->qtot > 0, oc, ov);
 }
 
 }  // namespace sp
@@ -240,13 +234,14 @@ extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int6
   if (idx_type != SP_I32 && idx_type != SP_I64) return SP_ERR_INVALID_ARG;
   *plan = nullptr;
   if (nmats == 0 && nreq > 0) return SP_ERR_INVALID_ARG;
-  if (nreq > INT32_MAX) return SP_ERR_OVERFLOW;  // a row's request is an int
+  if (nreq > kMaxReqs) return SP_ERR_OVERFLOW;  // packed source positions
   for (int64_t t = 0; t < nmats; ++t) {
     SP_TRY(check_csr(&mats[t]));
     if (mats[t].rowptr_type != mats[0].rowptr_type || mats[t].colidx_type != mats[0].colidx_type ||
         mats[t].value_type != mats[0].value_type)
       return SP_ERR_INVALID_ARG;  // one type combination per batch
     if (mats[t].ncols > (int64_t(1) << 32)) return SP_ERR_OVERFLOW;  // 32-bit sort keys
+    if (mats[t].nnz > kEntryMask) return SP_ERR_OVERFLOW;           // packed source positions
     if (idx_type == SP_I32 && (mats[t].nrows > INT32_MAX || mats[t].ncols > INT32_MAX)) return SP_ERR_OVERFLOW;
   }
   sp_pbatch* b = new sp_pbatch();
@@ -275,7 +270,6 @@ extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int6
     if (q.q) b->qtot += a.ncols;
     if (q.p) b->btot += (a.nrows + 31) / 32;
     if (a.ncols > b->max_cols) b->max_cols = a.ncols;
-    b->fin_extra += a.nnz / (XFAST + 1) + 1;  // rows of more than XFAST entries
   }
   b->roff[size_t(nreq)] = b->rows;
   const size_t is = itype_size(idx_type), vs = nmats > 0 ? vtype_size(b->value_type) : 4;
@@ -285,12 +279,11 @@ extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int6
   b->o_mat = cv.reserve(size_t(nmats) * sizeof(sp_csr));
   b->o_qinv = cv.reserve(size_t(b->qtot) * is);
   b->o_bits = cv.reserve(size_t(b->btot) * 4);
-  b->o_rs0 = cv.reserve(size_t(b->rows) * 8);
+  b->o_rsrc = cv.reserve(size_t(b->rows) * 8);
   b->o_rsn = cv.reserve(size_t(b->rows) * 8);
-  b->o_rreq = cv.reserve(size_t(b->rows) * 4);
   b->o_vp = cv.reserve(size_t(b->rows + 1) * 8);
   b->o_scan = cv.reserve(scan_ws_bytes(b->rows));
-  rows_reserve(cv, b->rows, b->nnz, vs, b->ro, true, b->fin_extra);
+  rows_reserve(cv, b->rows, b->nnz, vs, b->ro);
   cudaStream_t s = (cudaStream_t)stream;
   b->stream = s;
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
@@ -311,7 +304,8 @@ extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int6
     for (int64_t k = 0; k < nreq; ++k) {
       const PermReq& r = b->hreq[size_t(k)];
       const sp_csr& a = mats[r.mat];
-      b->hview[size_t(k)] = PermView{a.colidx, a.values, r.q ? qbase + size_t(r.qoff) * is : nullptr, a.ncols};
+      b->hview[size_t(k)] = PermView{(unsigned long long)a.colidx, (unsigned long long)a.values,
+                                     r.q ? (unsigned long long)(qbase + size_t(r.qoff) * is) : 0ull, a.ncols};
     }
   }
   sp_status st = SP_OK;

@@ -49,7 +49,7 @@ struct PermGs {
   __device__ long long src(long long r) const { return sstart[r]; }
   __device__ CI col(long long pos) const { return ld_stream(c_ + pos); }
   __device__ VT val(long long pos) const { return ld_stream(v_ + pos); }
-  __device__ CI map(CI c) const {
+  __device__ CI map(long long, CI c) const {
     if (!qinv) return c;
     const long long cl = (long long)c;
     if (cl < 0 || cl >= n) return CI(-1);

@@ -208,7 +208,7 @@ __device__ void smem_incl_max_w(uint32_t* a, int n, uint32_t* tmp) {
 // Gs: using CI, VT;
 //     __device__ long long src(long long r) const;     // source start of output row r
 //     __device__ typename Gs::CI col(long long pos) const;  // source column
-//     __device__ typename Gs::CI map(typename Gs::CI c) const;  // new column
+//     __device__ typename Gs::CI map(long long pos, typename Gs::CI c) const;  // new column
 //     __device__ typename Gs::VT val(long long pos) const;
 template <class Gs>
 __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
         if (ok[u]) v[u] = gs.val(pos[u]);
 #pragma unroll
       for (int u = 0; u < H; ++u)
-        if (ok[u]) cv[u] = gs.map(cv[u]);
+        if (ok[u]) cv[u] = gs.map(pos[u], cv[u]);
 #pragma unroll
       for (int u = 0; u < H; ++u) {
         if (!ok[u]) continue;
@@ -1048,7 +1048,7 @@ struct NoGather {
   using VT = VTt;
   __device__ long long src(long long) const { return 0; }
   __device__ CI col(long long) const { return CI(0); }
-  __device__ CI map(CI c) const { return c; }
+  __device__ CI map(long long, CI c) const { return c; }
   __device__ VT val(long long) const { return VT(0); }
 };
 

@@ -26,11 +26,11 @@ def ctx():
 
 
 def _long_rows(value_dtype=np.float32, seed=5):
-    """Rows of 0, 1, 64, 65 (either side of the warp path), 4096, 4097 (either side of
-    the run limit) and 12000 entries, then short rows."""
+    """Rows of 0, 1, 512, 513, 1024, 1025 (either side of the tile limits), 4096, 4097
+    (either side of the run limit) and 12000 entries, then short rows."""
     rng = np.random.default_rng(seed)
     n = 20000
-    lens = [0, 1, 64, 65, 4096, 4097, 12000] + list(rng.integers(0, 40, 200))
+    lens = [0, 1, 512, 513, 1024, 1025, 4096, 4097, 12000] + list(rng.integers(0, 40, 200))
     r = np.concatenate([np.full(L, i, np.int64) for i, L in enumerate(lens)])
     c = np.concatenate([np.sort(rng.choice(n, L, replace=False)) for L in lens]).astype(np.int64)
     v = rng.random(r.shape[0]).astype(value_dtype)
