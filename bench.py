@@ -60,8 +60,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=25, help="R-MAT scale of the headline workload")
     ap.add_argument("--no-extra", action="store_true", help="skip the extraction/assignment ops")
-    ap.add_argument("--ops", default="extract,assign,batch,serve",
-                    help="comma list of the extra sections to run (extract, assign, batch, serve)")
+    ap.add_argument("--ops", default="extract,assign,batch,pbatch,serve",
+                    help="comma list of the extra sections to run (extract, assign, batch, pbatch, serve)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--lookup-sweep", action="store_true",
@@ -349,6 +349,10 @@ def log_summary(res):
     if "batched_ms" in bt:
         log(f"SUMMARY batch: {bt['batched_ms']} ms batched vs {bt['plain_ms']} ms plain | graph fill "
             f"{bt['graph_fill_ms']} ms | {bt['batched_value'] / 1e9:.2f} G entries/s")
+    pb = ops.get("batch_permute", {})
+    if "batched_ms" in pb:
+        log(f"SUMMARY batch permute: {pb['batched_ms']} ms batched vs {pb['plain_ms']} ms plain | graph "
+            f"{pb['graph_ms']} ms | {pb['graph_value'] / 1e9:.2f} G entries/s")
     sv = ops.get("serve", {})
     for k, v in sv.items():
         if k.startswith("load_"):
@@ -436,6 +440,7 @@ def run_ours(args, ws, rank, local):
         sections = (("extract", "extract", lambda: bench_extract(ctx, args, dev, hbm, ws)),
                     ("assign", "assign", lambda: bench_assign(ctx, args, dev, hbm, ws)),
                     ("batch", "batch_extract", lambda: bench_batch(ctx, args, dev, ws)),
+                    ("pbatch", "batch_permute", lambda: bench_pbatch(ctx, args, dev, ws)),
                     ("serve", "serve", lambda: bench_serve(ctx, args, dev)))
         for name, key, fn in sections:
             if name not in want:
@@ -843,6 +848,75 @@ def bench_batch_tuned(ctx, dms, reqs, nnz, steps, ws):
             "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1)}
 
 
+def bench_pbatch(ctx, args, dev, ws, nreq=2000, max_rows=1 << 16, seed=6):
+    """Batched permutations: `nreq` symmetric reorderings P A P^T over the batching
+    workload's matrices of at most `max_rows` rows (the latency-bound end of the serving
+    mix), one host-only plan and one fill for the batch, against one call per request.
+    A sample of the requests' slices of the batch is compared with their own calls."""
+    import time
+    import torch
+    import synth
+    from paper_2509_20776_gb300 import CSR
+    mats, _ = batch_workload(dev, nreq=0)
+    small = [t for t, m in enumerate(mats) if m.nrows <= max_rows]
+    dms = [CSR(m.nrows, m.ncols, m.rowptr, m.colidx, m.values) for m in mats]
+    perms = {t: synth.random_permutation(mats[t].nrows, 9, t, device=dev) for t in small}
+    g = torch.Generator().manual_seed(seed)
+    reqs = []
+    for _ in range(nreq):
+        t = small[int(torch.randint(0, len(small), (1,), generator=g))]
+        reqs.append((t, perms[t], perms[t]))
+    bt = ctx.permute_batch(dms, reqs)
+    out = bt.alloc(torch.int64)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bt.fill(out, s)
+    torch.cuda.current_stream().wait_stream(s)
+    ctx.sync()
+    offs = bt.row_offsets()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bt.fill(out, torch.cuda.current_stream())
+    nnz = bt.nnz
+    steps = max(3, args.steps)
+    ms_graph = time_steps(graph.replay, steps, 2, ws) / steps
+    ctx.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        b2 = ctx.permute_batch(dms, reqs)
+        o2 = b2.alloc(torch.int64)
+        b2.fill(o2)
+        ctx.sync()
+        b2.close()
+    ms_batch = (time.perf_counter() - t0) * 1e3 / 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t, p, q in reqs:
+        ctx.sp_permute(dms[t], p, q, sync=False)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ms_plain = (time.perf_counter() - t0) * 1e3
+    same = True
+    for k in range(0, nreq, max(1, nreq // 50)):
+        t, p, q = reqs[k]
+        alone = ctx.sp_permute(dms[t], p, q)
+        a, b = int(out.rowptr[offs[k]]), int(out.rowptr[offs[k + 1]])
+        same &= bool(torch.equal(alone.colidx, out.colidx[a:b]) and
+                     torch.equal(alone.values.view(torch.int32), out.values[a:b].view(torch.int32)) and
+                     torch.equal(alone.rowptr.to(torch.int64), out.rowptr[offs[k]:offs[k + 1] + 1] - a))
+    bt.close()
+    return {"workload": f"{nreq} P A P^T over the {len(small)} batching-workload matrices of at most "
+                        f"{max_rows} rows ({nnz} entries in all)",
+            "nnz_out": nnz, "same_as_plain_sampled": same,
+            "batched_ms": round(ms_batch, 3), "batched_value": round(nnz / (ms_batch * 1e-3), 1),
+            "graph_ms": round(ms_graph, 3), "graph_value": round(nnz / (ms_graph * 1e-3), 1),
+            "plain_ms": round(ms_plain, 3), "plain_value": round(nnz / (ms_plain * 1e-3), 1),
+            "unit": UNIT, "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2),
+            "speedup_graph_vs_plain": round(ms_plain / ms_graph, 2)}
+
+
 def bench_serve(ctx, args, dev, nreq=100000, nreq_overload=10000):
     """Poisson stream of mixed requests (60 % P A P^T, 30 % extraction, 10 % assignment)
     over the batching workload's 64 matrices: `nreq` requests at 0.8 x the plain path's
@@ -891,6 +965,7 @@ def bench_serve(ctx, args, dev, nreq=100000, nreq_overload=10000):
         gaps = torch.empty(nreq, dtype=torch.float64).exponential_(rate, generator=g)
         arrivals = torch.cumsum(gaps, 0).tolist()
         plain = run_plain(ctx, dms, make(arrivals)[:nr])
+        srv.stats = {k: 0 for k in srv.stats}
         served = srv.run(make(arrivals)[:nr])
         nnz_p = sum(r.nnz_out for r in plain)
         nnz_s = sum(r.nnz_out for r in served)
@@ -898,7 +973,7 @@ def bench_serve(ctx, args, dev, nreq=100000, nreq_overload=10000):
         res[f"load_{load}x"] = {"rate_per_s": round(rate, 1), "requests": nr,
                                 "plain": {**sp, "value": round(nnz_p / sp["span_s"], 1)},
                                 "served": {**ss, "value": round(nnz_s / ss["span_s"], 1)},
-                                "same_nnz": nnz_p == nnz_s}
+                                "same_nnz": nnz_p == nnz_s, "server_stats": dict(srv.stats)}
     srv.close()
     return res
 

@@ -331,8 +331,9 @@ SP_API sp_status sp_batch_destroy(sp_ctx* ctx, sp_batch* batch);
  *   (a permutation keeps every entry, so the output size is known: *nnz_total = the
  *   sum of the matrices' nnz over the requests) and allocates one device buffer
  *   (inverse column maps, row bitmaps, the row table, the row pointer, the row-sort
- *   workspace), whose request tables it copies on `stream`: a fill on another stream
- *   must be ordered after it.  *plan borrows the matrices and p_k, q_k until
+ *   workspace), whose request tables it writes on `stream` by small kernel launches
+ *   (no copy from pageable memory, which would wait for the stream's earlier work): a
+ *   fill on another stream must be ordered after it.  *plan borrows the matrices and p_k, q_k until
  *   destroyed; the fill reads p_k and q_k when it runs, so a replayed graph picks up
  *   new permutations written into the same buffers.
  * sp_permute_batch_fill: runs the whole batch on `stream` (per request the inverse

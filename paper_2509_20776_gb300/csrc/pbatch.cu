@@ -12,6 +12,7 @@
 //   two-phase path of the single permutation over the whole batch: partition of the
 //   output rows, load-balanced chunk gather with the relabelling through each row's
 //   request, in-place row sort.
+#include <cstring>
 #include <vector>
 
 #include "dispatch.h"
@@ -40,6 +41,37 @@ struct PermView {
 constexpr int kReqShift = 40;  // source position = request * 2^40 + entry of its matrix
 constexpr long long kEntryMask = (1ll << kReqShift) - 1;
 constexpr long long kMaxReqs = 1ll << 23;
+
+// Host tables reach the device as kernel parameters (up to 32 KB per launch, copied at
+// launch): a copy from pageable host memory would first wait for the stream's earlier
+// work, and the plan must not wait for the device.
+constexpr int kUpBytes = 32704;  // payload per launch (parameter space 32764 bytes)
+struct UpChunk {
+  char* dst;  // 16-byte aligned
+  int n;
+  alignas(16) unsigned char b[kUpBytes];
+};
+__global__ void k_upload(const __grid_constant__ UpChunk c) {
+  const int nw = c.n >> 4;
+  const uint4* src = reinterpret_cast<const uint4*>(c.b);
+  uint4* dst = reinterpret_cast<uint4*>(c.dst);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+  for (int i = (nw << 4) + threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = char(c.b[i]);
+}
+
+inline sp_status upload(char* dst, const void* src, size_t bytes, cudaStream_t s) {
+  static thread_local UpChunk c;
+  const char* h = static_cast<const char*>(src);
+  for (size_t o = 0; o < bytes; o += kUpBytes) {
+    const size_t n = bytes - o < size_t(kUpBytes) ? bytes - o : size_t(kUpBytes);
+    c.dst = dst + o;
+    c.n = int(n);
+    memcpy(c.b, h + o, n);
+    k_upload<<<1, 256, 0, s>>>(c);
+    SP_CUDA(cudaGetLastError());
+  }
+  return SP_OK;
+}
 
 // per request: qinv[q[j]] = j (a repeat or an index out of range is not a permutation)
 // and the bitmap of p
@@ -308,14 +340,9 @@ extern "C" sp_status sp_permute_batch_plan(sp_ctx* ctx, const sp_csr* mats, int6
                                      r.q ? (unsigned long long)(qbase + size_t(r.qoff) * is) : 0ull, a.ncols};
     }
   }
-  sp_status st = SP_OK;
-  auto copy = [&](size_t off, const void* src, size_t bytes) {
-    if (st == SP_OK && bytes && cudaMemcpyAsync(cv.at<char>(off), src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      st = SP_ERR_CUDA;
-  };
-  copy(b->o_req, b->hreq.data(), size_t(nreq) * sizeof(PermReq));
-  copy(b->o_view, b->hview.data(), size_t(nreq) * sizeof(PermView));
-  copy(b->o_mat, b->hmats.data(), size_t(nmats) * sizeof(sp_csr));
+  sp_status st = upload(cv.at<char>(b->o_req), b->hreq.data(), size_t(nreq) * sizeof(PermReq), s);
+  if (st == SP_OK) st = upload(cv.at<char>(b->o_view), b->hview.data(), size_t(nreq) * sizeof(PermView), s);
+  if (st == SP_OK) st = upload(cv.at<char>(b->o_mat), b->hmats.data(), size_t(nmats) * sizeof(sp_csr), s);
   if (st != SP_OK) {
     sp_pbatch_destroy(ctx, b);
     return st;

@@ -10,8 +10,13 @@ time.  Every scheduling round the server
     whole round) and admits the batch by the exact output bytes that count returns: a
     batch that does not fit is held, counted but not filled, until retiring work frees
     enough memory (later extractions wait behind it, in order);
-  * fills admitted batches and issues the permutations and assignments round-robin on
-    several stream slots, each with its own library context, so their work overlaps.
+  * runs the round's permutations of small matrices (at most ``perm_batch_nnz``
+    entries) as one batch (``PermuteBatch``: a host-only plan and one fill for all of
+    them); larger ones, whose launches are amortised already, and a lone small one are
+    plain calls, so a small request never waits for a large one in its batch;
+  * fills admitted batches and issues the permutation batches, permutations and
+    assignments round-robin on several stream slots, each with its own library
+    context, so their work overlaps.
 Requests that arrive while others are on the GPU join the next round: slots and memory
 free up as earlier work retires.  ``run_plain`` serves the same stream one synchronous
 call per request, for comparison.  Every kernel is the library's; this module only
@@ -24,7 +29,7 @@ from dataclasses import dataclass, field
 
 import torch
 
-from ._binding import CSR, Context, ExtractBatch
+from ._binding import CSR, Context, ExtractBatch, PermuteBatch
 
 
 @dataclass
@@ -51,6 +56,7 @@ class Server:
     slots: int = 4
     mem_budget: int = 16 << 30      # bytes of outputs in flight
     max_batch: int = 4096           # extractions per round
+    perm_batch_nnz: int = 1 << 20   # permutations of matrices up to this size are batched
     keep_results: bool = False
     device: int = 0
     _ctx: list = field(default_factory=list)
@@ -60,7 +66,7 @@ class Server:
     def __post_init__(self):
         self._ctx = [Context(self.device) for _ in range(self.slots)]
         self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
-        self.stats = {"rounds": 0, "batches": 0, "held_rounds": 0, "peak_used": 0}
+        self.stats = {"rounds": 0, "batches": 0, "perm_batches": 0, "held_rounds": 0, "peak_used": 0}
 
     def close(self):
         for c in self._ctx:
@@ -121,6 +127,27 @@ class Server:
                 other.append(r)
                 used += b
                 i += 1
+            small = [r for r in other if r.kind == "permute" and self.mats[r.mat].nnz <= self.perm_batch_nnz]
+            if len(small) > 1:  # the round's small permutations as one batch
+                k = turn % self.slots
+                turn += 1
+                ctx, st = self._ctx[k], self._streams[k]
+                with torch.cuda.stream(st):
+                    pb = PermuteBatch(ctx, self.mats, [(r.mat, r.p, r.p) for r in small], stream=st)
+                    out = pb.alloc()
+                    pb.fill(out, st)
+                    offs = pb.row_offsets()
+                    pb.close()  # stream-ordered after the fill
+                    for j, r in enumerate(small):
+                        r.nnz_out = self.mats[r.mat].nnz
+                        if self.keep_results:
+                            r.result = (out, offs[j], offs[j + 1])
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                inflight.append((small, ev, sum(self._bound(r) for r in small), out))
+                self.stats["perm_batches"] += 1
+                batched = set(map(id, small))
+                other = [r for r in other if id(r) not in batched]
             for r in other:
                 k = turn % self.slots
                 turn += 1

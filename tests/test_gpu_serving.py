@@ -42,6 +42,23 @@ def _stream(mats, n, seed, rate):
     return reqs
 
 
+def _check_part(result, ref, what):
+    """A result that is a slice of a batch's CSR: (out, first row, end row)."""
+    out, r0, r1 = result
+    base, end = int(out.rowptr[r0]), int(out.rowptr[r1])
+    rp = (out.rowptr[r0:r1 + 1] - base).cpu().numpy().astype(np.int64)
+    assert np.array_equal(rp, ref.rowptr), f"{what} rowptr"
+    assert np.array_equal(out.colidx[base:end].cpu().numpy().astype(np.int64), ref.colidx), f"{what} colidx"
+    assert np.array_equal(bits(out.values[base:end].cpu().numpy()), bits(ref.values)), f"{what} values"
+
+
+def _check_result(result, ref, what):
+    if isinstance(result, tuple):
+        _check_part(result, ref, what)
+    else:
+        assert_same(result, ref, what)
+
+
 def test_served_equals_plain():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -69,20 +86,9 @@ def test_served_equals_plain():
             ref = oracle.extract(A, a.I.cpu().numpy(), a.J.cpu().numpy())
         else:
             ref = oracle.assign(A, a.I.cpu().numpy(), a.J.cpu().numpy(), to_oracle(a.B))
-        if a.kind == "extract":
-            out, r0, r1 = a.result
-            base, end = int(out.rowptr[r0]), int(out.rowptr[r1])
-            rp = (out.rowptr[r0:r1 + 1] - base).cpu().numpy().astype(np.int64)
-            assert np.array_equal(rp, ref.rowptr), f"request {k}: served extraction rowptr"
-            assert np.array_equal(out.colidx[base:end].cpu().numpy().astype(np.int64), ref.colidx), \
-                f"request {k}: served extraction colidx"
-            assert np.array_equal(bits(out.values[base:end].cpu().numpy()), bits(ref.values)), \
-                f"request {k}: served extraction values"
-            assert a.nnz_out == ref.nnz
-            assert_same(want, ref, f"request {k}: plain extraction")
-        else:
-            assert_same(a.result, ref, f"request {k}: served {a.kind}")
-            assert_same(want, ref, f"request {k}: plain {a.kind}")
+        _check_result(a.result, ref, f"request {k}: served {a.kind}")
+        assert a.nnz_out == ref.nnz
+        assert_same(want, ref, f"request {k}: plain {a.kind}")
     st = latency_stats(reqs_a)
     assert st["p99_ms"] >= st["p50_ms"] >= 0
     srv.close()
@@ -107,15 +113,43 @@ def test_extractions_held_by_memory():
     for k, r in enumerate(reqs):
         A = hosts[r.mat]
         if r.kind == "permute":
-            assert_same(r.result, oracle.permute(A, r.p.cpu().numpy(), r.p.cpu().numpy()), f"request {k}")
+            ref = oracle.permute(A, r.p.cpu().numpy(), r.p.cpu().numpy())
         elif r.kind == "assign":
-            assert_same(r.result, oracle.assign(A, r.I.cpu().numpy(), r.J.cpu().numpy(), to_oracle(r.B)),
-                        f"request {k}")
+            ref = oracle.assign(A, r.I.cpu().numpy(), r.J.cpu().numpy(), to_oracle(r.B))
         else:
             ref = oracle.extract(A, r.I.cpu().numpy(), r.J.cpu().numpy())
-            out, r0, r1 = r.result
-            base, end = int(out.rowptr[r0]), int(out.rowptr[r1])
-            assert np.array_equal((out.rowptr[r0:r1 + 1] - base).cpu().numpy().astype(np.int64), ref.rowptr)
-            assert np.array_equal(out.colidx[base:end].cpu().numpy().astype(np.int64), ref.colidx)
-            assert np.array_equal(bits(out.values[base:end].cpu().numpy()), bits(ref.values))
+        _check_result(r.result, ref, f"request {k}")
+    srv.close()
+
+
+def test_permutations_batched_per_round():
+    """Everything arrives at once under a large budget: the first round's permutations of
+    the small matrices run as one batch, the largest matrix's alone, and every result
+    (a slice of the batch's CSR, or a CSR of its own) equals the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_20776_gb300 import build
+    build.build()
+    from paper_2509_20776_gb300.serving import Server
+    mats = [to_dev(synth.rmat_csr(s, 6, seed=s + 2, symmetrize=True, value_kind="f32u01",
+                                  rowptr_dtype=torch.int64, colidx_dtype=torch.int32)) for s in (8, 10, 12)]
+    reqs = _stream(mats, 90, 7, 1e9)
+    srv = Server(mats, slots=2, keep_results=True, perm_batch_nnz=mats[1].nnz)
+    srv.run(reqs)
+    assert srv.stats["perm_batches"] >= 1
+    hosts = [to_oracle(m) for m in mats]
+    batched = alone = 0
+    for k, r in enumerate(reqs):
+        A = hosts[r.mat]
+        if r.kind == "permute":
+            ref = oracle.permute(A, r.p.cpu().numpy(), r.p.cpu().numpy())
+            batched += isinstance(r.result, tuple)
+            alone += r.mat == 2 and not isinstance(r.result, tuple)
+        elif r.kind == "assign":
+            ref = oracle.assign(A, r.I.cpu().numpy(), r.J.cpu().numpy(), to_oracle(r.B))
+        else:
+            ref = oracle.extract(A, r.I.cpu().numpy(), r.J.cpu().numpy())
+        _check_result(r.result, ref, f"request {k}: {r.kind}")
+        assert r.nnz_out == ref.nnz
+    assert batched > 1 and alone > 0
     srv.close()
