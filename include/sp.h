@@ -122,6 +122,11 @@ SP_API sp_status sp_ctx_sync(sp_ctx* ctx, sp_stream_t stream);
  * the offending position in the index vector; -1 if none). */
 SP_API int64_t sp_ctx_error_detail(const sp_ctx* ctx);
 
+/* Host: the CUDA runtime error code behind the calling thread's most recent
+ * SP_ERR_CUDA (0 if there was none), and in *where (may be NULL) a static string
+ * naming the library source line and the error ("file.cu:123 (cudaErrorXxx)"). */
+SP_API int sp_last_cuda_error(const char** where);
+
 /* Tuning and test knobs (values < 0 restore the default):
  *   SP_OPT_SPIN_LIMIT      polls a look-back wait makes before it gives up with
  *                          SP_ERR_TIMEOUT (default 1<<22, each poll sleeps ~100 ns);

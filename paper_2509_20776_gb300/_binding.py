@@ -133,6 +133,7 @@ SIGNATURES = {
     "sp_ctx_destroy": (_int, [_vp]),
     "sp_ctx_sync": (_int, [_vp, _vp]),
     "sp_ctx_error_detail": (_i64, [_vp]),
+    "sp_last_cuda_error": (_int, [ctypes.POINTER(ctypes.c_char_p)]),
     "sp_ctx_set_option": (_int, [_vp, _int, _i64]),
     "sp_ctx_set_tuning": (_int, [_vp, ctypes.POINTER(sp_tune_entry), _int]),
     "sp_tuning_lookup": (_int, [ctypes.POINTER(sp_tune_entry), _int, _int, _i64, ctypes.POINTER(sp_tune_entry)]),
@@ -272,6 +273,10 @@ class Context:
     def _check(self, code: int, where: str):
         if code != 0:
             detail = self.lib.sp_ctx_error_detail(self.handle) if getattr(self, "handle", None) else -1
+            if code == STATUS.index("SP_ERR_CUDA"):  # name the CUDA error and the library line behind it
+                w = ctypes.c_char_p()
+                self.lib.sp_last_cuda_error(ctypes.byref(w))
+                where = f"{where} [{(w.value or b'').decode()}]"
             raise SpError(code, where, detail)
 
     def close(self):

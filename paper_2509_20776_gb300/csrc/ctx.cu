@@ -1,5 +1,6 @@
 // Context lifecycle, allocator hook, workspace arena and device error reporting.
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <new>
 
@@ -93,6 +94,18 @@ sp_status check_csr(const sp_csr* A, bool allow_null_arrays) {
 
 }  // namespace sp
 
+namespace sp {
+namespace {
+thread_local int t_cuda_err = 0;
+thread_local char t_cuda_where[160] = "";
+}  // namespace
+void note_cuda_error(cudaError_t e, const char* file, int line) {
+  t_cuda_err = int(e);
+  const char* base = strrchr(file, '/');
+  snprintf(t_cuda_where, sizeof(t_cuda_where), "%s:%d (%s)", base ? base + 1 : file, line, cudaGetErrorName(e));
+}
+}  // namespace sp
+
 extern "C" {
 
 const char* sp_status_str(sp_status s) {
@@ -173,6 +186,12 @@ sp_status sp_ctx_sync(sp_ctx* ctx, sp_stream_t stream) {
 }
 
 int64_t sp_ctx_error_detail(const sp_ctx* ctx) { return ctx ? ctx->last_detail : -1; }
+
+
+int sp_last_cuda_error(const char** where) {
+  if (where) *where = sp::t_cuda_where;
+  return sp::t_cuda_err;
+}
 
 sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
   if (!ctx) return SP_ERR_INVALID_ARG;

@@ -54,10 +54,16 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 inline size_t itype_size(sp_itype t) { return t == SP_I64 ? 8 : 4; }
 inline size_t vtype_size(sp_vtype t) { return t == SP_F64 ? 8 : 4; }
 
+// The CUDA error behind the calling thread's most recent SP_ERR_CUDA, and where.
+void note_cuda_error(cudaError_t e, const char* file, int line);
+
 #define SP_CUDA(call)                                     \
   do {                                                    \
     cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return SP_ERR_CUDA;            \
+    if (e_ != cudaSuccess) {                              \
+      ::sp::note_cuda_error(e_, __FILE__, __LINE__);      \
+      return SP_ERR_CUDA;                                 \
+    }                                                     \
   } while (0)
 
 #define SP_TRY(call)                                      \

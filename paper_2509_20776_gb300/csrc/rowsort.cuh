@@ -1058,8 +1058,8 @@ sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col
   const int nsm = ctx->num_sms;
   VT* tval = static_cast<VT*>(w.tval);
   constexpr size_t csm = split_smem_bytes<SplitCoarse, VT>(), fsm = split_smem_bytes<SplitFine, VT>();
-  static bool once_h = (set_smem(k_split<SplitCoarse, CI, VT>, csm), set_smem(k_split<SplitFine, CI, VT>, fsm), true);
-  (void)once_h;
+  SP_CUDA(set_smem(k_split<SplitCoarse, CI, VT>, csm));
+  SP_CUDA(set_smem(k_split<SplitFine, CI, VT>, fsm));
   {
     SP_PHASE(SP_PHASE_HUGE);
     k_split<SplitCoarse, CI, VT><<<SplitCoarse::MINB * nsm, SplitCoarse::B, csm, s>>>(
@@ -1089,8 +1089,7 @@ sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, 
   const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   using SsRun = SsRunT<VT>;
   constexpr size_t rsm = ss_smem_bytes<SsRun, VT>();
-  static bool once_r = (set_smem(k_seg_sort<SsRun, CI, VT>, rsm), true);
-  (void)once_r;
+  SP_CUDA(set_smem(k_seg_sort<SsRun, CI, VT>, rsm));
   {
     SP_PHASE(SP_PHASE_LONG);
     k_seg_sort<SsRun, CI, VT><<<SsRun::MINB * nsm, SsRun::B, rsm, s>>>(
@@ -1156,8 +1155,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   // tiles, then the runs, then the heavy buckets queued by either
   const unsigned* no_runs = w.counters + 8;
   constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), lsm = ss_smem_bytes<SsTileL, VT>();
-  static bool once_s = (set_smem(k_seg_sort<SsTile, CI, VT>, tsm), set_smem(k_seg_sort<SsTileL, CI, VT>, lsm), true);
-  (void)once_s;
+  SP_CUDA(set_smem(large_tiles ? k_seg_sort<SsTileL, CI, VT> : k_seg_sort<SsTile, CI, VT>, large_tiles ? lsm : tsm));
   VT* tval = static_cast<VT*>(w.tval);
   {
     SP_PHASE(SP_PHASE_TILE);

@@ -175,8 +175,10 @@ sp_status launch_scan(sp_ctx* ctx, cudaStream_t s, Load load, Store store, long 
 }
 
 template <class K>
-inline void set_smem(K kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  // set before every launch that needs it: a flag kept in an inline template is shared by
+  // every translation unit of the library, but each one launches its own copy of a kernel
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
 }  // namespace sp
