@@ -430,15 +430,12 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   }
   SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp}, StoreDual<long long>{b->vp, nullptr, ctx->dstatus},
                      rows, cv.at<char>(o_sc)));
-  long long* h = nullptr;
-  SP_CUDA(cudaMallocHost(&h, 16));
-  cudaMemcpyAsync(h, b->vp + rows, 8, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h + 1, counters + 1, 4, cudaMemcpyDeviceToHost, s);
-  const sp_status st = ctx_collect(ctx, s);
+  long long* h = ctx->hbuf;  // the context's pinned scratch, read back before returning
+  SP_CUDA(cudaMemcpyAsync(h, b->vp + rows, 8, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(h + 1, counters + 1, 4, cudaMemcpyDeviceToHost, s));
+  SP_TRY(ctx_collect(ctx, s));
   b->nnz = h[0];
   b->n_slow = rank ? (long long)*reinterpret_cast<const unsigned*>(h + 1) : 0;
-  cudaFreeHost(h);
-  SP_TRY(st);
   // reserve now the workspace the fill's row sort needs, so the fill allocates nothing
   Carver cf;
   size_t rf[kRowsSlots];

@@ -152,9 +152,11 @@ sp_status sp_ctx_create(sp_ctx** out, int device, const sp_allocator* allocator)
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&ctx->dstatus, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&ctx->hstatus, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&ctx->hbuf, 16 * sizeof(long long)) != cudaSuccess ||
       cudaMemset(ctx->dstatus, 0, sizeof(DevStatus)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->dstatus) cudaFree(ctx->dstatus);
+    if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
     delete ctx;
     return SP_ERR_CUDA;
   }
@@ -170,6 +172,7 @@ sp_status sp_ctx_destroy(sp_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->dstatus);
   cudaFreeHost(ctx->hstatus);
+  cudaFreeHost(ctx->hbuf);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);

@@ -168,10 +168,7 @@ sp_status plan_alloc(sp_ctx* ctx, sp_plan* pl, size_t bytes, cudaStream_t s) {
   pl->buf = static_cast<char*>(ctx_alloc(ctx, bytes, s));
   if (!pl->buf) return SP_ERR_OOM;
   pl->buf_bytes = bytes;
-  if (cudaMallocHost(&pl->h_tail, 64) != cudaSuccess) {
-    cudaGetLastError();
-    return SP_ERR_CUDA;
-  }
+  pl->h_tail = ctx->hbuf;  // every use is read back before the count call returns
   return SP_OK;
 }
 
@@ -465,10 +462,6 @@ sp_status plan_release(sp_ctx* ctx, sp_plan* pl) {
   if (!pl) return SP_OK;
   if (pl->buf) ctx_free(ctx, pl->buf, pl->buf_bytes, pl->stream);
   if (pl->buf2) ctx_free(ctx, pl->buf2, pl->buf2_bytes, pl->stream);
-  if (pl->h_tail) {
-    cudaStreamSynchronize(pl->stream);
-    cudaFreeHost(pl->h_tail);
-  }
   delete pl;
   return SP_OK;
 }

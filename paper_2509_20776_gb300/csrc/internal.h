@@ -23,6 +23,10 @@ struct sp_ctx {
   cudaStream_t ws_stream = nullptr;
   sp::DevStatus* dstatus = nullptr;  // device error record
   sp::DevStatus* hstatus = nullptr;  // pinned host mirror
+  // pinned host scratch for the totals a synchronising call reads back (16 words); one
+  // buffer per context, so no call allocates page-locked memory (which would stop kernels
+  // on other streams from running concurrently with later work)
+  long long* hbuf = nullptr;
   int64_t spin_limit = int64_t(1) << 22;
   int64_t hold_tile = -1;
   int validate = 0;

@@ -48,7 +48,7 @@ struct sp_plan {
   long long n_slow = 0;
   long long list_cap = 0;
   unsigned* counters = nullptr;  // [0] n_cl [3] count ticket [4] rows of more than XFAST entries
-  long long* h_tail = nullptr;   // pinned host: totals read back by the count call
+  long long* h_tail = nullptr;   // the context's pinned scratch: totals read back by the count call
 };
 
 namespace sp {

@@ -224,6 +224,11 @@ def run_plain(ctx: Context, mats: list[CSR], reqs: list[Request], keep_results=F
 def latency_stats(reqs: list[Request]) -> dict:
     lat = torch.tensor([r.done - r.arrival for r in reqs], dtype=torch.float64)
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    by_kind = {}
+    for kind in sorted({r.kind for r in reqs}):
+        lk = torch.tensor([r.done - r.arrival for r in reqs if r.kind == kind], dtype=torch.float64)
+        by_kind[kind] = {"n": int(lk.numel()), "p50_ms": round(float(lk.quantile(0.5)) * 1e3, 3),
+                         "p99_ms": round(float(lk.quantile(0.99)) * 1e3, 3)}
     return {"p50_ms": round(float(lat.quantile(0.5)) * 1e3, 3),
             "p99_ms": round(float(lat.quantile(0.99)) * 1e3, 3),
-            "mean_ms": round(float(lat.mean()) * 1e3, 3), "span_s": round(span, 3)}
+            "mean_ms": round(float(lat.mean()) * 1e3, 3), "span_s": round(span, 3), "by_kind": by_kind}
