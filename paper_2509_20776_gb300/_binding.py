@@ -499,11 +499,17 @@ class Context:
                                              _stream(stream)), "sp_csr_validate")
 
 
+def mat_descs(mats):
+    """The descriptor array of a list of matrices, as the batch calls take it (build it
+    once for matrices that stay registered)."""
+    return (sp_csr * len(mats))(*[m.desc() for m in mats])
+
+
 class ExtractBatch:
     """A counted batch of extractions (``sp_extract_batch_count``): ``fill`` launches the
     whole batch without synchronising (capturable in a CUDA graph)."""
 
-    def __init__(self, ctx: Context, mats, requests, stream=None):
+    def __init__(self, ctx: Context, mats, requests, stream=None, descs=None):
         self.ctx = ctx
         self.mats = list(mats)
         self.requests = list(requests)
@@ -512,7 +518,8 @@ class ExtractBatch:
             raise ValueError("a batch needs at least one matrix")
         dt = self.requests[0][1].dtype if self.requests else torch.int32
         idx_t = _itype(dt)
-        self._descs = (sp_csr * len(self.mats))(*[m.desc() for m in self.mats])
+        # descs: the matrices' descriptor array (mat_descs), reused across batches
+        self._descs = descs if descs is not None else mat_descs(self.mats)
         self._reqs = (sp_extract_req * max(1, len(self.requests)))()
         for k, (mi, I, J) in enumerate(self.requests):
             if I.dtype != dt or J.dtype != dt:
@@ -565,7 +572,7 @@ class PermuteBatch:
     whole batch, its validation included, without synchronising (capturable in a CUDA
     graph)."""
 
-    def __init__(self, ctx: Context, mats, requests, stream=None):
+    def __init__(self, ctx: Context, mats, requests, stream=None, descs=None):
         self.ctx = ctx
         self.mats = list(mats)
         self.requests = list(requests)
@@ -576,7 +583,7 @@ class PermuteBatch:
         if len(dts) > 1:
             raise TypeError("all index tensors of a batch share one dtype")
         idx_t = _itype(dts.pop() if dts else torch.int32)
-        self._descs = (sp_csr * len(self.mats))(*[m.desc() for m in self.mats])
+        self._descs = descs if descs is not None else mat_descs(self.mats)
         self._reqs = (sp_permute_req * max(1, len(self.requests)))()
         for k, (mi, p, q) in enumerate(self.requests):
             a = self.mats[int(mi)] if 0 <= int(mi) < len(self.mats) else None

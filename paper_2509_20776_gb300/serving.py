@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 
 import torch
 
-from ._binding import CSR, Context, ExtractBatch, PermuteBatch
+from ._binding import CSR, Context, ExtractBatch, PermuteBatch, mat_descs
 
 
 @dataclass
@@ -61,11 +61,14 @@ class Server:
     device: int = 0
     _ctx: list = field(default_factory=list)
     _streams: list = field(default_factory=list)
+    _last: list = field(default_factory=list)  # per slot: event of its latest work
     stats: dict = field(default_factory=dict)
 
     def __post_init__(self):
         self._ctx = [Context(self.device) for _ in range(self.slots)]
         self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
+        self._last = [None] * self.slots
+        self._descs = mat_descs(self.mats)  # built once: the batch calls reuse it
         self.stats = {"rounds": 0, "batches": 0, "perm_batches": 0, "held_rounds": 0, "peak_used": 0}
 
     def close(self):
@@ -84,6 +87,15 @@ class Server:
     def _batch_bytes(bt: ExtractBatch) -> int:
         like = bt.mats[0]
         return bt.nnz * (like.colidx.element_size() + like.values.element_size()) + (bt.rows + 1) * 8
+
+    def _slot(self, turn: int) -> int:
+        """An idle slot if there is one (a call that synchronises, such as an extraction
+        count, then waits for nothing else), else the next in turn."""
+        for j in range(self.slots):
+            k = (turn + j) % self.slots
+            if self._last[k] is None or self._last[k].query():
+                return k
+        return turn % self.slots
 
     def run(self, reqs: list[Request]) -> list[Request]:
         """Serve ``reqs`` (sorted by arrival); fills ``done`` / ``nnz_out`` of each."""
@@ -129,11 +141,12 @@ class Server:
                 i += 1
             small = [r for r in other if r.kind == "permute" and self.mats[r.mat].nnz <= self.perm_batch_nnz]
             if len(small) > 1:  # the round's small permutations as one batch
-                k = turn % self.slots
-                turn += 1
+                k = self._slot(turn)
+                turn = k + 1
                 ctx, st = self._ctx[k], self._streams[k]
                 with torch.cuda.stream(st):
-                    pb = PermuteBatch(ctx, self.mats, [(r.mat, r.p, r.p) for r in small], stream=st)
+                    pb = PermuteBatch(ctx, self.mats, [(r.mat, r.p, r.p) for r in small], stream=st,
+                                      descs=self._descs)
                     out = pb.alloc()
                     pb.fill(out, st)
                     offs = pb.row_offsets()
@@ -144,13 +157,14 @@ class Server:
                             r.result = (out, offs[j], offs[j + 1])
                     ev = torch.cuda.Event()
                     ev.record(st)
+                    self._last[k] = ev
                 inflight.append((small, ev, sum(self._bound(r) for r in small), out))
                 self.stats["perm_batches"] += 1
                 batched = set(map(id, small))
                 other = [r for r in other if id(r) not in batched]
             for r in other:
-                k = turn % self.slots
-                turn += 1
+                k = self._slot(turn)
+                turn = k + 1
                 ctx, st = self._ctx[k], self._streams[k]
                 a = self.mats[r.mat]
                 with torch.cuda.stream(st):
@@ -163,13 +177,15 @@ class Server:
                         r.result = out
                     ev = torch.cuda.Event()
                     ev.record(st)
+                    self._last[k] = ev
                 inflight.append(([r], ev, self._bound(r), out))
             if ex:  # count the round's extractions as one batch
-                k = turn % self.slots
-                turn += 1
+                k = self._slot(turn)
+                turn = k + 1
                 ctx, st = self._ctx[k], self._streams[k]
                 with torch.cuda.stream(st):
-                    bt = ExtractBatch(ctx, self.mats, [(r.mat, r.I, r.J) for r in ex], stream=st)
+                    bt = ExtractBatch(ctx, self.mats, [(r.mat, r.I, r.J) for r in ex], stream=st,
+                                      descs=self._descs)
                 held = (ex, bt, k, self._batch_bytes(bt))
                 self.stats["batches"] += 1
             if held is not None:
@@ -185,6 +201,7 @@ class Server:
                                 r.result = (out, offs[j], offs[j + 1])
                         ev = torch.cuda.Event()
                         ev.record(st)
+                        self._last[k] = ev
                     used += nbytes
                     inflight.append((ex_h, ev, nbytes, (bt, out, offs)))
                     held = None
