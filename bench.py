@@ -72,6 +72,12 @@ def parse():
     return ap.parse_args()
 
 
+def peak_gbs():
+    """The HBM denominator: the measured copy bandwidth, else the fallback figure."""
+    pk = peaks()
+    return pk["hbm_gbs"] if pk else 6800.0
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -348,7 +354,8 @@ def log_summary(res):
     bt = ops.get("batch_extract", {})
     if "batched_ms" in bt:
         log(f"SUMMARY batch: {bt['batched_ms']} ms batched vs {bt['plain_ms']} ms plain | graph fill "
-            f"{bt['graph_fill_ms']} ms | {bt['batched_value'] / 1e9:.2f} G entries/s")
+            f"{bt['graph_fill_ms']} ms | whole batch from one graph {bt.get('graph_run_ms')} ms, frac "
+            f"{bt.get('graph_run_roofline', {}).get('frac')} | {bt['batched_value'] / 1e9:.2f} G entries/s")
     pb = ops.get("batch_permute", {})
     if "batched_ms" in pb:
         log(f"SUMMARY batch permute: {pb['batched_ms']} ms batched vs {pb['plain_ms']} ms plain | graph "
@@ -770,6 +777,28 @@ def bench_batch(ctx, args, dev, ws):
     nnz = bt.nnz
     steps = max(3, args.steps)
     ms_fill = time_steps(graph.replay, steps, 2, ws) / steps
+    # the whole batch (identify, count, row pointer, fill, sort) from one graph
+    out_r = bt.alloc(torch.int64)
+    with torch.cuda.stream(s):
+        bt.run(out_r, s)
+    torch.cuda.current_stream().wait_stream(s)
+    ctx.sync()
+    same_run = bool(torch.equal(out_r.rowptr, out.rowptr) and torch.equal(out_r.colidx, out.colidx))
+    graph_run = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_run):
+        bt.run(out_r, torch.cuda.current_stream())
+    ms_run = time_steps(graph_run.replay, steps, 2, ws) / steps
+    ctx.sync()
+    # algorithmic bytes of the batch: per output row I[i] and the row-pointer pair (read),
+    # the output row pointer (write); every selected source column (read); per kept entry
+    # its value (read) and column + value (write); J (read)
+    sel = 0
+    for mi, I, _ in reqs:
+        rp, il = mats[mi].rowptr, I.long()
+        sel += int((rp[il + 1] - rp[il]).sum())
+    nI = sum(I.numel() for _, I, _ in reqs)
+    nJ = sum(J.numel() for _, _, J in reqs)
+    alg = 28 * nI + 4 * sel + 12 * nnz + 4 * nJ
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(3):
@@ -793,6 +822,11 @@ def bench_batch(ctx, args, dev, ws):
            "nnz_out": nnz, "same_nnz_as_plain": plain_nnz == nnz,
            "batched_ms": round(ms_batch, 3), "batched_value": round(nnz / (ms_batch * 1e-3), 1),
            "graph_fill_ms": round(ms_fill, 3), "graph_fill_value": round(nnz / (ms_fill * 1e-3), 1),
+           "graph_run_ms": round(ms_run, 3), "graph_run_value": round(nnz / (ms_run * 1e-3), 1),
+           "graph_run_same_as_fill": same_run,
+           "alg_bytes": alg, "selected_source_entries": sel,
+           "graph_run_roofline": {"achieved": round(alg / (ms_run * 1e-3) / 1e9, 1), "peak": peak_gbs(),
+                                  "unit": "GB/s", "frac": round(alg / (ms_run * 1e-3) / 1e9 / peak_gbs(), 4)},
            "plain_ms": round(ms_plain, 3), "plain_value": round(nnz / (ms_plain * 1e-3), 1),
            "unit": UNIT, "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2)}
     res["autotuned"] = bench_batch_tuned(ctx, dms, reqs, nnz, steps, ws)

@@ -322,6 +322,15 @@ SP_API sp_status sp_extract_batch_count(sp_ctx* ctx, const sp_csr* mats, int64_t
                                         const sp_extract_req* reqs, int64_t nreq, sp_itype idx_type,
                                         sp_batch** batch, int64_t* nnz_total, sp_stream_t stream);
 SP_API sp_status sp_extract_batch_fill(sp_ctx* ctx, sp_batch* batch, sp_csr* out, sp_stream_t stream);
+/* sp_extract_batch_run: the whole batch again on the device -- identification, kept
+ *   counts, row pointer, fill and row sort -- into `out` (arrays as for the fill, the
+ *   counted nnz being their capacity).  It reads I_k and J_k when it runs, allocates
+ *   nothing (the count reserved its workspace) and never synchronises, so count, fill
+ *   and sort replay together from one CUDA graph while the inputs keep their addresses
+ *   and sizes.  If the inputs now select more entries than the counted nnz, the row
+ *   pointer is clamped to it, SP_ERR_OVERFLOW is recorded for sp_ctx_sync and the
+ *   output is not the extraction (no write leaves its arrays).  Errors: as the fill. */
+SP_API sp_status sp_extract_batch_run(sp_ctx* ctx, sp_batch* batch, sp_csr* out, sp_stream_t stream);
 /* First output row of request k (k = nreq gives the total); -1 for a bad k. */
 SP_API int64_t sp_batch_row_offset(const sp_batch* batch, int64_t k);
 /* Release a batch (stream-ordered on the stream of its count).  NULL is a no-op. */

@@ -151,6 +151,7 @@ SIGNATURES = {
                                  _vp]),
     "sp_extract_batch_count": (_int, [_vp, _PCSR, _i64, _PREQ, _i64, _int, _vp, _vp, _vp]),
     "sp_extract_batch_fill": (_int, [_vp, _vp, _PCSR, _vp]),
+    "sp_extract_batch_run": (_int, [_vp, _vp, _PCSR, _vp]),
     "sp_batch_row_offset": (_i64, [_vp, _i64]),
     "sp_batch_destroy": (_int, [_vp, _vp]),
     "sp_permute_batch_plan": (_int, [_vp, _PCSR, _i64, _PPREQ, _i64, _int, _vp, _vp, _vp]),
@@ -554,6 +555,14 @@ class ExtractBatch:
         self.ctx._check(self.ctx.lib.sp_extract_batch_fill(self.ctx.handle, self.handle,
                                                            ctypes.byref(self._out_desc), _stream(stream)),
                         "sp_extract_batch_fill")
+
+    def run(self, out: CSR, stream=None):
+        """The whole batch again (identify, count, row pointer, fill, sort) into `out`
+        (capacity: the counted nnz), without allocating or synchronising: capturable."""
+        self._run_desc = out.desc()
+        self.ctx._check(self.ctx.lib.sp_extract_batch_run(self.ctx.handle, self.handle,
+                                                          ctypes.byref(self._run_desc), _stream(stream)),
+                        "sp_extract_batch_run")
 
     def close(self):
         if self.handle:

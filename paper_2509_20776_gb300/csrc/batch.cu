@@ -79,7 +79,9 @@ struct sp_batch {
   std::vector<sp::ReqView> hviews;  // host copy (kept: the copy to rv is asynchronous)
   long long n_slow = 0;         // rank map: output rows of more than XFAST source entries
   long long* vp = nullptr;      // rows + 1: counts, then the output row pointer
-  size_t ws_bytes = 0;          // workspace the fill needs (reserved by the count)
+  unsigned* counters = nullptr; // 16 device counters of the count
+  char* scan_ws = nullptr;      // the row pointer scan's workspace
+  size_t ws_bytes = 0;          // workspace the fill and the run need (reserved by the count)
   cudaStream_t stream = nullptr;
 };
 
@@ -300,6 +302,26 @@ __global__ void k_batch_rows(const BatchReq* __restrict__ reqs, const BatchMat* 
   }
 }
 
+// Row pointer store of a run: clamped to the counted nnz (the output's capacity).
+template <class T>
+struct StoreCappedRp {
+  long long* vp;
+  T* out;
+  long long cap;
+  DevStatus* st;
+  __device__ void operator()(long long i, long long v) const {
+    if (v > cap) {
+      dev_fail(st, SP_ERR_OVERFLOW, i);
+      v = cap;
+    }
+    vp[i] = v;
+    out[i] = T(v);
+  }
+};
+
+template <class RP, class CI, class VT, class IX>
+sp_status batch_device_count(sp_ctx* ctx, sp_batch* b, cudaStream_t s, sp_csr* out);
+
 template <class RP, class CI, class VT, class IX>
 sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>& hm,
                            const std::vector<BatchReq>& hr, cudaStream_t s) {
@@ -341,7 +363,6 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   b->rsn = rank ? cv.at<long long>(o_rn) : nullptr;
   b->rreq = rank ? cv.at<int>(o_rq) : nullptr;
   b->rv = rank ? cv.at<ReqView>(o_rv) : nullptr;
-  unsigned* counters = cv.at<unsigned>(o_ct);
   if (rank && nreq > 0) {
     b->hviews.resize(size_t(nreq));
     for (long long k = 0; k < nreq; ++k) {
@@ -356,6 +377,36 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
   SP_CUDA(cudaMemcpyAsync(b->reqs, hr.data(), hr.size() * sizeof(BatchReq), cudaMemcpyHostToDevice, s));
   SP_CUDA(cudaMemcpyAsync(b->droff, b->roff.data(), size_t(nreq + 1) * 8, cudaMemcpyHostToDevice, s));
   SP_CUDA(cudaMemcpyAsync(b->djoff, joff.data(), size_t(nreq + 1) * 8, cudaMemcpyHostToDevice, s));
+  b->counters = cv.at<unsigned>(o_ct);
+  b->scan_ws = cv.at<char>(o_sc);
+  SP_TRY((batch_device_count<RP, CI, VT, IX>(ctx, b, s, nullptr)));
+  long long* h = ctx->hbuf;  // the context's pinned scratch, read back before returning
+  SP_CUDA(cudaMemcpyAsync(h, b->vp + rows, 8, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(h + 1, b->counters + 1, 4, cudaMemcpyDeviceToHost, s));
+  SP_TRY(ctx_collect(ctx, s));
+  b->nnz = h[0];
+  b->n_slow = rank ? (long long)*reinterpret_cast<const unsigned*>(h + 1) : 0;
+  // reserve now the workspace the fill's row sort needs (and a run's: any number of slow
+  // rows up to all of them), so neither allocates
+  Carver cf, cr;
+  size_t rf[kRowsSlots];
+  rows_reserve(cf, rows, b->nnz, sizeof(VT), rf, true, b->n_slow);
+  rows_reserve(cr, rows, b->nnz, sizeof(VT), rf, true, rank ? rows : 0);
+  b->ws_bytes = cf.total() > cr.total() ? cf.total() : cr.total();
+  char* base;
+  SP_TRY(ctx_workspace(ctx, b->ws_bytes, s, &base));
+  return SP_OK;
+}
+
+// The device part of the count: identify, per-row kept counts, and their exclusive scan
+// into b->vp.  With `out` (a run), the scan is clamped to the counted nnz (an overflow
+// is reported as SP_ERR_OVERFLOW) and mirrored into out's row pointer.  Launches only:
+// no allocation, no synchronisation.
+template <class RP, class CI, class VT, class IX>
+sp_status batch_device_count(sp_ctx* ctx, sp_batch* b, cudaStream_t s, sp_csr* out) {
+  const long long nreq = b->nreq, rows = b->rows, jtot = b->jtot, nw = b->nwords;
+  const bool rank = b->identify == 0;
+  unsigned* counters = b->counters;
   const int nsm = ctx->num_sms;
   IX* jkey = static_cast<IX*>(b->jkey);
   if (rank) {
@@ -369,7 +420,7 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
       }
       SP_CUDA(cudaGetLastError());
     }
-    SP_TRY(launch_scan(ctx, s, LoadPopc{b->jbits}, StoreRank{b->jbits, b->jmeta, nw}, nw, cv.at<char>(o_sc),
+    SP_TRY(launch_scan(ctx, s, LoadPopc{b->jbits}, StoreRank{b->jbits, b->jmeta, nw}, nw, b->scan_ws,
                        SP_PHASE_MAP));
     if (jtot > 0) {
       {
@@ -428,43 +479,30 @@ sp_status batch_count_impl(sp_ctx* ctx, sp_batch* b, const std::vector<BatchMat>
     }
     SP_CUDA(cudaGetLastError());
   }
-  SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp}, StoreDual<long long>{b->vp, nullptr, ctx->dstatus},
-                     rows, cv.at<char>(o_sc)));
-  long long* h = ctx->hbuf;  // the context's pinned scratch, read back before returning
-  SP_CUDA(cudaMemcpyAsync(h, b->vp + rows, 8, cudaMemcpyDeviceToHost, s));
-  SP_CUDA(cudaMemcpyAsync(h + 1, counters + 1, 4, cudaMemcpyDeviceToHost, s));
-  SP_TRY(ctx_collect(ctx, s));
-  b->nnz = h[0];
-  b->n_slow = rank ? (long long)*reinterpret_cast<const unsigned*>(h + 1) : 0;
-  // reserve now the workspace the fill's row sort needs, so the fill allocates nothing
-  Carver cf;
-  size_t rf[kRowsSlots];
-  rows_reserve(cf, rows, b->nnz, sizeof(VT), rf, true, b->n_slow);
-  b->ws_bytes = cf.total();
-  char* base;
-  SP_TRY(ctx_workspace(ctx, b->ws_bytes, s, &base));
+  if (!out) {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp}, StoreDual<long long>{b->vp, nullptr, ctx->dstatus},
+                       rows, b->scan_ws));
+  } else if (out->rowptr_type == SP_I64) {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp},
+                       StoreCappedRp<long long>{b->vp, static_cast<long long*>(out->rowptr), b->nnz, ctx->dstatus},
+                       rows, b->scan_ws));
+  } else {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{b->vp},
+                       StoreCappedRp<int32_t>{b->vp, static_cast<int32_t*>(out->rowptr), b->nnz, ctx->dstatus},
+                       rows, b->scan_ws));
+  }
   return SP_OK;
 }
 
+// The fill after the row pointer: kept entries of every output row written at b->vp,
+// then the row sort.  nnz: the output's entries (capacity); n_slow: rows the fill may
+// queue for the sort.  Its workspace was reserved by the count.
 template <class RP, class CI, class VT, class IX>
-sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s) {
-  const long long rows = b->rows, nnz = b->nnz;
-  // the row sort's workspace was reserved by the count: check it before any launch, so
-  // a failure leaves the output untouched
+sp_status batch_fill_body(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s, long long nnz, long long n_slow) {
+  const long long rows = b->rows;
   Carver cf;
   size_t rf[kRowsSlots];
-  rows_reserve(cf, rows, nnz, sizeof(VT), rf, true, b->n_slow);
-  if (nnz > 0 && cf.total() > ctx->ws_cap) return SP_ERR_INTERNAL;
-  // the int64 row pointer is the batch's own; an int32 output gets a narrowed copy
-  if (out->rowptr_type == SP_I64) {
-    SP_CUDA(cudaMemcpyAsync(out->rowptr, b->vp, size_t(rows + 1) * 8, cudaMemcpyDeviceToDevice, s));
-  } else {
-    SP_PHASE(SP_PHASE_OTHER);
-    k_narrow<int32_t><<<grid_for(rows + 1, 256, ctx->num_sms * 8), 256, 0, s>>>(
-        b->vp, rows + 1, static_cast<int32_t*>(out->rowptr), ctx->dstatus);
-  }
-  SP_CUDA(cudaGetLastError());
-  if (nnz == 0) return SP_OK;
+  rows_reserve(cf, rows, nnz, sizeof(VT), rf, true, n_slow);
   CI* oc = static_cast<CI*>(out->colidx);
   VT* ov = static_cast<VT*>(out->values);
   const int kb = ceil_log2_u64(uint64_t(b->max_nj > 1 ? b->max_nj : 1));
@@ -474,7 +512,7 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
     char* base;
     SP_TRY(ctx_workspace(ctx, cf.total(), s, &base));
     cf.bind(base);
-    const RowsWs w = rows_bind(cf, rows, nnz, rf, true, b->n_slow);
+    const RowsWs w = rows_bind(cf, rows, nnz, rf, true, n_slow);
     SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
     {
       SP_PHASE(SP_PHASE_GATHER);
@@ -498,8 +536,40 @@ sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s)
   char* base;
   SP_TRY(ctx_workspace(ctx, cf.total(), s, &base));
   cf.bind(base);
-  const RowsWs w = rows_bind(cf, rows, nnz, rf, true, b->n_slow);
+  const RowsWs w = rows_bind(cf, rows, nnz, rf, true, n_slow);
   return run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, b->vp, rows, nnz, kb, w, nullptr, true, oc, ov);
+}
+
+template <class RP, class CI, class VT, class IX>
+sp_status batch_fill_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s) {
+  const long long rows = b->rows, nnz = b->nnz;
+  // the row sort's workspace was reserved by the count: check it before any launch, so
+  // a failure leaves the output untouched
+  Carver cf;
+  size_t rf[kRowsSlots];
+  rows_reserve(cf, rows, nnz, sizeof(VT), rf, true, b->n_slow);
+  if (nnz > 0 && cf.total() > ctx->ws_cap) return SP_ERR_INTERNAL;
+  // the int64 row pointer is the batch's own; an int32 output gets a narrowed copy
+  if (out->rowptr_type == SP_I64) {
+    SP_CUDA(cudaMemcpyAsync(out->rowptr, b->vp, size_t(rows + 1) * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    SP_PHASE(SP_PHASE_OTHER);
+    k_narrow<int32_t><<<grid_for(rows + 1, 256, ctx->num_sms * 8), 256, 0, s>>>(
+        b->vp, rows + 1, static_cast<int32_t*>(out->rowptr), ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  if (nnz == 0) return SP_OK;
+  return batch_fill_body<RP, CI, VT, IX>(ctx, b, out, s, nnz, b->n_slow);
+}
+
+// A run: the count's device part again (clamped to the counted nnz), then the fill.
+template <class RP, class CI, class VT, class IX>
+sp_status batch_run_impl(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s) {
+  const long long rows = b->rows, nnz = b->nnz;
+  if (b->ws_bytes > ctx->ws_cap) return SP_ERR_INTERNAL;  // reserved by the count
+  SP_TRY((batch_device_count<RP, CI, VT, IX>(ctx, b, s, out)));
+  if (nnz == 0) return SP_OK;
+  return batch_fill_body<RP, CI, VT, IX>(ctx, b, out, s, nnz, b->identify == 0 ? rows : 0);
 }
 
 }  // namespace sp
@@ -603,6 +673,33 @@ extern "C" sp_status sp_extract_batch_fill(sp_ctx* ctx, sp_batch* b, sp_csr* out
         return dispatch_i(b->idx_type, [&](auto ix) {
           using IX = decltype(ix);
           return batch_fill_impl<RP, CI, VT, IX>(ctx, b, out, s);
+        });
+      });
+    });
+  });
+}
+
+extern "C" sp_status sp_extract_batch_run(sp_ctx* ctx, sp_batch* b, sp_csr* out, sp_stream_t stream) {
+  if (!ctx || !b || !out) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type != SP_I32 && out->rowptr_type != SP_I64) return SP_ERR_INVALID_ARG;
+  if (out->rowptr_type == SP_I32 && b->nnz > INT32_MAX) return SP_ERR_OVERFLOW;
+  if (!out->rowptr || (b->nnz > 0 && (!out->colidx || !out->values))) return SP_ERR_INVALID_ARG;
+  if (out->colidx_type != b->colidx_type || out->value_type != b->value_type) return SP_ERR_INVALID_ARG;
+  out->nrows = b->rows;
+  out->ncols = b->max_nj;
+  out->nnz = b->nnz;
+  if (b->nmats == 0) return SP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx_begin_call(ctx, SP_OP_BATCH, b->rows);
+  return dispatch_i(b->rowptr_type, [&](auto rp) {
+    using RP = decltype(rp);
+    return dispatch_i(b->colidx_type, [&](auto ci) {
+      using CI = decltype(ci);
+      return dispatch_v(b->value_type, [&](auto vt) {
+        using VT = decltype(vt);
+        return dispatch_i(b->idx_type, [&](auto ix) {
+          using IX = decltype(ix);
+          return batch_run_impl<RP, CI, VT, IX>(ctx, b, out, s);
         });
       });
     });

@@ -149,3 +149,75 @@ def test_batch_errors(ctx, identify):
     assert e.value.name == "SP_ERR_INVALID_ARG"
     out, offs = ctx.sp_extract_batch(dms, [(1, I, torch.tensor([3], dtype=torch.int32).cuda())])
     assert offs == [0, 2]
+
+
+@pytest.mark.parametrize("identify", [0, 1])
+def test_batch_run_whole_graph(ctx, identify):
+    """Count once, then the whole batch (identify, count, row pointer, fill, sort) from one
+    CUDA graph; replayed after every request's I and J are shuffled in place (the same
+    selections, so the same sizes), it gives the new inputs' results."""
+    ms = _mats()
+    dms = [to_dev(m) for m in ms]
+    reqs = _requests(ms, 150, 7)
+    dreqs = [(mi, I.cuda(), J.cuda()) for mi, I, J in reqs]
+    ctx.set_shapes(identify=identify)
+    try:
+        bt = ctx.extract_batch(dms, dreqs)
+        out = bt.alloc(torch.int64)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            bt.run(out, s)  # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        ctx.sync()
+        _check(out, bt.row_offsets(), ms, reqs, f"run, identify {identify}")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bt.run(out, torch.cuda.current_stream())
+        gen = torch.Generator().manual_seed(17)
+        new = []
+        for (mi, I, J), (_, dI, dJ) in zip(reqs, dreqs):
+            I2 = I[torch.randperm(I.numel(), generator=gen)]
+            J2 = J[torch.randperm(J.numel(), generator=gen)]
+            dI.copy_(I2)
+            dJ.copy_(J2)
+            new.append((mi, I2, J2))
+        out.colidx.zero_()
+        out.values.zero_()
+        out.rowptr.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        ctx.sync()
+        _check(out, bt.row_offsets(), ms, new, f"graph replay of the run, identify {identify}")
+        bt.close()
+    finally:
+        ctx.set_shapes(identify=-1)
+
+
+def test_batch_run_overflow_is_reported(ctx):
+    """A run whose inputs now select more entries than the count found reports
+    SP_ERR_OVERFLOW at the next sync, writes nothing outside the output, and the
+    context stays usable."""
+    from paper_2509_20776_gb300 import SpError
+    ms = _mats()
+    dms = [to_dev(m) for m in ms]
+    A = ms[3]  # R-MAT scale 14: rows of very different lengths
+    rl = A.rowptr[1:] - A.rowptr[:-1]
+    light, heavy = int(torch.argmin(rl + (rl == 0) * 10**9)), int(torch.argmax(rl))
+    I = torch.full((8,), light, dtype=torch.int32).cuda()
+    J = torch.arange(A.ncols, dtype=torch.int32).cuda()
+    bt = ctx.extract_batch(dms, [(3, I, J)])
+    cap = bt.nnz
+    out = bt.alloc(torch.int64)
+    guard = torch.full((1024,), 7, dtype=torch.int32, device="cuda")  # a neighbour to watch
+    I.fill_(heavy)
+    bt.run(out)
+    with pytest.raises(SpError) as e:
+        ctx.sync()
+    assert e.value.name == "SP_ERR_OVERFLOW"
+    assert int(out.rowptr[-1]) == cap
+    assert bool((guard == 7).all())
+    bt.close()
+    I.fill_(light)
+    ref, offs = ctx.sp_extract_batch(dms, [(3, I, J)])
+    assert ref.nnz == cap and offs == [0, 8]
