@@ -231,6 +231,252 @@ struct SegStore {
   }
 };
 
+// Longest row of B (row pointer rpB, n rows), saturated at 2^32 - 1.
+__global__ void k_max_row_len(const long long* __restrict__ rp, long long n, unsigned* out) {
+  unsigned mx = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long L = rp[i + 1] - rp[i];
+    const unsigned l = L <= 0 ? 0u : (L > 0xFFFFFFFFll ? 0xFFFFFFFFu : unsigned(L));
+    mx = l > mx ? l : mx;
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+// ---- rebuilt rows by merging (REPLACE, rows of B of at most 32 entries) ------------------
+// Row I[i] of A' is the merge of two sorted runs: A's row without the columns of J
+// (ascending already: A is canonical) and B's row i relabelled through J (at most 32
+// entries, sorted in registers by a bitonic network).  Every kept A entry lands at its
+// kept rank plus the number of B' keys below it (a search over the warp's registers);
+// every B' entry at its rank plus the number of kept A entries below it (accumulated
+// chunk by chunk).  No row sort follows.
+constexpr unsigned kPadKey = 0xFFFFFFFFu;
+
+// lower bound of `key` in the ascending values `v` held by lanes [0, 32) (kPadKey for
+// unused lanes): the number of lanes whose value is below `key`.  All lanes call it.
+__device__ __forceinline__ int warp_lower_bound(uint32_t v, uint32_t key) {
+  int pos = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const uint32_t x = __shfl_sync(0xffffffffu, v, pos + step - 1);
+    if (x < key) pos += step;
+  }
+  const uint32_t x = __shfl_sync(0xffffffffu, v, pos & 31);
+  return pos + ((pos < 32 && x < key) ? 1 : 0);
+}
+
+// Ascending bitonic sort of (key, value) over the warp's 32 lanes.
+template <class VT>
+__device__ __forceinline__ void warp_sort32(uint32_t& k, VT& v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const uint32_t ok = __shfl_xor_sync(0xffffffffu, k, j);
+      const VT ov = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool up = (lane & size) == 0, lower = (lane & j) == 0;
+      if (lower == up ? ok < k : ok > k) {
+        k = ok;
+        v = ov;
+      }
+    }
+  }
+}
+
+template <class RP, class CI, class VT, class IX>
+struct MergeSrc {
+  const RP* rpA;
+  const CI* colA;
+  const VT* valA;
+  const long long* rpB;
+  const CI* colB;
+  const VT* valB;
+  const IX* I;
+  const IX* J;
+  const uint32_t* jbits;
+  long long m, n, nnzA, nJ, nnzB;
+  // A's row I[i] and B's row i (ranges validated as the count's loader does)
+  __device__ void rows(long long i, long long& sA, long long& LA, long long& sB, long long& LB) const {
+    sA = LA = sB = LB = 0;
+    const long long r = (long long)I[i];
+    if (r >= 0 && r < m) {
+      const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+      if (s >= 0 && e >= s && e <= nnzA) {
+        sA = s;
+        LA = e - s;
+      }
+    }
+    const long long s = rpB[i], e = rpB[i + 1];
+    if (s >= 0 && e >= s && e <= nnzB) {
+      sB = s;
+      LB = e - s;
+    }
+  }
+  // B's row i relabelled through J into this lane's (key, value), sorted across the warp;
+  // returns the number of entries (B entries with a column outside [0, nJ) are dropped,
+  // as the count drops them)
+  __device__ int load_b(long long sB, long long LB, uint32_t& bk, VT& bv) const {
+    const int lane = threadIdx.x & 31;
+    bk = kPadKey;
+    bv = VT(0);
+    if (lane < LB) {
+      const long long c = (long long)colB[sB + lane];
+      if (c >= 0 && c < nJ) {
+        bk = uint32_t((long long)ld_map(J + c));
+        bv = valB[sB + lane];
+      }
+    }
+    warp_sort32(bk, bv);
+    return __popc(__ballot_sync(0xffffffffu, bk != kPadKey));
+  }
+  __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
+};
+
+// Rows of at most SRC_LONG source entries (A's and B's together), one warp each.
+template <class RP, class CI, class VT, class IX>
+__global__ void __launch_bounds__(256) k_assign_merge_warp(MergeSrc<RP, CI, VT, IX> ms, long long nI,
+                                                           const long long* __restrict__ vp, CI* __restrict__ tcol,
+                                                           VT* __restrict__ tval, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = w0; i < nI; i += nw) {
+    long long sA, LA, sB, LB;
+    ms.rows(i, sA, LA, sB, LB);
+    if (LA + LB > SRC_LONG) continue;  // k_assign_merge_long (the count listed it)
+    const long long o = vp[i], oe = vp[i + 1];
+    uint32_t bk;
+    VT bv;
+    const int nb = ms.load_b(sB, LB, bk, bv);
+    long long kbase = 0;
+    unsigned cntA = 0;
+    for (long long e0 = 0; e0 < LA; e0 += 32) {
+      const long long e = e0 + lane;
+      const bool valid = e < LA;
+      const long long c = valid ? (long long)ld_stream(ms.colA + sA + e) : 0;
+      const bool kept = valid && c >= 0 && c < ms.n && !ms.in_j(c);
+      VT v;
+      if (kept) v = ld_stream(ms.valA + sA + e);
+      const unsigned km = __ballot_sync(0xffffffffu, kept);
+      const uint32_t ck = valid ? uint32_t(c) : kPadKey;
+      const int nless = warp_lower_bound(bk, ck);   // B' keys below this A column
+      const int lbc = warp_lower_bound(ck, bk);     // this chunk's A columns below this B' key
+      if (kept) {
+        const long long pos = o + kbase + __popc(km & lt) + nless;
+        if (pos < oe) {
+          st_stream(tcol + pos, CI(c));
+          st_stream(tval + pos, v);
+        } else {
+          dev_fail(st, SP_ERR_INTERNAL, -30);
+        }
+      }
+      cntA += __popc(km & (lbc >= 32 ? 0xffffffffu : ((1u << lbc) - 1u)));
+      kbase += __popc(km);
+    }
+    if (lane < nb) {
+      const long long pos = o + lane + cntA;
+      if (pos < oe) {
+        st_stream(tcol + pos, CI(bk));
+        st_stream(tval + pos, bv);
+      } else {
+        dev_fail(st, SP_ERR_INTERNAL, -31);
+      }
+    }
+    if (lane == 0 && o + kbase + nb != oe) dev_fail(st, SP_ERR_INTERNAL, -32);
+  }
+}
+
+// Rows of more than SRC_LONG source entries (the count's list), one 1024-thread CTA each:
+// every warp takes 32 consecutive entries of a slice, the kept ranks are scanned across
+// the block, and each warp's counts of kept entries below the B' keys are added up.
+template <class RP, class CI, class VT, class IX>
+__global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT, IX> ms,
+                                                            const long long* __restrict__ cl_rows,
+                                                            const unsigned* __restrict__ n_cl, long long cl_cap,
+                                                            const long long* __restrict__ vp, unsigned* ticket,
+                                                            CI* __restrict__ tcol, VT* __restrict__ tval,
+                                                            DevStatus* st) {
+  constexpr int NW = 1024 / 32;
+  __shared__ unsigned s_item;
+  __shared__ unsigned s_wc[NW], s_wx[NW], s_tot, s_cnt[32];
+  __shared__ long long s_base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned count = *n_cl;
+  if (count > cl_cap) count = unsigned(cl_cap);
+  for (;;) {
+    if (t == 0) {
+      s_item = atomicAdd(ticket, 1u);
+      s_base = 0;
+    }
+    if (t < 32) s_cnt[t] = 0;
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= count) break;
+    const long long i = cl_rows[item];
+    long long sA, LA, sB, LB;
+    ms.rows(i, sA, LA, sB, LB);
+    const long long o = vp[i], oe = vp[i + 1];
+    uint32_t bk;
+    VT bv;
+    const int nb = ms.load_b(sB, LB, bk, bv);
+    unsigned cntA = 0;
+    for (long long e0 = 0; e0 < LA; e0 += (long long)blockDim.x * LOAD_U) {
+#pragma unroll
+      for (int u = 0; u < LOAD_U; ++u) {
+        const long long e = e0 + (long long)u * blockDim.x + t;  // warp w: 32 consecutive entries
+        const bool valid = e < LA;
+        const long long c = valid ? (long long)ld_stream(ms.colA + sA + e) : 0;
+        const bool kept = valid && c >= 0 && c < ms.n && !ms.in_j(c);
+        VT v;
+        if (kept) v = ld_stream(ms.valA + sA + e);
+        const unsigned km = __ballot_sync(0xffffffffu, kept);
+        const uint32_t ck = valid ? uint32_t(c) : kPadKey;
+        const int nless = warp_lower_bound(bk, ck);
+        const int lbc = warp_lower_bound(ck, bk);
+        cntA += __popc(km & (lbc >= 32 ? 0xffffffffu : ((1u << lbc) - 1u)));
+        if (lane == 0) s_wc[w] = __popc(km);
+        __syncthreads();
+        if (w == 0) {
+          const unsigned x = s_wc[lane];
+          const unsigned inc = warp_incl_sum(x);
+          s_wx[lane] = inc - x;
+          if (lane == NW - 1) s_tot = inc;
+        }
+        __syncthreads();
+        if (kept) {
+          const long long pos = o + s_base + s_wx[w] + __popc(km & lt) + nless;
+          if (pos < oe) {
+            st_stream(tcol + pos, CI(c));
+            st_stream(tval + pos, v);
+          } else {
+            dev_fail(st, SP_ERR_INTERNAL, -33);
+          }
+        }
+        __syncthreads();
+        if (t == 0) s_base += s_tot;
+      }
+    }
+    atomicAdd(&s_cnt[lane], cntA);
+    __syncthreads();
+    if (w == 0) {
+      if (lane < nb) {
+        const long long pos = o + lane + s_cnt[lane];
+        if (pos < oe) {
+          st_stream(tcol + pos, CI(bk));
+          st_stream(tval + pos, bv);
+        } else {
+          dev_fail(st, SP_ERR_INTERNAL, -34);
+        }
+      }
+      if (lane == 0 && o + s_base + nb != oe) dev_fail(st, SP_ERR_INTERNAL, -35);
+    }
+    __syncthreads();
+  }
+}
+
 template <class RP, class CI, class IX>
 sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const sp_csr& A = pl->A;
@@ -295,6 +541,13 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   }
   SP_TRY(widen_rowptr(ctx, s, B.rowptr, B.rowptr_type, nI + 1, pl->rpB));
   if (nI > 0) {
+    {
+      SP_PHASE(SP_PHASE_COUNT);
+      k_max_row_len<<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(pl->rpB, nI, pl->counters + 6);
+    }
+    SP_CUDA(cudaGetLastError());
+  }
+  if (nI > 0) {
     CountLists cl{pl->cl_rows, pl->counters + 0, pl->list_cap};
     auto count = [&](const auto& ct) -> sp_status {
       {
@@ -329,9 +582,11 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
                      cv.at<char>(o_s2)));
   SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp_out + m, 8, cudaMemcpyDeviceToHost, s));
   SP_CUDA(cudaMemcpyAsync(pl->h_tail + 1, pl->vp + nI, 8, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(pl->h_tail + 2, pl->counters + 6, 4, cudaMemcpyDeviceToHost, s));
   SP_TRY(ctx_collect(ctx, s));
   pl->nnz_out = pl->h_tail[0];
   pl->nnz_temp = pl->h_tail[1];
+  pl->max_lb = nI > 0 ? (long long)*reinterpret_cast<const unsigned*>(pl->h_tail + 2) : 0;
   return SP_OK;
 }
 
@@ -398,7 +653,30 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   cv.bind(base);
   CI* tcol = cv.at<CI>(o_tc);
   VT* tval = cv.at<VT>(o_tv);
-  if (nt > 0) {
+  if (nt > 0 && pl->mode == SP_ASSIGN_REPLACE && pl->max_lb <= 32) {
+    // rebuilt rows merged in order: A's surviving run and B's relabelled row, no sort
+    const sp_csr& B = pl->B;
+    const MergeSrc<RP, CI, VT, IX> ms{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
+                                     static_cast<const VT*>(A.values), pl->rpB, static_cast<const CI*>(B.colidx),
+                                     static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
+                                     static_cast<const IX*>(pl->J), static_cast<const uint32_t*>(pl->jmap), A.nrows,
+                                     A.ncols, A.nnz, pl->nJ, B.nnz};
+    unsigned* ticket = cv.at<unsigned>(o_tk);
+    SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
+    const int nsm = ctx->num_sms;
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_assign_merge_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ms, nI, pl->vp, tcol, tval,
+                                                                            ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_assign_merge_long<<<nsm, 1024, 0, s>>>(ms, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket,
+                                                tcol, tval, ctx->dstatus);
+    }
+    SP_CUDA(cudaGetLastError());
+  } else if (nt > 0) {
     // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
     SP_TRY((assign_stage<RP, CI, VT, IX>(ctx, pl, tcol, tval, cv.at<unsigned>(o_tk), s)));
     const RowsWs w1 = rows_bind(cv, nI, nt, r1);

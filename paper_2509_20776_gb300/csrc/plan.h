@@ -46,6 +46,7 @@ struct sp_plan {
   uint32_t* jsk = nullptr;
   uint32_t* jsp = nullptr;
   long long n_slow = 0;
+  long long max_lb = 0;  // assignment: longest row of B (the merge fill takes rows of at most 32)
   long long list_cap = 0;
   unsigned* counters = nullptr;  // [0] n_cl [3] count ticket [4] rows of more than XFAST entries
   long long* h_tail = nullptr;   // the context's pinned scratch: totals read back by the count call

@@ -296,6 +296,33 @@ def test_assign_hubs_and_roundtrip(ctx):
     assert_same(E, to_oracle(Bm), "extract after assign")
 
 
+@pytest.mark.parametrize("longest", [32, 33])
+def test_assign_merge_boundaries(ctx, longest):
+    """REPLACE with every row of B at most 32 entries takes the merge fill (A's surviving
+    run and B's relabelled row merged in order, no row sort); one row of 33 takes the
+    staged fill and the row sort.  Rows of B of 0, 1, 31 and the longest length, hub rows
+    of A on both kernels of the merge (warp and CTA), keys before, between and after A's."""
+    A = rmat(14)
+    n = A.nrows
+    rng = np.random.default_rng(longest)
+    rest = synth.random_subset(n - 16, 1500, 5, 1) + 16
+    I = torch.cat([torch.arange(16, dtype=rest.dtype), rest])
+    I = I[torch.randperm(I.numel(), generator=torch.Generator().manual_seed(5))]
+    nJ = 3000
+    J = synth.random_subset(n, nJ, 5, 2)
+    lens = rng.choice([0, 1, 31, 32], size=I.numel())
+    lens[rng.integers(0, I.numel())] = longest
+    r = np.repeat(np.arange(I.numel()), lens)
+    c = np.concatenate([np.sort(rng.choice(nJ, L, replace=False)) for L in lens]).astype(np.int64)
+    v = rng.random(r.shape[0]).astype(np.float32)
+    Bo = oracle.build_csr(I.numel(), nJ, r, c, v)
+    Bd = from_oracle(Bo)
+    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), Bd)
+    assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), Bo), f"assign, longest B row {longest}")
+    E = ctx.sp_extract(Ap, I.cuda(), J.cuda())
+    assert_same(E, Bo, "extract after assign")
+
+
 def _union_b(A, I, J, seed, kind):
     """B of |I| x |J|: every entry of A(I, J) with a fresh value, plus random others, so
     the union modes meet both B entries that hit A and B entries that do not."""
