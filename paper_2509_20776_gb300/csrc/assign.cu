@@ -13,6 +13,7 @@
 // one load-balanced gather then assembles A' from A's untouched rows and the staged
 // rows.
 #include "dispatch.h"
+#include "extract_rows.cuh"
 #include "kernels.cuh"
 #include "plan.h"
 #include "rowsort.cuh"
@@ -24,6 +25,8 @@ template <class RP, class CIt, class VTt, class IX>
 struct AssignLoader {
   using CI = CIt;
   using VT = VTt;
+  // rows go to the CTA kernels by A's run alone, as the REPLACE count lists them
+  static constexpr bool kLongFirst = true;
   const RP* rpA;
   const CI* colA;
   const VT* valA;
@@ -243,6 +246,26 @@ __global__ void k_max_row_len(const long long* __restrict__ rp, long long n, uns
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
+// REPLACE count (k_xcount over A's runs): an entry of A survives unless its column is
+// assigned; the rebuilt row adds all of B's row, so the row pointer's scan adds it.
+struct AssignKeep {
+  const uint32_t* jbits;
+  long long n;
+  __device__ __forceinline__ bool test(long long c) const {
+    return c >= 0 && c < n && !((ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u);
+  }
+  __device__ __forceinline__ bool map(long long c, uint32_t& key) const {
+    if (!test(c)) return false;
+    key = uint32_t(c);
+    return true;
+  }
+};
+struct RebuiltLen {
+  const long long* kept;  // kept entries of A's run
+  const long long* rpB;
+  __device__ long long operator()(long long i) const { return kept[i] + (rpB[i + 1] - rpB[i]); }
+};
+
 // ---- rebuilt rows by merging (REPLACE, rows of B of at most 32 entries) ------------------
 // Row I[i] of A' is the merge of two sorted runs: A's row without the columns of J
 // (ascending already: A is canonical) and B's row i relabelled through J (at most 32
@@ -265,13 +288,12 @@ __device__ __forceinline__ int warp_lower_bound(uint32_t v, uint32_t key) {
   return pos + ((pos < 32 && x < key) ? 1 : 0);
 }
 
-// Ascending bitonic sort of (key, value) over the warp's 32 lanes.
+// Ascending bitonic sort of (key, value) over the warp's first P lanes (P a power of two,
+// the same in every lane; lanes at and above P hold only padding keys).
 template <class VT>
-__device__ __forceinline__ void warp_sort32(uint32_t& k, VT& v) {
+__device__ __forceinline__ void warp_sort(uint32_t& k, VT& v, int P) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
+  for (int size = 2; size <= P; size <<= 1) {
     for (int j = size >> 1; j > 0; j >>= 1) {
       const uint32_t ok = __shfl_xor_sync(0xffffffffu, k, j);
       const VT ov = __shfl_xor_sync(0xffffffffu, v, j);
@@ -295,18 +317,14 @@ struct MergeSrc {
   const IX* I;
   const IX* J;
   const uint32_t* jbits;
+  const long long* rs0;  // A's run of every row of I, recorded by the count
+  const long long* rsn;
   long long m, n, nnzA, nJ, nnzB;
-  // A's row I[i] and B's row i (ranges validated as the count's loader does)
+  // A's row I[i] (as the count resolved it) and B's row i (range validated)
   __device__ void rows(long long i, long long& sA, long long& LA, long long& sB, long long& LB) const {
-    sA = LA = sB = LB = 0;
-    const long long r = (long long)I[i];
-    if (r >= 0 && r < m) {
-      const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
-      if (s >= 0 && e >= s && e <= nnzA) {
-        sA = s;
-        LA = e - s;
-      }
-    }
+    sA = rs0[i];
+    LA = rsn[i];
+    sB = LB = 0;
     const long long s = rpB[i], e = rpB[i + 1];
     if (s >= 0 && e >= s && e <= nnzB) {
       sB = s;
@@ -327,7 +345,8 @@ struct MergeSrc {
         bv = valB[sB + lane];
       }
     }
-    warp_sort32(bk, bv);
+    const int P = LB <= 2 ? 2 : 1 << (32 - __clz(int(LB) - 1));
+    warp_sort(bk, bv, P);
     return __popc(__ballot_sync(0xffffffffu, bk != kPadKey));
   }
   __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
@@ -345,7 +364,7 @@ __global__ void __launch_bounds__(256) k_assign_merge_warp(MergeSrc<RP, CI, VT, 
   for (long long i = w0; i < nI; i += nw) {
     long long sA, LA, sB, LB;
     ms.rows(i, sA, LA, sB, LB);
-    if (LA + LB > SRC_LONG) continue;  // k_assign_merge_long (the count listed it)
+    if (LA > SRC_LONG) continue;  // k_assign_merge_long (the count listed it)
     const long long o = vp[i], oe = vp[i + 1];
     uint32_t bk;
     VT bv;
@@ -497,6 +516,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_s2 = cv.reserve(scan_ws_bytes(m));
   const bool merge = pl->mode != SP_ASSIGN_REPLACE;
   const size_t o_ji = cv.reserve(merge ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_r0 = cv.reserve(merge ? 0 : size_t(nI) * 8);  // REPLACE: A's run of every row of I
+  const size_t o_rn = cv.reserve(merge ? 0 : size_t(nI) * 8);
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
   cv.bind(pl->buf);
   IX* rowmap = cv.at<IX>(o_rm);
@@ -508,6 +529,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   pl->rpB = cv.at<long long>(o_rb);
   pl->cl_rows = cv.at<long long>(o_cl);
   pl->counters = cv.at<unsigned>(o_cn);
+  pl->sstart = merge ? nullptr : cv.at<long long>(o_r0);
+  pl->slen = merge ? nullptr : cv.at<long long>(o_rn);
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
   SP_CUDA(cudaMemsetAsync(rowmap, 0xFF, size_t(m) * sizeof(IX), s));
@@ -569,14 +592,34 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
           static_cast<const CI*>(B.colidx), nullptr, I, J, jinv, jbits, m, n, A.nnz, nJ, B.nnz,
           pl->mode == SP_ASSIGN_PLUS ? 1 : 0}));
     } else {
-      SP_TRY(count(AssignLoader<RP, CI, uint32_t, IX>{static_cast<const RP*>(A.rowptr),
-                                                      static_cast<const CI*>(A.colidx), nullptr, pl->rpB,
-                                                      static_cast<const CI*>(B.colidx), nullptr, I, J,
-                                                      jbits, m, n, A.nnz, nJ, B.nnz}));
+      // REPLACE: the surviving entries of A's runs, lane-per-row (k_xcount; runs of more
+      // than SRC_LONG entries listed for one CTA each); B's rows are added by the scan
+      const AssignKeep keep{jbits, n};
+      const CI* colA = static_cast<const CI*>(A.colidx);
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        const XOne<CI, uint32_t, AssignKeep> src{colA, nullptr, keep};
+        const XResolveI<RP, IX> res{static_cast<const RP*>(A.rowptr), I, m, A.nnz, pl->sstart, pl->slen,
+                                    ctx->dstatus};
+        k_xcount<<<grid_for((nI + 31) / 32 * 32, XB, nsm * 8), XB, 0, s>>>(
+            src, res, nI, pl->vp, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->counters + 4, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
+      {
+        SP_PHASE(SP_PHASE_COUNT);
+        const XLongRows<CI, uint32_t, AssignKeep> lr{colA, nullptr, keep, pl->sstart, pl->slen};
+        k_count_long<<<nsm, 1024, 0, s>>>(lr, pl->vp, cl, pl->counters + 3, ctx->dstatus);
+      }
+      SP_CUDA(cudaGetLastError());
     }
   }
-  SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
-                     StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_s1)));
+  if (merge) {
+    SP_TRY(launch_scan(ctx, s, LoadArray<long long>{pl->vp},
+                       StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI, cv.at<char>(o_s1)));
+  } else {
+    SP_TRY(launch_scan(ctx, s, RebuiltLen{pl->vp, pl->rpB}, StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI,
+                       cv.at<char>(o_s1)));
+  }
   AssignLen<RP, IX> len{static_cast<const RP*>(A.rowptr), rowmap, pl->vp, A.nnz};
   SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{pl->vp_out, nullptr, ctx->dstatus}, m,
                      cv.at<char>(o_s2)));
@@ -659,8 +702,8 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
     const MergeSrc<RP, CI, VT, IX> ms{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
                                      static_cast<const VT*>(A.values), pl->rpB, static_cast<const CI*>(B.colidx),
                                      static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
-                                     static_cast<const IX*>(pl->J), static_cast<const uint32_t*>(pl->jmap), A.nrows,
-                                     A.ncols, A.nnz, pl->nJ, B.nnz};
+                                     static_cast<const IX*>(pl->J), static_cast<const uint32_t*>(pl->jmap), pl->sstart,
+                                     pl->slen, A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz};
     unsigned* ticket = cv.at<unsigned>(o_tk);
     SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
     const int nsm = ctx->num_sms;

@@ -147,7 +147,7 @@ __global__ void k_count_warp(Ct ct, long long nlisted, long long* __restrict__ c
         cl.rsn[i] = rs[u].n0;
       }
       Ls[u] = rs[u].n0 + rs[u].n1;
-      lng[u] = Ls[u] > SRC_LONG;
+      lng[u] = row_is_long<Ct>(rs[u]);
       bt.valid[u] = !lng[u] && lane < Ls[u];
       bt.set_row(u, i);
       if (bt.valid[u]) bt.at(u, rs[u], lane);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(Ld ld, long long nlisted, 
       o[u] = mine ? vp[i] : 0;
       oe[u] = mine ? vp[i + 1] : 0;
       Ls[u] = rs[u].n0 + rs[u].n1;
-      lng[u] = Ls[u] > SRC_LONG;
+      lng[u] = row_is_long<Ld>(rs[u]);
       bt.valid[u] = !lng[u] && lane < Ls[u];
       bt.set_row(u, i);
       if (bt.valid[u]) bt.at(u, rs[u], lane);

@@ -23,6 +23,8 @@
 // U independent chains of dependent loads are in flight per thread.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sp {
@@ -132,5 +134,16 @@ struct CountOnly {
 // Rows whose source holds more than SRC_LONG entries are "source-long": the count and
 // fill passes give each of them a whole CTA instead of a warp.
 constexpr int SRC_LONG = 1024;
+
+// Whether a row goes to the CTA-per-row kernels by the length of its first run alone (a
+// loader declares kLongFirst = true; by default both runs count).
+template <class Ld, class = void>
+struct long_by_first : std::false_type {};
+template <class Ld>
+struct long_by_first<Ld, std::void_t<decltype(Ld::kLongFirst)>> : std::bool_constant<Ld::kLongFirst> {};
+template <class Ld>
+__device__ __forceinline__ bool row_is_long(const RowSrc& rs) {
+  return (long_by_first<Ld>::value ? rs.n0 : rs.n0 + rs.n1) > SRC_LONG;
+}
 
 }  // namespace sp
