@@ -176,64 +176,87 @@ struct AssignMergeLoader {
   }
 };
 
-// length of row r of A': untouched rows keep len_A, rows of I take the rebuilt length
-template <class RP, class IX>
+// length of row r of A': len_A plus a correction that is non-zero only on rows of I
+// (rebuilt length - len_A, scattered by k_assign_delta), so the scan reads two dense
+// arrays and no map
+template <class RP>
+__device__ __forceinline__ long long len_a(const RP* rpA, long long r, long long nnzA) {
+  const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
+  return (s >= 0 && e >= s && e <= nnzA) ? e - s : 0;
+}
+template <class RP>
 struct AssignLen {
   const RP* rpA;
-  const IX* rowmap;
-  const long long* vt;  // row pointer of the rebuilt rows
+  const int* delta;
   long long nnzA;
-  __device__ long long operator()(long long r) const {
-    const long long i = (long long)rowmap[r];
-    if (i >= 0) return vt[i + 1] - vt[i];
-    const long long s = (long long)rpA[r], e = (long long)rpA[r + 1];
-    return (s >= 0 && e >= s && e <= nnzA) ? e - s : 0;
-  }
+  __device__ long long operator()(long long r) const { return len_a(rpA, r, nnzA) + (long long)delta[r]; }
 };
+template <class RP, class IX>
+__global__ void k_assign_delta(const IX* __restrict__ I, long long nI, const RP* __restrict__ rpA, long long m,
+                               long long nnzA, const long long* __restrict__ vt, int* __restrict__ delta,
+                               DevStatus* st) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nI;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = (long long)I[i];
+    if (r < 0 || r >= m) continue;  // reported by the row map
+    const long long d = (vt[i + 1] - vt[i]) - len_a(rpA, r, nnzA);
+    if (d > 0x7fffffffll || d < -0x7fffffffll) dev_fail(st, SP_ERR_OVERFLOW, i);
+    else delta[r] = int(d);
+  }
+}
 
 // Assembly of A' as segments (segcopy.cuh): a segment starts at row 0, at every row of I
 // and after every row of I; a run of rows outside I is contiguous in A and in A', a row
-// of I is its staged rebuilt row.  The scan over the rows numbers the segment starts; its
-// store writes each segment (first output position, source position) and the count.
-template <class IX>
-struct SegStart {
-  const IX* rowmap;
-  __device__ bool operator()(long long r) const {
-    return r == 0 || (long long)rowmap[r] >= 0 || (long long)rowmap[r - 1] >= 0;
-  }
-};
-template <class IX>
-struct SegCount {
-  SegStart<IX> st;
-  __device__ long long operator()(long long r) const { return st(r) ? 1 : 0; }
+// of I is its staged rebuilt row.  The scan over the bitmap words of I's rows numbers the
+// segment starts (32 rows per element); its store writes each segment (first output
+// position, source position) and the count.
+__device__ __forceinline__ uint32_t seg_starts(const uint32_t* ibits, long long w, long long m) {
+  const uint32_t b = ibits[w], prev = w > 0 ? ibits[w - 1] >> 31 : 1u;  // row 0 starts one
+  uint32_t s = b | (b << 1) | prev;
+  const long long r0 = w * 32;
+  if (m - r0 < 32) s &= (1u << (m - r0)) - 1u;  // rows past the last do not start one
+  return s;
+}
+struct SegWordCount {
+  const uint32_t* ibits;
+  long long m;
+  __device__ long long operator()(long long w) const { return __popc(seg_starts(ibits, w, m)); }
 };
 template <class RP, class IX>
-struct SegStore {
-  SegStart<IX> st;
+struct SegWordStore {
+  const uint32_t* ibits;
   const IX* rowmap;
   const RP* rpA;
   const long long* vt;  // row pointer of the staged rebuilt rows
   const long long* vp_out;
   CopySeg* segs;
-  long long m, cap;
+  long long m, nw, cap;
   long long* nseg;
   DevStatus* dst;
-  __device__ void operator()(long long r, long long j) const {
-    if (j > cap) {
-      dev_fail(dst, SP_ERR_INTERNAL, -33);
-      return;
-    }
-    if (r == m) {  // j = number of segments; the sentinel closes the last one
+  __device__ void operator()(long long w, long long j) const {
+    if (w == nw) {  // j = number of segments; the sentinel closes the last one
+      if (j > cap) {
+        dev_fail(dst, SP_ERR_INTERNAL, -33);
+        return;
+      }
       *nseg = j;
       segs[j] = CopySeg{vp_out[m], 0};
       return;
     }
-    if (!st(r)) return;
-    const long long i = (long long)rowmap[r];
-    segs[j] = CopySeg{vp_out[r], i >= 0 ? (vt[i] | kSegB) : (long long)rpA[r]};
+    uint32_t sm = seg_starts(ibits, w, m);
+    const uint32_t b = ibits[w];
+    while (sm) {
+      const int k = __ffs(sm) - 1;
+      sm &= sm - 1;
+      if (j >= cap) {
+        dev_fail(dst, SP_ERR_INTERNAL, -36);
+        return;
+      }
+      const long long r = w * 32 + k;
+      segs[j++] = CopySeg{vp_out[r], ((b >> k) & 1u) ? (vt[(long long)rowmap[r]] | kSegB) : (long long)rpA[r]};
+    }
   }
 };
-
 // Longest row of B (row pointer rpB, n rows), saturated at 2^32 - 1.
 __global__ void k_max_row_len(const long long* __restrict__ rp, long long n, unsigned* out) {
   unsigned mx = 0;
@@ -408,8 +431,9 @@ __global__ void __launch_bounds__(256) k_assign_merge_warp(MergeSrc<RP, CI, VT, 
 }
 
 // Rows of more than SRC_LONG source entries (the count's list), one 1024-thread CTA each:
-// every warp takes 32 consecutive entries of a slice, the kept ranks are scanned across
-// the block, and each warp's counts of kept entries below the B' keys are added up.
+// a step takes LOAD_U x 1024 consecutive entries, warp w of slice u the 32 entries at
+// u * 1024 + 32 w; the kept counts of the step's LOAD_U x 32 chunks are scanned once, in
+// chunk order, and each warp's counts of kept entries below the B' keys are added up.
 template <class RP, class CI, class VT, class IX>
 __global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT, IX> ms,
                                                             const long long* __restrict__ cl_rows,
@@ -417,9 +441,10 @@ __global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT,
                                                             const long long* __restrict__ vp, unsigned* ticket,
                                                             CI* __restrict__ tcol, VT* __restrict__ tval,
                                                             DevStatus* st) {
-  constexpr int NW = 1024 / 32;
+  constexpr int NW = 1024 / 32, NCH = NW * LOAD_U;  // chunks of one step
+  static_assert(NCH % 32 == 0 && NCH <= 32 * 32, "one warp scans a step's chunks");
   __shared__ unsigned s_item;
-  __shared__ unsigned s_wc[NW], s_wx[NW], s_tot, s_cnt[32];
+  __shared__ unsigned s_wc[NCH], s_tot, s_cnt[32];
   __shared__ long long s_base;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -443,40 +468,57 @@ __global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT,
     const int nb = ms.load_b(sB, LB, bk, bv);
     unsigned cntA = 0;
     for (long long e0 = 0; e0 < LA; e0 += (long long)blockDim.x * LOAD_U) {
+      long long cc[LOAD_U];
+      VT vv[LOAD_U];
+      unsigned km[LOAD_U];
+      int nless[LOAD_U];
 #pragma unroll
       for (int u = 0; u < LOAD_U; ++u) {
-        const long long e = e0 + (long long)u * blockDim.x + t;  // warp w: 32 consecutive entries
+        const long long e = e0 + (long long)u * blockDim.x + t;
         const bool valid = e < LA;
-        const long long c = valid ? (long long)ld_stream(ms.colA + sA + e) : 0;
-        const bool kept = valid && c >= 0 && c < ms.n && !ms.in_j(c);
-        VT v;
-        if (kept) v = ld_stream(ms.valA + sA + e);
-        const unsigned km = __ballot_sync(0xffffffffu, kept);
-        const uint32_t ck = valid ? uint32_t(c) : kPadKey;
-        const int nless = warp_lower_bound(bk, ck);
+        cc[u] = valid ? (long long)ld_stream(ms.colA + sA + e) : 0;
+        const bool kept = valid && cc[u] >= 0 && cc[u] < ms.n && !ms.in_j(cc[u]);
+        if (kept) vv[u] = ld_stream(ms.valA + sA + e);
+        km[u] = __ballot_sync(0xffffffffu, kept);
+        const uint32_t ck = valid ? uint32_t(cc[u]) : kPadKey;
+        nless[u] = warp_lower_bound(bk, ck);
         const int lbc = warp_lower_bound(ck, bk);
-        cntA += __popc(km & (lbc >= 32 ? 0xffffffffu : ((1u << lbc) - 1u)));
-        if (lane == 0) s_wc[w] = __popc(km);
-        __syncthreads();
-        if (w == 0) {
-          const unsigned x = s_wc[lane];
-          const unsigned inc = warp_incl_sum(x);
-          s_wx[lane] = inc - x;
-          if (lane == NW - 1) s_tot = inc;
-        }
-        __syncthreads();
-        if (kept) {
-          const long long pos = o + s_base + s_wx[w] + __popc(km & lt) + nless;
-          if (pos < oe) {
-            st_stream(tcol + pos, CI(c));
-            st_stream(tval + pos, v);
-          } else {
-            dev_fail(st, SP_ERR_INTERNAL, -33);
-          }
-        }
-        __syncthreads();
-        if (t == 0) s_base += s_tot;
+        cntA += __popc(km[u] & (lbc >= 32 ? 0xffffffffu : ((1u << lbc) - 1u)));
+        if (lane == 0) s_wc[u * NW + w] = __popc(km[u]);
       }
+      __syncthreads();
+      if (w == 0) {  // exclusive prefix of the step's chunk counts, in chunk order
+        constexpr int PER = NCH / 32;
+        unsigned x[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          x[q] = s_wc[lane * PER + q];
+          sum += x[q];
+        }
+        const unsigned inc = warp_incl_sum(sum);
+        unsigned run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          s_wc[lane * PER + q] = run;
+          run += x[q];
+        }
+        if (lane == 31) s_tot = inc;
+      }
+      __syncthreads();
+      const long long base = s_base;
+#pragma unroll
+      for (int u = 0; u < LOAD_U; ++u) {
+        if (!((km[u] >> lane) & 1u)) continue;
+        const long long pos = o + base + s_wc[u * NW + w] + __popc(km[u] & lt) + nless[u];
+        if (pos < oe) {
+          st_stream(tcol + pos, CI(cc[u]));
+          st_stream(tval + pos, vv[u]);
+        } else {
+          dev_fail(st, SP_ERR_INTERNAL, -33);
+        }
+      }
+      __syncthreads();  // every thread has read s_base and s_wc
+      if (t == 0) s_base += s_tot;
     }
     atomicAdd(&s_cnt[lane], cntA);
     __syncthreads();
@@ -516,6 +558,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   const size_t o_s2 = cv.reserve(scan_ws_bytes(m));
   const bool merge = pl->mode != SP_ASSIGN_REPLACE;
   const size_t o_ji = cv.reserve(merge ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_dl = cv.reserve(size_t(m) * 4);                 // row-length corrections on rows of I
+  const size_t o_ib = cv.reserve(size_t((m + 31) / 32) * 4);      // bitmap of I's rows
   const size_t o_r0 = cv.reserve(merge ? 0 : size_t(nI) * 8);  // REPLACE: A's run of every row of I
   const size_t o_rn = cv.reserve(merge ? 0 : size_t(nI) * 8);
   SP_TRY(plan_alloc(ctx, pl, cv.total(), s));
@@ -529,17 +573,27 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   pl->rpB = cv.at<long long>(o_rb);
   pl->cl_rows = cv.at<long long>(o_cl);
   pl->counters = cv.at<unsigned>(o_cn);
+  pl->ibits = cv.at<uint32_t>(o_ib);
+  int* delta = cv.at<int>(o_dl);
   pl->sstart = merge ? nullptr : cv.at<long long>(o_r0);
   pl->slen = merge ? nullptr : cv.at<long long>(o_rn);
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(pl->counters, 0, 64, s));
   SP_CUDA(cudaMemsetAsync(rowmap, 0xFF, size_t(m) * sizeof(IX), s));
   SP_CUDA(cudaMemsetAsync(jbits, 0, size_t((n + 31) / 32) * 4, s));
+  SP_CUDA(cudaMemsetAsync(pl->ibits, 0, size_t((m + 31) / 32) * 4, s));
+  SP_CUDA(cudaMemsetAsync(delta, 0, size_t(m) * 4, s));
   if (nI > 0) {
     {
       SP_PHASE(SP_PHASE_MAP);
       k_inverse_map<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, rowmap, ctx->dstatus,
                                                                     SP_ERR_DUPLICATE_INDEX);
+    }
+    SP_CUDA(cudaGetLastError());
+    {
+      SP_PHASE(SP_PHASE_MAP);
+      k_mark_bits<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, pl->ibits, ctx->dstatus,
+                                                                  SP_ERR_DUPLICATE_INDEX);
     }
     SP_CUDA(cudaGetLastError());
   }
@@ -620,7 +674,13 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
     SP_TRY(launch_scan(ctx, s, RebuiltLen{pl->vp, pl->rpB}, StoreDual<long long>{pl->vp, nullptr, ctx->dstatus}, nI,
                        cv.at<char>(o_s1)));
   }
-  AssignLen<RP, IX> len{static_cast<const RP*>(A.rowptr), rowmap, pl->vp, A.nnz};
+  if (nI > 0) {
+    SP_PHASE(SP_PHASE_SCAN);
+    k_assign_delta<RP, IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, static_cast<const RP*>(A.rowptr), m,
+                                                                      A.nnz, pl->vp, delta, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
+  AssignLen<RP> len{static_cast<const RP*>(A.rowptr), delta, A.nnz};
   SP_TRY(launch_scan(ctx, s, len, StoreDual<long long>{pl->vp_out, nullptr, ctx->dstatus}, m,
                      cv.at<char>(o_s2)));
   SP_CUDA(cudaMemcpyAsync(pl->h_tail, pl->vp_out + m, 8, cudaMemcpyDeviceToHost, s));
@@ -731,11 +791,11 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   CopySeg* segs = cv.at<CopySeg>(o_sg);
   long long* nseg = cv.at<long long>(o_ns);
   long long* chunk_first = cv.at<long long>(o_cf);
-  const SegStart<IX> st{rowmap};
-  SP_TRY(launch_scan(ctx, s, SegCount<IX>{st},
-                     SegStore<RP, IX>{st, rowmap, static_cast<const RP*>(A.rowptr), pl->vp, pl->vp_out, segs, m,
-                                      segcap, nseg, ctx->dstatus},
-                     m, cv.at<char>(o_sc), SP_PHASE_PARTITION));
+  const long long nw = (m + 31) / 32;
+  SP_TRY(launch_scan(ctx, s, SegWordCount{pl->ibits, m},
+                     SegWordStore<RP, IX>{pl->ibits, rowmap, static_cast<const RP*>(A.rowptr), pl->vp, pl->vp_out,
+                                          segs, m, nw, segcap, nseg, ctx->dstatus},
+                     nw, cv.at<char>(o_sc), SP_PHASE_PARTITION));
   const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(chunk_first, 0xFF, size_t(nchunks) * 8, s));
   {

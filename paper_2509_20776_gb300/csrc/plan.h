@@ -19,6 +19,7 @@ struct sp_plan {
   // device pointers inside buf
   void* jmap = nullptr;        // extraction: jinv (nJ positions); assignment: J bitmap
   void* rowmap = nullptr;      // assignment: rowmap (m entries of idx type)
+  uint32_t* ibits = nullptr;   // assignment: bitmap of I's rows (m bits)
   void* jbits = nullptr;       // extraction: membership bitmap of J
   void* jinv = nullptr;        // assignment (union modes): column -> position in J
   long long* vp = nullptr;     // extraction: row pointer of B; assignment: of rows I (temp)
