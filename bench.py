@@ -536,7 +536,7 @@ def e2e_permute(ctx, A, ops, args, ws):
         for st in cps:
             main.wait_stream(st)
 
-    steps = max(1, args.steps // 2)
+    steps = max(1, args.steps)
     step()  # warm-up
     drain()
     torch.cuda.synchronize()
