@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--lookup-sweep", action="store_true",
                     help="print the measured rate of uniform random 4-byte lookups per table size and exit")
+    ap.add_argument("--profile-case", default="", choices=["", "assign-rmat24", "extract-er23"],
+                    help="one small operation for a one-kernel ncu capture (no bench line): the "
+                         "assignment on R-MAT scale 24 ef 24 with |I| = |J| = 2^20, or the extraction "
+                         "of half the rows and columns of ER 2^23 x 32")
     ap.add_argument("--rows-limit", type=int, default=0,
                     help="profiling case: R random rows of the headline matrix (all columns), "
                          "one permutation with independent random p, q; prints its line and exits")
@@ -325,6 +329,46 @@ def run_rows_limited(args, ctx, holder, dev):
     ctx.sync()
     return {"rows_limit": R, "ncols": Ar.ncols, "nnz": Ar.nnz, "ms_per_op": round(ms / max(1, args.steps), 4),
             "workload": "R random rows of the headline matrix, all columns; P A Q^T with random p, q"}
+
+
+def profile_case(args):
+    """--profile-case: the named operation, twice (the second for the capture), at a size
+    whose device footprint stays at a few GB; prints its phase times."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2509_20776_gb300 import CSR, Context, SP_OPT_TIMING
+    dev = torch.device("cuda", 0)
+    ctx = Context(0)
+    if args.profile_case == "assign-rmat24":
+        A = synth.rmat_csr(24, 24, (0.57, 0.19, 0.19, 0.05), seed=0, symmetrize=False, value_kind="f32u01",
+                           rowptr_dtype=torch.int64, colidx_dtype=torch.int32, device=dev)
+        k = 1 << 20
+        Bm = synth.er_csr(k, k, 8, seed=1, value_kind="f32u01", rowptr_dtype=torch.int64,
+                          colidx_dtype=torch.int32, device=dev)
+        I = synth.random_subset(A.nrows, k, 4, 1, device=dev)
+        J = synth.random_subset(A.ncols, k, 4, 2, device=dev)
+        Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
+        Bd = CSR(Bm.nrows, Bm.ncols, Bm.rowptr, Bm.colidx, Bm.values)
+        run = lambda: ctx.sp_assign(Ad, I, J, Bd)  # noqa: E731
+    else:
+        n = 1 << 23
+        A = synth.er_csr(n, n, 32, seed=0, value_kind="f32u01", rowptr_dtype=torch.int64,
+                         colidx_dtype=torch.int32, device=dev)
+        I = synth.random_subset(n, n // 2, 3, 1, device=dev)
+        J = synth.random_subset(n, n // 2, 3, 2, device=dev)
+        Ad = CSR(A.nrows, A.ncols, A.rowptr, A.colidx, A.values)
+        run = lambda: ctx.sp_extract(Ad, I, J)  # noqa: E731
+    for _ in range(2):
+        ctx.set_option(SP_OPT_TIMING, 1)
+        ctx.phase_stats(reset=True)
+        out = run()
+        ctx.sync()
+        st = ctx.phase_stats(reset=True)
+        log(f"{args.profile_case}: {out.nnz} entries, phases (ms) " +
+            str({k: round(v[0], 3) for k, v in st.items() if v[1]}))
+        del out
 
 
 def log_summary(res):
@@ -1156,6 +1200,9 @@ def main():
     args = parse()
     if args.lookup_sweep:
         print(json.dumps(lookup_sweep()), flush=True)
+        return
+    if args.profile_case:
+        profile_case(args)
         return
     ws, rank, local = dist_init()
     if args.impl == "reference":
