@@ -34,7 +34,7 @@ namespace sp {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int XFAST = 64;     // rows of at most this many source entries: masks, warp sort
 constexpr int XC_ROWS = 6;    // rows whose columns a counting warp loads together
-constexpr int XF_ROWS = 4;    // rows whose kept entries a filling warp loads together
+constexpr int XF_ROWS = 2;    // rows whose kept entries a filling warp loads together
 constexpr int XB = 256;       // threads per CTA of the count / fill
 constexpr unsigned kDropped = 0xFFFFFFFFu;  // padding key: never below a key
 
@@ -313,7 +313,7 @@ __device__ __forceinline__ void x_queue(long long o, long long k, int key_bits, 
 // kSorted: the relabelling keeps the source order (ascending J), so slots are ranks and
 // no row is queued.
 template <class Src, bool kSorted>
-__global__ void __launch_bounds__(XB, 3) k_xfill(Src src, long long nI, const long long* __restrict__ rs0,
+__global__ void __launch_bounds__(XB, 4) k_xfill(Src src, long long nI, const long long* __restrict__ rs0,
                                                 const long long* __restrict__ rsn, const long long* __restrict__ vp,
                                                 typename Src::CI* __restrict__ out_col,
                                                 typename Src::VT* __restrict__ out_val, FinalEntry* fin,
