@@ -72,6 +72,8 @@ struct HugeEntry {  // a run longer than SS_RUN_MAX; coarse split: keys in [lo, 
 constexpr int GC_BLOCK = 256;                  // gather: threads per CTA
 constexpr int GC_CH = 4096;                    // gather: output positions per CTA
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
+constexpr int GC_MINB = 5;                     // gather: resident CTAs per SM (persistent grid)
+constexpr int GC_H = 4;                        // gather: positions a thread loads before it stores
 
 // ---- partition ----------------------------------------------------------------------
 // Row r weighs SS_ROW_W plus its length when a tile sorts it (length <= tmax, the tile
@@ -211,7 +213,7 @@ __device__ void smem_incl_max_w(uint32_t* a, int n, uint32_t* tmp) {
 //     __device__ typename Gs::CI map(long long pos, typename Gs::CI c) const;  // new column
 //     __device__ typename Gs::VT val(long long pos) const;
 template <class Gs>
-__global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
+__global__ void __launch_bounds__(GC_BLOCK, GC_MINB) k_gather_chunks(Gs gs, const long long* __restrict__ vp,
                                                             long long nrows, long long total,
                                                             const long long* __restrict__ chunk_first,
                                                             long long nchunks,
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(GC_BLOCK, 4) k_gather_chunks(Gs gs, const long
     long long n0 = 0, n1 = 0, ns = 0;
     if (more) setup(rb_next + t, n0, n1, ns);
     // all loads, then all stores (the compiler cannot move stores above later loads)
-    constexpr int H = 8;
+    constexpr int H = GC_H;
 #pragma unroll
     for (int h = 0; h < ITEMS; h += H) {
       CI cv[H];
@@ -1144,7 +1146,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     if (w.nchunks > 0x7fffffffll) return SP_ERR_OVERFLOW;
     {
       SP_PHASE(SP_PHASE_GATHER);
-      const long long g = w.nchunks < 4ll * nsm ? w.nchunks : 4ll * nsm;  // persistent, 4 per SM
+      const long long g = w.nchunks < (long long)GC_MINB * nsm ? w.nchunks : (long long)GC_MINB * nsm;  // persistent
       k_gather_chunks<Gs><<<unsigned(g), GC_BLOCK, 0, s>>>(*gs, vp, nrows, nnz, w.chunk_first, w.nchunks,
                                                            out_col, out_val);
     }
