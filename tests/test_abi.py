@@ -44,3 +44,13 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.sp_ctx_create(None, 0, None) == 1
     assert lib.sp_permute(None, None, None, None, 0, None, None) == 1
     assert lib.sp_ctx_set_option(None, 0, 0) == 1
+
+
+def test_last_cuda_error_starts_clear(lib):
+    """No call has failed with SP_ERR_CUDA yet: code 0 and an empty location."""
+    lib.sp_last_cuda_error.restype = ctypes.c_int
+    lib.sp_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
+    where = ctypes.c_char_p()
+    assert lib.sp_last_cuda_error(ctypes.byref(where)) == 0
+    assert (where.value or b"") == b""
+    assert lib.sp_last_cuda_error(None) == 0
