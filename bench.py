@@ -551,9 +551,19 @@ def e2e_permute(ctx, A, ops, args, ws):
                 dst[a:b].copy_(src[a:b], non_blocking=True)
 
     done = [torch.cuda.Event()]  # the previous step's last permutation (no longer reads dA)
+    # results go to a ring of preallocated outputs, RING steps deep: a slot is written again
+    # only after its previous result copies have finished (bounded device memory however
+    # far the copies lag behind the permutations)
+    RING = 3
+    ring = [[CSR(A.nrows, A.ncols, torch.empty_like(dA[0]), torch.empty_like(dA[1]), torch.empty_like(dA[2]))
+             for _ in ops] for _ in range(RING)]
+    copied = [[None for _ in ops] for _ in range(RING)]  # events: the slot's copies are done
+    turn = [0]
 
     def step():
         main = torch.cuda.current_stream()
+        slot = turn[0] % RING
+        turn[0] += 1
         for st in cps_in:
             st.wait_event(done[0])
         for d, h in zip(dA, hA):
@@ -561,17 +571,23 @@ def e2e_permute(ctx, A, ops, args, ws):
         for st in cps_in:
             main.wait_stream(st)
         Ad = CSR(A.nrows, A.ncols, dA[0], dA[1], dA[2])
-        for (dp, dq), (hp, hq) in zip(dperm, hperm):
+        for j, ((dp, dq), (hp, hq)) in enumerate(zip(dperm, hperm)):
             dp.copy_(hp, non_blocking=True)
             if dq is not None:
                 dq.copy_(hq, non_blocking=True)
-            B = ctx.sp_permute(Ad, dp, dq if dq is not None else dp, sync=False)
+            for ev in copied[slot][j] or []:
+                main.wait_event(ev)
+            B = ctx.sp_permute(Ad, dp, dq if dq is not None else dp, sync=False, out=ring[slot][j])
             for st in cps:
                 st.wait_stream(main)
             for h, t in ((out_rp, B.rowptr), (out_ci, B.colidx), (out_v, B.values)):
                 pieces(h, t, cps)
-                for st in cps:
-                    t.record_stream(st)  # keep B's memory until its copies are done
+            evs = []
+            for st in cps:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                evs.append(ev)
+            copied[slot][j] = evs
         done[0] = torch.cuda.Event()
         done[0].record(main)
 
@@ -601,7 +617,8 @@ def e2e_permute(ctx, A, ops, args, ws):
     return {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": round(ms / steps, 3),
             "schedule": "steps overlap: result copies of a step run with the next step's input copy and "
-                        "permutations; the timed region ends after the last result copy"}
+                        "permutations (results in a ring of preallocated outputs three steps deep); the "
+                        "timed region ends after the last result copy"}
 
 
 def bench_extract(ctx, args, dev, hbm, ws):
