@@ -43,7 +43,7 @@ WORKLOAD = ("R-MAT scale {scale} (a,b,c,d)=(0.57,0.19,0.19,0.05), edge factor 16
 # relabel map keeps its full-size L2 pressure); scaled to a full launch by the entries
 # it moves (profiles/gather_dram_rmat25_rows2m.md).  Only valid for the kernel
 # as captured: retake the capture when it changes.
-GATHER_DRAM_BYTES_PER_ENTRY = 24.87  # 1 642 645 248 B over 66 045 976 entries
+GATHER_DRAM_BYTES_PER_ENTRY = 25.07  # 1 655 663 104 B over 66 045 976 entries
 
 _T0 = time.time()
 
