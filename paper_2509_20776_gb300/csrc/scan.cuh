@@ -27,7 +27,7 @@ struct ScanCtl {
 };
 
 template <class Load, class Store>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scan(Load load, Store store, ScanCtl c) {
+__global__ void __launch_bounds__(SCAN_BLOCK, 5) k_scan(Load load, Store store, ScanCtl c) {
   constexpr int B = SCAN_BLOCK, IT = SCAN_ITEMS, TILE = SCAN_TILE;
   __shared__ long long buf[TILE + TILE / 16];
   __shared__ long long tmp[B / 32 + 1];
