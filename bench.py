@@ -70,6 +70,9 @@ def parse():
                     help="one small operation for a one-kernel ncu capture (no bench line): the "
                          "assignment on R-MAT scale 24 ef 24 with |I| = |J| = 2^20, or the extraction "
                          "of half the rows and columns of ER 2^23 x 32")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the row sort's key-range split runs on the context's side "
+                         "stream, concurrent with the tile sort; 0: all on one stream")
     ap.add_argument("--rows-limit", type=int, default=0,
                     help="profiling case: R random rows of the headline matrix (all columns), "
                          "one permutation with independent random p, q; prints its line and exits")
@@ -417,9 +420,10 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2509_20776_gb300 import CSR, Context, SP_OPT_TIMING
+    from paper_2509_20776_gb300 import CSR, Context, SP_OPT_TIMING, SP_OPT_OVERLAP
     dev = torch.device("cuda", local)
     ctx = Context(local)
+    ctx.set_option(SP_OPT_OVERLAP, args.overlap)
     pk = peaks()
     hbm = pk["hbm_gbs"] if pk else 6800.0
     log("generating the permutation workload")

@@ -156,6 +156,14 @@ SP_API int sp_last_cuda_error(const char** where);
  *                          1); 1 = J sorted once, binary search per stored entry
  *                          (Algorithm 5's search: |J| log |J| set-up, no column-sized
  *                          table). */
+/* Scheduling (same output either way):
+ *   SP_OPT_OVERLAP         1 (default): a row sort that has both rows longer than 4096
+ *                          entries and tiles of short rows runs the long rows' key-range
+ *                          split on the context's own side stream (created with the
+ *                          device's highest stream priority) while the tiles are sorted
+ *                          on the caller's stream; the two are forked and joined with
+ *                          events, so the call stays ordered on the caller's stream and
+ *                          capturable; 0: every launch on the caller's stream. */
 typedef enum sp_option {
   SP_OPT_SPIN_LIMIT = 0,
   SP_OPT_SCAN_HOLD_TILE = 1,
@@ -166,7 +174,8 @@ typedef enum sp_option {
   SP_OPT_COUNT_ROWS = 6,
   SP_OPT_FILL_ROWS = 7,
   SP_OPT_BATCH_ROWS = 8,
-  SP_OPT_IDENTIFY = 9
+  SP_OPT_IDENTIFY = 9,
+  SP_OPT_OVERLAP = 10
 } sp_option;
 SP_API sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value);
 

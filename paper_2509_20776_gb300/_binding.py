@@ -23,6 +23,7 @@ SP_OPT_SPIN_LIMIT, SP_OPT_SCAN_HOLD_TILE, SP_OPT_VALIDATE, SP_OPT_TIMING = 0, 1,
 # kernel shapes (run-time; every value gives the same output)
 SP_OPT_TILE_SHAPE, SP_OPT_HEAVY, SP_OPT_COUNT_ROWS, SP_OPT_FILL_ROWS, SP_OPT_BATCH_ROWS = 4, 5, 6, 7, 8
 SP_OPT_IDENTIFY = 9
+SP_OPT_OVERLAP = 10
 SHAPE_OPTIONS = {"tile_shape": SP_OPT_TILE_SHAPE, "heavy": SP_OPT_HEAVY, "count_rows": SP_OPT_COUNT_ROWS,
                  "fill_rows": SP_OPT_FILL_ROWS, "batch_rows": SP_OPT_BATCH_ROWS, "identify": SP_OPT_IDENTIFY}
 SHAPE_VALUES = {"tile_shape": (0, 1), "heavy": (128, 256, 512, 1024, 2048, 4096), "count_rows": (1, 2, 3, 4),

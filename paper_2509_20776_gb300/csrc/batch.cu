@@ -518,7 +518,7 @@ sp_status batch_fill_body(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s,
       SP_PHASE(SP_PHASE_GATHER);
       const XBatchSrc<CI, VT> src{b->rreq, b->rv, b->jrp};
       k_xfill<XBatchSrc<CI, VT>, false><<<grid_for((rows + 31) / 32 * 32, XB, ctx->num_sms * 8), XB, 0, s>>>(
-          src, rows, b->rs0, b->rsn, b->vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+          src, rows, b->rs0, b->rsn, b->vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
           w.huge_cap, kb, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());

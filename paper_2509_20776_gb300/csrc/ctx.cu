@@ -149,14 +149,22 @@ sp_status sp_ctx_create(sp_ctx** out, int device, const sp_allocator* allocator)
     }
     cudaGetLastError();
   }
+  int prio_least = 0, prio_greatest = 0;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&ctx->dstatus, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&ctx->hstatus, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&ctx->hbuf, 16 * sizeof(long long)) != cudaSuccess ||
-      cudaMemset(ctx->dstatus, 0, sizeof(DevStatus)) != cudaSuccess) {
+      cudaMemset(ctx->dstatus, 0, sizeof(DevStatus)) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
+    if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     delete ctx;
     return SP_ERR_CUDA;
   }
@@ -173,6 +181,9 @@ sp_status sp_ctx_destroy(sp_ctx* ctx) {
   cudaFree(ctx->dstatus);
   cudaFreeHost(ctx->hstatus);
   cudaFreeHost(ctx->hbuf);
+  cudaStreamDestroy(ctx->side);
+  cudaEventDestroy(ctx->fork_ev);
+  cudaEventDestroy(ctx->join_ev);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -226,6 +237,10 @@ sp_status sp_ctx_set_option(sp_ctx* ctx, sp_option key, int64_t value) {
     case SP_OPT_IDENTIFY:
       if (value > 1) return SP_ERR_INVALID_ARG;
       ctx->opt.identify = value < 0 ? 0 : int(value);
+      return SP_OK;
+    case SP_OPT_OVERLAP:
+      if (value > 1) return SP_ERR_INVALID_ARG;
+      ctx->overlap = value < 0 ? 1 : int(value);
       return SP_OK;
   }
   return SP_ERR_INVALID_ARG;

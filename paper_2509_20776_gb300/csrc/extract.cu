@@ -431,11 +431,11 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
       const XOne<CI, VT, Rel> src{ci, vv, rel};
       if (sorted)
         k_xfill<XOne<CI, VT, Rel>, true><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
-                                                          w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+                                                          w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
                                                           w.huge_cap, kb, ctx->dstatus);
       else
         k_xfill<XOne<CI, VT, Rel>, false><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
-                                                           w.counters + 0, w.fin_cap, w.huge, w.counters + 1,
+                                                           w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
                                                            w.huge_cap, kb, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());

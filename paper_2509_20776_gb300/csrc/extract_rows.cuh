@@ -304,9 +304,7 @@ __device__ __forceinline__ void x_queue(long long o, long long k, int key_bits, 
     if (q < fin_cap) fin[q] = FinalEntry{o, k, BUF_OUT, 0};
     else dev_fail(st, SP_ERR_INTERNAL, -27);
   } else {
-    const unsigned q = atomicAdd(huge_n, 1u);
-    if (q < huge_cap) huge[q] = HugeEntry{o, k, 0u, key_bits, BUF_OUT, 0};
-    else dev_fail(st, SP_ERR_INTERNAL, -28);
+    queue_huge(huge, huge_n, huge_cap, HugeEntry{o, k, 0u, key_bits, BUF_OUT, 0}, st, -28);
   }
 }
 

@@ -27,6 +27,11 @@ struct sp_ctx {
   // buffer per context, so no call allocates page-locked memory (which would stop kernels
   // on other streams from running concurrently with later work)
   long long* hbuf = nullptr;
+  // a second stream of this context (highest priority) and the events that fork work onto
+  // it and join it back; overlap = 0 keeps every launch on the caller's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  int overlap = 1;
   int64_t spin_limit = int64_t(1) << 22;
   int64_t hold_tile = -1;
   int validate = 0;

@@ -69,6 +69,20 @@ struct HugeEntry {  // a run longer than SS_RUN_MAX; coarse split: keys in [lo, 
   int pad;
 };
 
+// The rows queued for the key-range split.  n[0] counts the rows queued at the front of
+// the list, n[1] the rows of at least SPLIT_HUB entries queued from its back; the split
+// hands out the back first, so that a hub row (one CTA for up to milliseconds) starts at
+// once instead of wherever the queueing order put it.  cap >= nnz / SS_RUN_MAX + 1 bounds
+// the number of rows longer than SS_RUN_MAX, so the two ends never meet.
+constexpr long long SPLIT_HUB = 1ll << 16;
+__device__ __forceinline__ void queue_huge(HugeEntry* list, unsigned* n, long long cap, const HugeEntry& e,
+                                           DevStatus* st, long long err) {
+  const bool hub = e.len >= SPLIT_HUB;
+  const unsigned q = atomicAdd(n + (hub ? 1 : 0), 1u);
+  if (q < cap) list[hub ? cap - 1 - q : q] = e;
+  else dev_fail(st, SP_ERR_INTERNAL, err);
+}
+
 constexpr int GC_BLOCK = 256;                  // gather: threads per CTA
 constexpr int GC_CH = 4096;                    // gather: output positions per CTA
 constexpr int GC_ITEMS = GC_CH / GC_BLOCK;
@@ -103,7 +117,7 @@ struct RowsPartition {
   unsigned* fin_n;
   long long fin_cap;
   HugeEntry* huge;  // rows for k_split
-  unsigned* huge_n;
+  unsigned* huge_n;  // two counts (queue_huge)
   long long huge_cap;
   int key_bits;
   int classify;  // list the rows that do not fit a tile (only when the rows are sorted)
@@ -136,9 +150,7 @@ struct RowsPartition {
         if (q < fin_cap) fin[q] = FinalEntry{o0, L, BUF_OUT, 0};
         else dev_fail(st, SP_ERR_INTERNAL, -15);
       } else {
-        const unsigned q = atomicAdd(huge_n, 1u);
-        if (q < huge_cap) huge[q] = HugeEntry{o0, L, 0u, key_bits, BUF_OUT, 0};
-        else dev_fail(st, SP_ERR_INTERNAL, -16);
+        queue_huge(huge, huge_n, huge_cap, HugeEntry{o0, L, 0u, key_bits, BUF_OUT, 0}, st, -16);
       }
     }
   }
@@ -405,14 +417,17 @@ __global__ void __launch_bounds__(S::B, S::MINB)
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ unsigned s_item;
   const int t = threadIdx.x;
-  unsigned count = *nruns_p;
-  if (count > runs_cap) count = unsigned(runs_cap);
+  // the list's back (rows of >= SPLIT_HUB entries) first, then its front
+  long long nb_ = nruns_p[1], nf_ = nruns_p[0];
+  if (nb_ > runs_cap) nb_ = runs_cap;
+  if (nf_ > runs_cap - nb_) nf_ = runs_cap - nb_;
+  const long long count = nb_ + nf_;
   for (;;) {
     if (t == 0) s_item = atomicAdd(ticket, 1u);
     __syncthreads();
-    const unsigned item = s_item;
+    const long long item = s_item;
     if (item >= count) break;
-    const HugeEntry he = runs[item];
+    const HugeEntry he = runs[item < nb_ ? runs_cap - 1 - item : item - nb_];
     const long long g0 = he.off, L = he.len;
     const int sbuf = he.buf;
     const int dbuf = sbuf == BUF_TEMP ? BUF_OUT : BUF_TEMP;
@@ -979,8 +994,9 @@ struct RowsWs {
   long long* tile_first = nullptr;
   long long* chunk_first = nullptr;
   long long* ntiles = nullptr;
-  unsigned* counters = nullptr;  // [0] fin_n [1] huge_n [2] nxt_n [3..4] tickets [5] spare
+  unsigned* counters = nullptr;  // [0] fin_n [1] spare [2] spare [3..4] tickets [5] spare
                                  // [6..7] heavy-run counts [8..9] zero (no tiles)
+                                 // [10..11] huge list counts [12..13] nxt list counts
   FinalEntry* fin = nullptr;
   HugeEntry* huge = nullptr;
   HugeEntry* nxt = nullptr;
@@ -988,6 +1004,8 @@ struct RowsWs {
   uint32_t* tkey = nullptr;
   void* tval = nullptr;
   char* scan_ws = nullptr;
+  unsigned* huge_n() const { return counters + 10; }
+  unsigned* nxt_n() const { return counters + 12; }
 };
 
 constexpr int kRowsSlots = 12;
@@ -1054,7 +1072,7 @@ struct NoGather {
   __device__ VT val(long long) const { return VT(0); }
 };
 
-// Key-range split of the rows queued in w.huge (counter 1) into runs queued in w.fin.
+// Key-range split of the rows queued in w.huge (counts w.huge_n()) into runs queued in w.fin.
 template <class CI, class VT>
 sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col, VT* out_val) {
   const int nsm = ctx->num_sms;
@@ -1065,8 +1083,8 @@ sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col
   {
     SP_PHASE(SP_PHASE_HUGE);
     k_split<SplitCoarse, CI, VT><<<SplitCoarse::MINB * nsm, SplitCoarse::B, csm, s>>>(
-        w.huge, w.counters + 1, w.huge_cap, w.counters + 3, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
-        w.fin_cap, w.nxt, w.counters + 2, w.nxt_cap, ctx->dstatus);
+        w.huge, w.huge_n(), w.huge_cap, w.counters + 3, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
+        w.fin_cap, w.nxt, w.nxt_n(), w.nxt_cap, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
   // the fine split: the coarse buckets that hold more than SS_RUN_MAX entries (skewed keys
@@ -1074,7 +1092,7 @@ sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col
   {
     SP_PHASE(SP_PHASE_HUGE);
     k_split<SplitFine, CI, VT><<<SplitFine::MINB * nsm, SplitFine::B, fsm, s>>>(
-        w.nxt, w.counters + 2, w.nxt_cap, w.counters + 4, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
+        w.nxt, w.nxt_n(), w.nxt_cap, w.counters + 4, w.tkey, tval, out_col, out_val, w.fin, w.counters + 0,
         w.fin_cap, w.nxt, w.counters + 5, 0, ctx->dstatus);
   }
   SP_CUDA(cudaGetLastError());
@@ -1115,8 +1133,8 @@ sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, 
   return SP_OK;
 }
 
-// Sorts in place the rows a caller queued itself in w.fin / w.huge (counters 0 and 1,
-// zeroed with the rest of w.counters before the caller queued them).
+// Sorts in place the rows a caller queued itself in w.fin / w.huge (counter 0 and
+// w.huge_n(), zeroed with the rest of w.counters before the caller queued them).
 template <class CI, class VT>
 sp_status sort_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, CI* out_col, VT* out_val) {
   SP_TRY((split_queued<CI, VT>(ctx, s, w, out_col, out_val)));
@@ -1132,7 +1150,7 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
   SP_CUDA(cudaMemsetAsync(w.counters, 0, 16 * 4, s));
   const int nsm = ctx->num_sms;
   unsigned* fin_n = w.counters + 0;
-  unsigned* huge_n = w.counters + 1;
+  unsigned* huge_n = w.huge_n();
   // kernel shapes of this call (context options or the tuning table)
   const bool large_tiles = ctx->cur.tile_shape == 1;
   const long long tmax = large_tiles ? SsTileL::CP : SsTile::CP;
@@ -1153,11 +1171,28 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
     SP_CUDA(cudaGetLastError());
   }
   if (!sort) return SP_OK;
-  if (nnz > SS_RUN_MAX) SP_TRY((split_queued<CI, VT>(ctx, s, w, out_col, out_val)));
-  // tiles, then the runs, then the heavy buckets queued by either
-  const unsigned* no_runs = w.counters + 8;
+  // The key-range split (rows longer than SS_RUN_MAX, queued by the partition) and the
+  // tile sort (rows of at most tmax) touch disjoint rows.  With the context's overlap on,
+  // the split runs on the context's side stream, whose higher priority dispatches its CTAs
+  // (a hub row's first) ahead of the tiles', while the tiles run on `s`: the SMs that the
+  // split's tail leaves idle take tiles.  The runs, which the split queues, wait for both.
   constexpr size_t tsm = ss_smem_bytes<SsTile, VT>(), lsm = ss_smem_bytes<SsTileL, VT>();
   SP_CUDA(set_smem(large_tiles ? k_seg_sort<SsTileL, CI, VT> : k_seg_sort<SsTile, CI, VT>, large_tiles ? lsm : tsm));
+  const bool fork = nnz > SS_RUN_MAX && ctx->overlap && ctx->side;
+  if (fork) {
+    SP_CUDA(cudaEventRecord(ctx->fork_ev, s));
+    SP_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
+    const sp_status st = split_queued<CI, VT>(ctx, ctx->side, w, out_col, out_val);
+    SP_CUDA(cudaEventRecord(ctx->join_ev, ctx->side));
+    if (st != SP_OK) {
+      SP_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+      return st;
+    }
+  } else if (nnz > SS_RUN_MAX) {
+    SP_TRY((split_queued<CI, VT>(ctx, s, w, out_col, out_val)));
+  }
+  // tiles, then the runs, then the heavy buckets queued by either
+  const unsigned* no_runs = w.counters + 8;
   VT* tval = static_cast<VT*>(w.tval);
   {
     SP_PHASE(SP_PHASE_TILE);
@@ -1170,7 +1205,9 @@ sp_status run_rows(sp_ctx* ctx, cudaStream_t s, const long long* vp, long long n
           vp, w.tile_first, w.ntiles, w.fin, no_runs, 0, w.tkey, tval, out_col, out_val, w.hv[0],
           w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
   }
-  SP_CUDA(cudaGetLastError());
+  const cudaError_t launched = cudaGetLastError();
+  if (fork) SP_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+  SP_CUDA(launched);
   return sort_runs<CI, VT>(ctx, s, w, key_bits, out_col, out_val);
 }
 

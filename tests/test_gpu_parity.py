@@ -152,6 +152,32 @@ def test_row_length_boundaries(ctx):
     assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "boundaries")
 
 
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_split_list_both_ends(ctx, overlap):
+    """Rows of 4097 .. 65535 entries are queued at the front of the key-range split's list,
+    rows of 65536 and more at its back (taken first): several of each, through the
+    permutation's partition and through the extraction's fill queue (J keeps every
+    column, I repeats the hub rows).  Short rows make tiles, which the permutation sorts
+    concurrently with the split (overlap 1) or after it (overlap 0)."""
+    from paper_2509_20776_gb300 import SP_OPT_OVERLAP
+    Ls = [65536, 5000, 0, 4097, 131072, 70001, 65535, 3, 9000, 65537, 40000, 1, 100000]
+    L = boundary_matrix(Ls, 300000, seed=4)
+    S = synth.er_csr(3000, 300000, 200, seed=9, value_kind="f32u01", rowptr_dtype=torch.int64)
+    A = synth.CSRTensors(L.nrows + S.nrows, 300000, torch.cat([L.rowptr, S.rowptr[1:] + L.nnz]),
+                         torch.cat([L.colidx, S.colidx.to(L.colidx.dtype)]), torch.cat([L.values, S.values]))
+    q = synth.random_permutation(300000, 4, 1)
+    p = synth.random_permutation(A.nrows, 4, 0)
+    ctx.set_option(SP_OPT_OVERLAP, overlap)
+    try:
+        B = ctx.sp_permute(to_dev(A), p.cuda(), q.cuda())
+        assert_same(B, oracle.permute(to_oracle(A), p.numpy(), q.numpy()), "split list")
+        I = torch.tensor([4, 0, 1, 12, 4, 6, 9, 5, 10, 0, 20, 3000], dtype=torch.int32)
+        B = ctx.sp_extract(to_dev(A), I.cuda(), q.cuda())
+        assert_same(B, oracle.extract(to_oracle(A), I.numpy(), q.numpy()), "split list extract")
+    finally:
+        ctx.set_option(SP_OPT_OVERLAP, -1)
+
+
 @pytest.mark.parametrize("n", [1 << 22, 1 << 24])
 def test_skewed_keys_long_row(ctx, n):
     """Keys packed into a narrow range with outliers: heavy buckets in the row sort and,
