@@ -227,7 +227,8 @@ struct SegWordStore {
   const uint32_t* ibits;
   const IX* rowmap;
   const RP* rpA;
-  const long long* vt;  // row pointer of the staged rebuilt rows
+  const long long* vt;  // row pointer of the staged rebuilt rows; null: the merge writes
+                        // them in place (their segments are kSegSkip)
   const long long* vp_out;
   CopySeg* segs;
   long long m, nw, cap;
@@ -253,7 +254,8 @@ struct SegWordStore {
         return;
       }
       const long long r = w * 32 + k;
-      segs[j++] = CopySeg{vp_out[r], ((b >> k) & 1u) ? (vt[(long long)rowmap[r]] | kSegB) : (long long)rpA[r]};
+      const bool in_i = (b >> k) & 1u;
+      segs[j++] = CopySeg{vp_out[r], !in_i ? (long long)rpA[r] : vt ? (vt[(long long)rowmap[r]] | kSegB) : kSegSkip};
     }
   }
 };
@@ -375,10 +377,18 @@ struct MergeSrc {
   __device__ bool in_j(long long c) const { return (ld_map(jbits + (c >> 5)) >> (c & 31)) & 1u; }
 };
 
+// First output position of rebuilt row i: in A' itself (vdst = A''s row pointer, row I[i])
+// or in the staging buffer (vdst null, row pointer vp of the rebuilt rows).
+template <class IX>
+__device__ __forceinline__ long long merge_out(const long long* vdst, const IX* I, const long long* vp, long long i) {
+  return vdst ? vdst[(long long)I[i]] : vp[i];
+}
+
 // Rows of at most SRC_LONG source entries (A's and B's together), one warp each.
 template <class RP, class CI, class VT, class IX>
 __global__ void __launch_bounds__(256) k_assign_merge_warp(MergeSrc<RP, CI, VT, IX> ms, long long nI,
-                                                           const long long* __restrict__ vp, CI* __restrict__ tcol,
+                                                           const long long* __restrict__ vp,
+                                                           const long long* __restrict__ vdst, CI* __restrict__ tcol,
                                                            VT* __restrict__ tval, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(256) k_assign_merge_warp(MergeSrc<RP, CI, VT, 
     long long sA, LA, sB, LB;
     ms.rows(i, sA, LA, sB, LB);
     if (LA > SRC_LONG) continue;  // k_assign_merge_long (the count listed it)
-    const long long o = vp[i], oe = vp[i + 1];
+    const long long o = merge_out(vdst, ms.I, vp, i), oe = o + (vp[i + 1] - vp[i]);
     uint32_t bk;
     VT bv;
     const int nb = ms.load_b(sB, LB, bk, bv);
@@ -438,7 +448,8 @@ template <class RP, class CI, class VT, class IX>
 __global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT, IX> ms,
                                                             const long long* __restrict__ cl_rows,
                                                             const unsigned* __restrict__ n_cl, long long cl_cap,
-                                                            const long long* __restrict__ vp, unsigned* ticket,
+                                                            const long long* __restrict__ vp,
+                                                            const long long* __restrict__ vdst, unsigned* ticket,
                                                             CI* __restrict__ tcol, VT* __restrict__ tval,
                                                             DevStatus* st) {
   constexpr int NW = 1024 / 32, NCH = NW * LOAD_U;  // chunks of one step
@@ -462,7 +473,7 @@ __global__ void __launch_bounds__(1024) k_assign_merge_long(MergeSrc<RP, CI, VT,
     const long long i = cl_rows[item];
     long long sA, LA, sB, LB;
     ms.rows(i, sA, LA, sB, LB);
-    const long long o = vp[i], oe = vp[i + 1];
+    const long long o = merge_out(vdst, ms.I, vp, i), oe = o + (vp[i + 1] - vp[i]);
     uint32_t bk;
     VT bv;
     const int nb = ms.load_b(sB, LB, bk, bv);
@@ -739,64 +750,47 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   const long long m = A.nrows, nI = pl->nI, nt = pl->nnz_temp, nnz_out = pl->nnz_out;
   SP_TRY(store_rowptr(ctx, s, pl->vp_out, m + 1, Ap->rowptr_type, Ap->rowptr));
   if (nnz_out == 0) return SP_OK;
+  // merge: the rebuilt rows (A's surviving run and B's relabelled row, both in order) are
+  // written straight into A'; otherwise they are staged, sorted, and copied with the rest
+  const bool merge = nt > 0 && pl->mode == SP_ASSIGN_REPLACE && pl->max_lb <= 32;
+  const bool staged = nt > 0 && !merge;
   const long long segcap = m < 2 * nI + 1 ? m : 2 * nI + 1;
   const long long nchunks = (nnz_out + SC_CH - 1) / SC_CH;
   Carver cv;
-  const size_t o_tc = cv.reserve(size_t(nt) * sizeof(CI));
-  const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
+  const size_t o_tc = cv.reserve(staged ? size_t(nt) * sizeof(CI) : 0);
+  const size_t o_tv = cv.reserve(staged ? size_t(nt) * sizeof(VT) : 0);
   const size_t o_tk = cv.reserve(16);
   const size_t o_sg = cv.reserve(size_t(segcap + 1) * sizeof(CopySeg));
   const size_t o_ns = cv.reserve(8);
   const size_t o_cf = cv.reserve(size_t(nchunks) * 8);
   const size_t o_sc = cv.reserve(scan_ws_bytes(m));
   size_t r1[kRowsSlots];
-  rows_reserve(cv, nI, nt, sizeof(VT), r1);
+  rows_reserve(cv, staged ? nI : 0, staged ? nt : 0, sizeof(VT), r1);
   char* base;
   SP_TRY(ctx_workspace(ctx, cv.total(), s, &base));
   cv.bind(base);
-  CI* tcol = cv.at<CI>(o_tc);
-  VT* tval = cv.at<VT>(o_tv);
-  if (nt > 0 && pl->mode == SP_ASSIGN_REPLACE && pl->max_lb <= 32) {
-    // rebuilt rows merged in order: A's surviving run and B's relabelled row, no sort
-    const sp_csr& B = pl->B;
-    const MergeSrc<RP, CI, VT, IX> ms{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
-                                     static_cast<const VT*>(A.values), pl->rpB, static_cast<const CI*>(B.colidx),
-                                     static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
-                                     static_cast<const IX*>(pl->J), static_cast<const uint32_t*>(pl->jmap), pl->sstart,
-                                     pl->slen, A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz};
-    unsigned* ticket = cv.at<unsigned>(o_tk);
-    SP_CUDA(cudaMemsetAsync(ticket, 0, 16, s));
-    const int nsm = ctx->num_sms;
-    {
-      SP_PHASE(SP_PHASE_GATHER);
-      k_assign_merge_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ms, nI, pl->vp, tcol, tval,
-                                                                            ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-    {
-      SP_PHASE(SP_PHASE_GATHER);
-      k_assign_merge_long<<<nsm, 1024, 0, s>>>(ms, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp, ticket,
-                                                tcol, tval, ctx->dstatus);
-    }
-    SP_CUDA(cudaGetLastError());
-  } else if (nt > 0) {
+  CI* tcol = staged ? cv.at<CI>(o_tc) : nullptr;
+  VT* tval = staged ? cv.at<VT>(o_tv) : nullptr;
+  const int nsm = ctx->num_sms;
+  if (staged) {
     // rebuilt rows: A's surviving entries and B's relabelled ones, staged, then sorted
     SP_TRY((assign_stage<RP, CI, VT, IX>(ctx, pl, tcol, tval, cv.at<unsigned>(o_tk), s)));
     const RowsWs w1 = rows_bind(cv, nI, nt, r1);
     const int kb = ceil_log2_u64(uint64_t(A.ncols));
     SP_TRY((run_rows<CI, VT, NoGather<CI, VT>>(ctx, s, pl->vp, nI, nt, kb, w1, nullptr, true, tcol, tval)));
   }
-  // assembly: runs of untouched rows from A, rows of I from the staging buffer
+  // assembly: runs of untouched rows from A, rows of I from the staging buffer (or left
+  // to the merge)
   const IX* rowmap = static_cast<const IX*>(pl->rowmap);
   CopySeg* segs = cv.at<CopySeg>(o_sg);
   long long* nseg = cv.at<long long>(o_ns);
   long long* chunk_first = cv.at<long long>(o_cf);
   const long long nw = (m + 31) / 32;
   SP_TRY(launch_scan(ctx, s, SegWordCount{pl->ibits, m},
-                     SegWordStore<RP, IX>{pl->ibits, rowmap, static_cast<const RP*>(A.rowptr), pl->vp, pl->vp_out,
-                                          segs, m, nw, segcap, nseg, ctx->dstatus},
+                     SegWordStore<RP, IX>{pl->ibits, rowmap, static_cast<const RP*>(A.rowptr),
+                                          staged ? pl->vp : nullptr, pl->vp_out, segs, m, nw, segcap, nseg,
+                                          ctx->dstatus},
                      nw, cv.at<char>(o_sc), SP_PHASE_PARTITION));
-  const int nsm = ctx->num_sms;
   SP_CUDA(cudaMemsetAsync(chunk_first, 0xFF, size_t(nchunks) * 8, s));
   {
     SP_PHASE(SP_PHASE_PARTITION);
@@ -805,17 +799,55 @@ sp_status assign_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* Ap, cudaStream_t s)
   SP_CUDA(cudaGetLastError());
   using CW = std::conditional_t<sizeof(CI) == 4, uint32_t, unsigned long long>;
   using VW = std::conditional_t<sizeof(VT) == 4, uint32_t, unsigned long long>;
-  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const int vec = al(A.colidx) && al(A.values) && al(tcol) && al(tval) && al(Ap->colidx) && al(Ap->values);
-  {
-    SP_PHASE(SP_PHASE_GATHER);
-    const long long g = nchunks < 8ll * nsm ? nchunks : 8ll * nsm;
-    k_seg_copy<CW, VW><<<unsigned(g), SC_BLOCK, 0, s>>>(
-        segs, nseg, nnz_out, chunk_first, nchunks, static_cast<const CW*>(A.colidx), static_cast<const VW*>(A.values),
-        A.nnz, reinterpret_cast<const CW*>(tcol), reinterpret_cast<const VW*>(tval), nt,
-        static_cast<CW*>(Ap->colidx), static_cast<VW*>(Ap->values), vec, ctx->dstatus);
+  // The copy and the merge write disjoint rows of A'.  With the context's overlap on, the
+  // copy (bandwidth-bound) runs on the side stream at SC_MINB_OVERLAP CTAs per SM while
+  // the merge (latency-bound) takes the rest of each SM on `s`.
+  const bool fork = merge && ctx->overlap && ctx->side;
+  cudaStream_t cs = fork ? ctx->side : s;
+  if (fork) {
+    SP_CUDA(cudaEventRecord(ctx->fork_ev, s));
+    SP_CUDA(cudaStreamWaitEvent(cs, ctx->fork_ev, 0));
   }
-  SP_CUDA(cudaGetLastError());
+  cudaError_t launched;
+  {
+    ::sp::PhaseScope ph(ctx, cs, SP_PHASE_GATHER);
+    const long long gmax = (long long)(fork ? SC_MINB_OVERLAP : SC_MINB) * nsm;
+    const long long g = nchunks < gmax ? nchunks : gmax;
+    k_seg_copy<CW, VW><<<unsigned(g), SC_BLOCK, 0, cs>>>(
+        segs, nseg, nnz_out, chunk_first, nchunks, static_cast<const CW*>(A.colidx), static_cast<const VW*>(A.values),
+        A.nnz, reinterpret_cast<const CW*>(tcol), reinterpret_cast<const VW*>(tval), staged ? nt : 0,
+        static_cast<CW*>(Ap->colidx), static_cast<VW*>(Ap->values), vec, ctx->dstatus);
+    launched = cudaGetLastError();
+  }
+  if (fork) SP_CUDA(cudaEventRecord(ctx->join_ev, cs));
+  if (launched == cudaSuccess && merge) {
+    const sp_csr& B = pl->B;
+    const MergeSrc<RP, CI, VT, IX> ms{static_cast<const RP*>(A.rowptr), static_cast<const CI*>(A.colidx),
+                                     static_cast<const VT*>(A.values), pl->rpB, static_cast<const CI*>(B.colidx),
+                                     static_cast<const VT*>(B.values), static_cast<const IX*>(pl->I),
+                                     static_cast<const IX*>(pl->J), static_cast<const uint32_t*>(pl->jmap), pl->sstart,
+                                     pl->slen, A.nrows, A.ncols, A.nnz, pl->nJ, B.nnz};
+    CI* oc = static_cast<CI*>(Ap->colidx);
+    VT* ov = static_cast<VT*>(Ap->values);
+    unsigned* ticket = cv.at<unsigned>(o_tk);
+    launched = cudaMemsetAsync(ticket, 0, 16, s);
+    if (launched == cudaSuccess) {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_assign_merge_warp<<<grid_for(nI * 32, 256, nsm * 16), 256, 0, s>>>(ms, nI, pl->vp, pl->vp_out, oc, ov,
+                                                                            ctx->dstatus);
+      launched = cudaGetLastError();
+    }
+    if (launched == cudaSuccess) {
+      SP_PHASE(SP_PHASE_GATHER);
+      k_assign_merge_long<<<nsm, 1024, 0, s>>>(ms, pl->cl_rows, pl->counters + 0, pl->list_cap, pl->vp,
+                                                pl->vp_out, ticket, oc, ov, ctx->dstatus);
+      launched = cudaGetLastError();
+    }
+  }
+  if (fork) SP_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+  SP_CUDA(launched);
   return SP_OK;
 }
 

@@ -7,7 +7,9 @@
 // 8-byte elements); its source is loaded as whole 16-byte words and realigned in
 // registers when source and destination differ in alignment.  Groups that cross a
 // segment boundary, touch an array's last words, or belong to unaligned arrays are copied
-// element by element.
+// element by element.  A segment whose src is kSegSkip is left alone: its positions are
+// written by another kernel (which may run at the same time, so no 16-byte store of the
+// copy ever covers one of them).
 #pragma once
 
 #include "common.cuh"
@@ -19,9 +21,12 @@ struct CopySeg {
   long long src;  // first source position; bit 62: the second array
 };
 constexpr long long kSegB = 1ll << 62;
+constexpr long long kSegSkip = 1ll << 61;  // src of a segment another kernel writes: not copied
 constexpr int SC_CH = 8192;        // output positions per chunk (a multiple of four)
 constexpr int SC_BLOCK = 256;
 constexpr int SC_SEGS = SC_BLOCK;  // segment descriptors staged in shared memory at once
+constexpr int SC_MINB = 8;          // persistent grid: CTAs per SM
+constexpr int SC_MINB_OVERLAP = 4;  // the same while another kernel shares the SMs
 
 // Four consecutive elements of T starting at element s of src (n elements), realigned
 // from whole 16-byte words; false when those words would leave [0, n) (caller copies the
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(SC_BLOCK) k_seg_copy(const CopySeg* __restrict
           else hi = mid - 1;
         }
         const long long send = s_dst[lo + 1];
+        if (s_src[lo] == kSegSkip && g >= p0 && g >= s_dst[lo] && g + 4 <= send) continue;
         const bool whole = vec && g >= p0 && g >= s_dst[lo] && g + 4 <= send;
         if (whole) {
           const long long sp = s_src[lo];
@@ -165,6 +171,7 @@ __global__ void __launch_bounds__(SC_BLOCK) k_seg_copy(const CopySeg* __restrict
           if (q < p0 || q >= p1) continue;
           while (sj + 1 < ns && s_dst[sj + 1] <= q) ++sj;
           const long long sp = s_src[sj];
+          if (sp == kSegSkip) continue;
           const long long s = (sp & ~kSegB) + (q - s_dst[sj]);
           if (sp & kSegB) {
             if (s >= 0 && s < nb) {

@@ -322,12 +322,16 @@ def test_assign_hubs_and_roundtrip(ctx):
     assert_same(E, to_oracle(Bm), "extract after assign")
 
 
-@pytest.mark.parametrize("longest", [32, 33])
-def test_assign_merge_boundaries(ctx, longest):
+@pytest.mark.parametrize("longest,overlap", [(32, 1), (32, 0), (33, 1)])
+def test_assign_merge_boundaries(ctx, longest, overlap):
     """REPLACE with every row of B at most 32 entries takes the merge fill (A's surviving
-    run and B's relabelled row merged in order, no row sort); one row of 33 takes the
-    staged fill and the row sort.  Rows of B of 0, 1, 31 and the longest length, hub rows
-    of A on both kernels of the merge (warp and CTA), keys before, between and after A's."""
+    run and B's relabelled row merged in order straight into A', no row sort, while the
+    copy of the other rows runs beside it (overlap 1) or before it); one row of 33 takes
+    the staged fill and the row sort.  Rows of B of 0, 1, 31 and the longest length, hub
+    rows of A on both kernels of the merge (warp and CTA), keys before, between and after
+    A's; rows of I next to each other and alone, so copy segments of every length lie
+    between the merged rows."""
+    from paper_2509_20776_gb300 import SP_OPT_OVERLAP
     A = rmat(14)
     n = A.nrows
     rng = np.random.default_rng(longest)
@@ -343,7 +347,11 @@ def test_assign_merge_boundaries(ctx, longest):
     v = rng.random(r.shape[0]).astype(np.float32)
     Bo = oracle.build_csr(I.numel(), nJ, r, c, v)
     Bd = from_oracle(Bo)
-    Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), Bd)
+    ctx.set_option(SP_OPT_OVERLAP, overlap)
+    try:
+        Ap = ctx.sp_assign(to_dev(A), I.cuda(), J.cuda(), Bd)
+    finally:
+        ctx.set_option(SP_OPT_OVERLAP, -1)
     assert_same(Ap, oracle.assign(to_oracle(A), I.numpy(), J.numpy(), Bo), f"assign, longest B row {longest}")
     E = ctx.sp_extract(Ap, I.cuda(), J.cuda())
     assert_same(E, Bo, "extract after assign")
