@@ -205,12 +205,15 @@ def row_classes(rowptr):
     return out
 
 
-def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup_peak):
+def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup_peak, concurrent=()):
     """Roofline of the phase that takes the most device time: its algorithmic bytes per
     launch over its average CUDA-event duration (int32 columns, fp32 values).  The gather
     moves 16 B per entry (read and write column + value, the scope's per-entry bytes) plus
     16 B per row (output row pointer, source start); its 4-byte relabel lookup per entry is
-    counted separately (frac_incl_lookup) and against the measured random-lookup rate."""
+    counted separately (frac_incl_lookup) and against the measured random-lookup rate.
+    Phases in `concurrent` run on a second stream beside another phase: their event times
+    include the time they share the SMs, so they are reported but never taken as the
+    dominant kernel."""
     e_tile, r_tile = classes["tile"]
     e_long, _ = classes["long"]
     e_huge, _ = classes["huge"]
@@ -232,7 +235,7 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup
     launches_total = ops_per_step * steps
     best = None
     for ph, (ms, cnt) in stats.items():
-        if cnt == 0 or ms <= 0 or ph not in per_op:
+        if cnt == 0 or ms <= 0 or ph not in per_op or ph in concurrent:
             continue
         if best is None or ms > best[1]:
             best = (ph, ms, cnt)
@@ -248,6 +251,8 @@ def roofline_permute(stats, classes, m, n, ops_per_step, steps, peak_gbs, lookup
            "frac_of_nominal_7900gbs": round(achieved / 7900.0, 4),
            "avg_launch_ms": round(ms / cnt, 4),
            "phase_ms": {k: round(v[0], 3) for k, v in stats.items() if v[1]}}
+    if concurrent:
+        out["phase_ms_concurrent"] = sorted(concurrent)
     if ph == "gather":
         with_lookup = (per_op[ph] + 4 * nnz) * launches_total / sec / 1e9
         out["frac_incl_lookup"] = round(with_lookup / peak_gbs, 4)
@@ -461,7 +466,8 @@ def run_ours(args, ws, rank, local):
     out_per_step = nnz * len(ops)
     value = out_per_step * args.steps * ws / (ms * 1e-3)
     lk = lookup_probe(A.ncols, A.colidx, dev)
-    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, lk)
+    roof = roofline_permute(stats_timed, classes, m, A.ncols, len(ops), args.steps, hbm, lk,
+                            concurrent=("huge",) if args.overlap else ())
     # whole op: read and write col + val per entry, p and rowptr pair per row, q and qinv
     alg_bytes_op = 16 * nnz + 28 * m + 12 * A.ncols
     op_frac = alg_bytes_op * len(ops) * args.steps / (ms * 1e-3) / 1e9 / hbm

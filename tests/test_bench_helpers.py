@@ -38,6 +38,18 @@ def test_roofline_of_dominant_phase():
     assert abs(r["lookup_roofline"]["frac"] - 1000 * 6 / 6e-3 / 1e9 / 100.0) < 1e-4
 
 
+def test_concurrent_phase_never_dominant():
+    """A phase timed on the side stream (the split beside the tile sort) is listed but not
+    chosen, however long its events bracket."""
+    classes = {"tile": (400, 10), "long": (300, 2), "huge": (300, 1)}
+    stats = {"gather": (6.0, 6), "tile": (3.0, 6), "huge": (9.0, 6)}
+    r = bench.roofline_permute(stats, classes, 100, 100, 3, 2, 1000.0, None)
+    assert r["phase"] == "huge"
+    r = bench.roofline_permute(stats, classes, 100, 100, 3, 2, 1000.0, None, concurrent=("huge",))
+    assert r["phase"] == "gather" and r["phase_ms_concurrent"] == ["huge"]
+    assert r["phase_ms"]["huge"] == 9.0
+
+
 def test_traffic_only_from_captures():
     classes = {"tile": (10, 5), "long": (0, 0), "huge": (0, 0)}
     r = bench.roofline_permute({"gather": (1.0, 3)}, classes, 5, 5, 3, 1, 100.0, None)
