@@ -157,13 +157,15 @@ SP_API int sp_last_cuda_error(const char** where);
  *                          (Algorithm 5's search: |J| log |J| set-up, no column-sized
  *                          table). */
 /* Scheduling (same output either way):
- *   SP_OPT_OVERLAP         1 (default): a row sort that has both rows longer than 4096
- *                          entries and tiles of short rows runs the long rows' key-range
- *                          split on the context's own side stream (created with the
- *                          device's highest stream priority) while the tiles are sorted
- *                          on the caller's stream; the two are forked and joined with
- *                          events, so the call stays ordered on the caller's stream and
- *                          capturable; 0: every launch on the caller's stream. */
+ *   SP_OPT_OVERLAP         1 (default): phases that write disjoint rows run side by side,
+ *                          one of them on the context's own side stream (created with the
+ *                          device's highest stream priority): a row sort's key-range
+ *                          split of the rows longer than 4096 entries beside the tile sort
+ *                          of its short rows, and an assignment's copy of the rows outside
+ *                          I beside the merge of the rows of I (REPLACE); the side work is
+ *                          forked from and joined back to the caller's stream with events,
+ *                          so the call stays ordered on that stream and capturable;
+ *                          0: every launch on the caller's stream. */
 typedef enum sp_option {
   SP_OPT_SPIN_LIMIT = 0,
   SP_OPT_SCAN_HOLD_TILE = 1,
