@@ -597,14 +597,8 @@ sp_status assign_count_impl(sp_ctx* ctx, sp_plan* pl, cudaStream_t s) {
   if (nI > 0) {
     {
       SP_PHASE(SP_PHASE_MAP);
-      k_inverse_map<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, rowmap, ctx->dstatus,
-                                                                    SP_ERR_DUPLICATE_INDEX);
-    }
-    SP_CUDA(cudaGetLastError());
-    {
-      SP_PHASE(SP_PHASE_MAP);
-      k_mark_bits<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, pl->ibits, ctx->dstatus,
-                                                                  SP_ERR_DUPLICATE_INDEX);
+      k_inverse_map_bits<IX><<<grid_for(nI, 256, nsm * 8), 256, 0, s>>>(I, nI, m, rowmap, pl->ibits,
+                                                                         ctx->dstatus, SP_ERR_DUPLICATE_INDEX);
     }
     SP_CUDA(cudaGetLastError());
   }
@@ -925,6 +919,7 @@ sp_status assign_permute_impl(sp_ctx* ctx, sp_plan* pl, const IX* p, const IX* q
   const size_t o_tv = cv.reserve(size_t(nt) * sizeof(VT));
   const size_t o_tk = cv.reserve(16);
   const size_t o_qinv = cv.reserve(q ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_qbits = cv.reserve(q ? size_t((n + 31) / 32) * 4 : 0);
   const size_t o_pbits = cv.reserve((p && !sym) ? size_t((m + 31) / 32) * 4 : 0);
   const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
   const size_t o_ss = cv.reserve(size_t(m) * 8);
@@ -937,11 +932,13 @@ sp_status assign_permute_impl(sp_ctx* ctx, sp_plan* pl, const IX* p, const IX* q
   const int nsm = ctx->num_sms;
   IX* qinv = q ? cv.at<IX>(o_qinv) : nullptr;
   if (q) {
+    uint32_t* qbits = cv.at<uint32_t>(o_qbits);
     SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(n) * sizeof(IX), s));
+    SP_CUDA(cudaMemsetAsync(qbits, 0, size_t((n + 31) / 32) * 4, s));
     {
       SP_PHASE(SP_PHASE_MAP);
-      k_inverse_map<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, ctx->dstatus,
-                                                                   SP_ERR_NOT_PERMUTATION);
+      k_inverse_map_bits<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, qbits, ctx->dstatus,
+                                                                        SP_ERR_NOT_PERMUTATION);
     }
     SP_CUDA(cudaGetLastError());
   }

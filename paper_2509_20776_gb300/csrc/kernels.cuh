@@ -30,6 +30,32 @@ __global__ void k_inverse_map(const IX* __restrict__ idx, long long len, long lo
   }
 }
 
+// The same map with a membership bitmap beside it: a repeated index is found by the
+// bitmap's atomicOr (1 bit per value, small enough to stay in L2) and the map takes one
+// plain store per index instead of a compare-and-swap on an entry of the n-entry map.
+// The first index to set a value's bit writes its position; a later repeat only reports
+// dup_code.  inv (-1) and bits (0) are cleared before the launch; afterwards bits is J's,
+// I's or q's membership bitmap.
+template <class IX>
+__global__ void k_inverse_map_bits(const IX* __restrict__ idx, long long len, long long n,
+                                   IX* __restrict__ inv, uint32_t* __restrict__ bits, DevStatus* st,
+                                   int dup_code) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long v = (long long)idx[k];
+    if (v < 0 || v >= n) {
+      dev_fail(st, SP_ERR_INDEX_RANGE, k);
+      continue;
+    }
+    const uint32_t m = 1u << (v & 31);
+    if (atomicOr(bits + (v >> 5), m) & m) {
+      dev_fail(st, dup_code, k);
+      continue;
+    }
+    inv[v] = IX(k);
+  }
+}
+
 // membership bitmap (1 bit per index); repeated indices are reported as dup_code, or
 // only flagged in *dup_flag when one is given
 template <class IX>

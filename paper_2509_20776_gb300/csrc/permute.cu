@@ -65,6 +65,7 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   const bool out64 = B->rowptr_type == SP_I64;
   Carver cv;
   const size_t o_qinv = cv.reserve(q ? size_t(n) * sizeof(IX) : 0);
+  const size_t o_qbits = cv.reserve(q ? size_t((n + 31) / 32) * 4 : 0);
   const size_t o_pbits = cv.reserve((p && !sym) ? size_t((m + 31) / 32) * 4 : 0);
   const size_t o_vp = cv.reserve(out64 ? 0 : size_t(m + 1) * 8);
   const size_t o_scan = cv.reserve(scan_ws_bytes(m));
@@ -79,11 +80,13 @@ sp_status permute_impl(sp_ctx* ctx, const sp_csr* A, const IX* p, const IX* q, s
   const int nsm = ctx->num_sms;
   // Identify: inverse column map (validates q), row permutation check (validates p)
   if (q) {
+    uint32_t* qbits = cv.at<uint32_t>(o_qbits);
     SP_CUDA(cudaMemsetAsync(qinv, 0xFF, size_t(n) * sizeof(IX), s));
+    SP_CUDA(cudaMemsetAsync(qbits, 0, size_t((n + 31) / 32) * 4, s));
     {
       SP_PHASE(SP_PHASE_MAP);
-      k_inverse_map<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, ctx->dstatus,
-                                                                   SP_ERR_NOT_PERMUTATION);
+      k_inverse_map_bits<IX><<<grid_for(n, 256, nsm * 8), 256, 0, s>>>(q, n, n, qinv, qbits, ctx->dstatus,
+                                                                        SP_ERR_NOT_PERMUTATION);
     }
     SP_CUDA(cudaGetLastError());
   }

@@ -504,6 +504,12 @@ def test_errors(ctx):
     with pytest.raises(SpError) as e:
         ctx.sp_permute(A, bad, None)
     assert e.value.name == "SP_ERR_NOT_PERMUTATION"
+    with pytest.raises(SpError) as e:  # the same repeat in the column permutation
+        ctx.sp_permute(A, None, bad)
+    assert e.value.name == "SP_ERR_NOT_PERMUTATION"
+    with pytest.raises(SpError) as e:  # and in both (the symmetric form builds one map)
+        ctx.sp_permute(A, bad, bad)
+    assert e.value.name == "SP_ERR_NOT_PERMUTATION"
     oob = torch.arange(100, dtype=torch.int32).cuda()
     oob[3] = 1000
     with pytest.raises(SpError) as e:
@@ -513,6 +519,14 @@ def test_errors(ctx):
         ctx.sp_assign(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
                       torch.tensor([3, 3], dtype=torch.int32).cuda(), to_dev(er(2, 2, seed=1)))
     assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
+    with pytest.raises(SpError) as e:  # and distinct I
+        ctx.sp_assign(A, torch.tensor([4, 4], dtype=torch.int32).cuda(),
+                      torch.tensor([3, 5], dtype=torch.int32).cuda(), to_dev(er(2, 2, seed=1)))
+    assert e.value.name == "SP_ERR_DUPLICATE_INDEX"
+    with pytest.raises(SpError) as e:  # the fused assignment + permutation checks q the same way
+        ctx.sp_assign_permute(A, torch.tensor([0, 1], dtype=torch.int32).cuda(),
+                              torch.tensor([3, 5], dtype=torch.int32).cuda(), to_dev(er(2, 2, seed=1)), q=bad)
+    assert e.value.name == "SP_ERR_NOT_PERMUTATION"
     with pytest.raises(SpError) as e:
         ctx.sp_extract(A, torch.tensor([0, 100], dtype=torch.int32).cuda(),
                        torch.tensor([3], dtype=torch.int32).cuda())
