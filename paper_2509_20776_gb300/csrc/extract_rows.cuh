@@ -12,9 +12,11 @@
 //       stored entry: Algorithm 5's search, for small |J|.
 //   Count (k_xcount).  A warp takes 32 selected rows ("a block"): lane l resolves row
 //     i0 + l (I[i], range check, the row-pointer pair), so 32 index chains are in flight,
-//     and records the row's source start and length for the fill.  The warp then loads
-//     the columns of XC_ROWS rows at once (two per lane), tests each against J's bitmap
-//     and counts the members (ballot + popc).
+//     and records the row's source start and length for the fill.  A row of at most
+//     XC_LANE entries is then counted by its own lane (all its columns loaded at once,
+//     every lane's row in flight together); the warp takes the longer rows XC_ROWS at a
+//     time (two columns per lane), tests each column against J's bitmap and counts the
+//     members (ballot + popc).
 //   Fill (k_xfill).  A warp again takes 32 rows; for XF_ROWS rows at once it loads the
 //     columns and values, relabels the kept entries (rank word + position), compacts them
 //     (ballot slots) into a per-warp shared buffer and ranks each among its row's new
@@ -34,6 +36,8 @@ namespace sp {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int XFAST = 64;     // rows of at most this many source entries: masks, warp sort
 constexpr int XC_ROWS = 6;    // rows whose columns a counting warp loads together
+template <class CI>
+constexpr int xc_lane() { return sizeof(CI) == 4 ? 16 : 8; }  // rows a lane counts alone
 constexpr int XF_ROWS = 2;    // rows whose kept entries a filling warp loads together
 constexpr int XB = 256;       // threads per CTA of the count / fill
 constexpr unsigned kDropped = 0xFFFFFFFFu;  // padding key: never below a key
@@ -204,9 +208,11 @@ __global__ void __launch_bounds__(XB, 4) k_xcount(Src src, Res res, long long nI
                                                  unsigned* n_slow, DevStatus* st) {
   using CI = typename Src::CI;
   using H = typename Src::H;
-  constexpr int R = XC_ROWS;
+  constexpr int R = XC_ROWS, XL = xc_lane<CI>();
   constexpr long long kLong = Src::kLongCta ? SRC_LONG : (1ll << 62);
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned char s_lane[XB / 32][32];  // the lanes of the warp's longer rows, in order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i0 = w0 * 32; i0 < nI; i0 += nw * 32) {
@@ -223,18 +229,34 @@ __global__ void __launch_bounds__(XB, 4) k_xcount(Src src, Res res, long long nI
     if (lane == 0 && slow) atomicAdd(n_slow, unsigned(__popc(slow)));
     if (L > kLong) push_row(cl_rows, n_cl, cl_cap, i, st);
     long long mine = 0;
-    const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
+    // short rows: the lane's own row, all its columns in flight at once
+    if (L <= XL) {
+      const CI* cp = src.cols(h);
+      CI cc[XL];
+#pragma unroll
+      for (int e = 0; e < XL; ++e) cc[e] = e < L ? ld_stream(cp + s + e) : CI(0);
+#pragma unroll
+      for (int e = 0; e < XL; ++e) mine += (e < L && src.test(h, (long long)cc[e])) ? 1 : 0;
+    }
+    // longer rows (up to kLong): the warp, XC_ROWS rows at a time
+    const unsigned lm = __ballot_sync(kFull, L > XL && L <= kLong);
+    if ((lm >> lane) & 1u) s_lane[wid][__popc(lm & lt)] = (unsigned char)lane;
+    __syncwarp();
+    const int nr = __popc(lm);
     for (int g = 0; g < nr; g += R) {
       long long ss[R];
       int LL[R];  // the row's length, capped (the loop over a longer row re-reads it)
+      int ln[R];  // its lane
       CI c0[R], c1[R];
-      // the handle of row g + u (nothing for a single matrix; one shuffle for a batch)
-      auto hof = [&](int u) { return Src::shfl(h, (g + u) & 31); };
+#pragma unroll
+      for (int u = 0; u < R; ++u) ln[u] = g + u < nr ? int(s_lane[wid][g + u]) : 0;
+      // the handle of row u of the group (nothing for a single matrix; one shuffle for a batch)
+      auto hof = [&](int u) { return Src::shfl(h, ln[u]); };
 #pragma unroll
       for (int u = 0; u < R; ++u) {
-        ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
-        const long long l = __shfl_sync(kFull, L, (g + u) & 31);
-        if constexpr (Src::kLongCta) LL[u] = (g + u < nr && l <= kLong) ? int(l) : 0;
+        ss[u] = __shfl_sync(kFull, s, ln[u]);
+        const long long l = __shfl_sync(kFull, L, ln[u]);
+        if constexpr (Src::kLongCta) LL[u] = g + u < nr ? int(l) : 0;
         else LL[u] = g + u < nr ? int(l < (1 << 30) ? l : (1 << 30)) : 0;
       }
 #pragma unroll
@@ -260,7 +282,7 @@ __global__ void __launch_bounds__(XB, 4) k_xcount(Src src, Res res, long long nI
         using LT = std::conditional_t<Src::kLongCta, int, long long>;
         LT Lu = LT(LL[u]);
         if constexpr (!Src::kLongCta) {
-          if (LL[u] > 64) Lu = __shfl_sync(kFull, L, (g + u) & 31);
+          if (LL[u] > 64) Lu = __shfl_sync(kFull, L, ln[u]);
         }
         for (LT e0 = 64; e0 < Lu; e0 += 32 * LOAD_U) {
           CI cc[LOAD_U];
@@ -275,9 +297,10 @@ __global__ void __launch_bounds__(XB, 4) k_xcount(Src src, Res res, long long nI
             c += __popc(__ballot_sync(kFull, e < Lu && src.test(hu, (long long)cc[v])));
           }
         }
-        if (lane == g + u) mine = c;
+        if (g + u < nr && lane == ln[u]) mine = c;
       }
     }
+    __syncwarp();  // s_lane is rewritten by the next block of rows
     if (i < nI && L <= kLong) cnt[i] = mine;
   }
 }
