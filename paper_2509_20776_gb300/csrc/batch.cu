@@ -519,7 +519,7 @@ sp_status batch_fill_body(sp_ctx* ctx, sp_batch* b, sp_csr* out, cudaStream_t s,
       const XBatchSrc<CI, VT> src{b->rreq, b->rv, b->jrp};
       k_xfill<XBatchSrc<CI, VT>, false><<<grid_for((rows + 31) / 32 * 32, XB, ctx->num_sms * 8), XB, 0, s>>>(
           src, rows, b->rs0, b->rsn, b->vp, oc, ov, w.fin, w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
-          w.huge_cap, kb, ctx->dstatus);
+          w.huge_cap, kb, b->max_nj <= 0xFFFFFFFFll ? XF_LANE : 0, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
     return sort_queued<CI, VT>(ctx, s, w, kb, oc, ov);

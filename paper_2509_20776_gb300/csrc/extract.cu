@@ -424,6 +424,7 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
   const VT* vv = static_cast<const VT*>(A.values);
   const long long groups = (nI + 31) / 32;
   const int g = grid_for(groups * 32, XB, nsm * 8);
+  const int lane_rows = pl->nJ <= 0xFFFFFFFFll ? XF_LANE : 0;  // keys (positions in J) below the padding key
   auto fill = [&](auto rel) -> sp_status {
     using Rel = decltype(rel);
     {
@@ -432,11 +433,11 @@ sp_status extract_fill_impl(sp_ctx* ctx, sp_plan* pl, sp_csr* B, cudaStream_t s)
       if (sorted)
         k_xfill<XOne<CI, VT, Rel>, true><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
                                                           w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
-                                                          w.huge_cap, kb, ctx->dstatus);
+                                                          w.huge_cap, kb, lane_rows, ctx->dstatus);
       else
         k_xfill<XOne<CI, VT, Rel>, false><<<g, XB, 0, s>>>(src, nI, pl->sstart, pl->slen, pl->vp, oc, ov, w.fin,
                                                            w.counters + 0, w.fin_cap, w.huge, w.huge_n(),
-                                                           w.huge_cap, kb, ctx->dstatus);
+                                                           w.huge_cap, kb, lane_rows, ctx->dstatus);
     }
     SP_CUDA(cudaGetLastError());
     // rows of more than SRC_LONG source entries: one CTA each, kept entries in source order

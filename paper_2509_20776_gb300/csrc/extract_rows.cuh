@@ -17,11 +17,14 @@
 //     every lane's row in flight together); the warp takes the longer rows XC_ROWS at a
 //     time (two columns per lane), tests each column against J's bitmap and counts the
 //     members (ballot + popc).
-//   Fill (k_xfill).  A warp again takes 32 rows; for XF_ROWS rows at once it loads the
-//     columns and values, relabels the kept entries (rank word + position), compacts them
-//     (ballot slots) into a per-warp shared buffer and ranks each among its row's new
-//     columns, so a row of at most XFAST source entries is written once, sorted, at its
-//     final place.  Longer rows are written in source order and queued for the row sort.
+//   Fill (k_xfill).  A warp again takes 32 rows.  A row of at most XF_LANE source
+//     entries is filled by its own lane: its columns and values loaded at once, the kept
+//     ones relabelled and sorted by a network in registers, written once.  For longer
+//     rows the warp loads XF_ROWS rows at once, relabels the kept entries (rank word +
+//     position), compacts them (ballot slots) into a per-warp shared buffer and ranks
+//     each among its row's new columns, so a row of at most XFAST source entries is
+//     written once, sorted, at its final place.  Longer rows are written in source order
+//     and queued for the row sort.
 //   Random lookups, not HBM bytes, bound both passes: one 4-byte lookup per SM cycle
 //   while its table is L2-resident (~300 G/s on GB300), fewer for tables above ~100 MB.
 #pragma once
@@ -39,6 +42,27 @@ constexpr int XC_ROWS = 6;    // rows whose columns a counting warp loads togeth
 template <class CI>
 constexpr int xc_lane() { return sizeof(CI) == 4 ? 16 : 8; }  // rows a lane counts alone
 constexpr int XF_ROWS = 2;    // rows whose kept entries a filling warp loads together
+constexpr int XF_LANE = 8;    // rows of at most this many source entries: filled by their own lane
+
+// Sorting network on XF_LANE (key, value) pairs held in registers: 19 comparators in 6
+// layers (a test checks the table on all 256 0/1 inputs, which by the 0-1 principle
+// proves it sorts every input).
+template <class VT>
+__device__ __forceinline__ void sort8(uint32_t (&k)[8], VT (&v)[8]) {
+  constexpr int P[19][2] = {{0, 2}, {1, 3}, {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}, {0, 1}, {2, 3},
+                            {4, 5}, {6, 7}, {2, 4}, {3, 5}, {1, 4}, {3, 6}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+  for (int c = 0; c < 19; ++c) {
+    const int a = P[c][0], b = P[c][1];
+    const bool sw = k[b] < k[a];
+    const uint32_t ka = k[a], kb = k[b];
+    const VT va = v[a], vb = v[b];
+    k[a] = sw ? kb : ka;
+    k[b] = sw ? ka : kb;
+    v[a] = sw ? vb : va;
+    v[b] = sw ? va : vb;
+  }
+}
 constexpr int XB = 256;       // threads per CTA of the count / fill
 constexpr unsigned kDropped = 0xFFFFFFFFu;  // padding key: never below a key
 
@@ -339,14 +363,18 @@ __global__ void __launch_bounds__(XB, 4) k_xfill(Src src, long long nI, const lo
                                                 typename Src::CI* __restrict__ out_col,
                                                 typename Src::VT* __restrict__ out_val, FinalEntry* fin,
                                                 unsigned* fin_n, long long fin_cap, HugeEntry* huge, unsigned* huge_n,
-                                                long long huge_cap, int key_bits, DevStatus* st) {
+                                                long long huge_cap, int key_bits, int lane_rows, DevStatus* st) {
+  // lane_rows: XF_LANE when every key is below kDropped (the lane path pads with it), else
+  // 0; the lane path is compiled for 4-byte columns and values (its registers)
   using CI = typename Src::CI;
   using VT = typename Src::VT;
   using H = typename Src::H;
+  constexpr bool kLane = sizeof(CI) == 4 && sizeof(VT) == 4;
   constexpr int R = XF_ROWS, NWB = XB / 32, KW = XFAST + 4;
   constexpr long long kLong = Src::kLongCta ? SRC_LONG : (1ll << 62);
   __shared__ __align__(16) uint32_t s_key[NWB][KW];  // a row's kept keys (+ padding for 4-wide loads)
   __shared__ VT s_val[NWB][XFAST];
+  __shared__ unsigned char s_lane[NWB][32];  // the lanes of the warp's rows for the warp path, in order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint32_t* wk = s_key[wid];
@@ -365,19 +393,56 @@ __global__ void __launch_bounds__(XB, 4) k_xfill(Src src, long long nI, const lo
       h = src.handle(i);
     }
     if (!kSorted && L > XFAST) x_queue(o, oe - o, key_bits, fin, fin_n, fin_cap, huge, huge_n, huge_cap, st);
-    const int nr = nI - i0 < 32 ? int(nI - i0) : 32;
+    // rows of at most lane_rows entries: the lane's own row, all its loads and relabels in
+    // flight together, the kept entries sorted in registers and written once
+    const bool by_lane = L <= (kLane ? lane_rows : 0);
+    if constexpr (kLane) if (by_lane && L > 0) {
+      const CI* cp = src.cols(h);
+      const VT* vq = src.vals(h);
+      CI cc[XF_LANE];
+      VT vv[XF_LANE];
+      uint32_t kk[XF_LANE];
+#pragma unroll
+      for (int e = 0; e < XF_LANE; ++e) cc[e] = e < L ? ld_stream(cp + s + e) : CI(0);
+#pragma unroll
+      for (int e = 0; e < XF_LANE; ++e) vv[e] = e < L ? ld_stream(vq + s + e) : VT(0);
+      int nk = 0;
+#pragma unroll
+      for (int e = 0; e < XF_LANE; ++e) {
+        uint32_t key = kDropped;
+        const bool p = e < L && src.map(h, (long long)cc[e], key);
+        kk[e] = p ? key : kDropped;
+        nk += p ? 1 : 0;
+      }
+      if (nk != oe - o) {  // the count disagrees with the fill (a library bug)
+        dev_fail(st, SP_ERR_INTERNAL, -29);
+      } else {
+        sort8(kk, vv);
+#pragma unroll
+        for (int e = 0; e < XF_LANE; ++e)
+          if (e < nk) x_put(out_col, out_val, o + e, oe, kk[e], vv[e], st);
+      }
+    }
+    // rows of lane_rows < L <= XFAST entries: the warp, XF_ROWS rows at a time
+    const unsigned lm = __ballot_sync(kFull, !by_lane && L <= XFAST);
+    if ((lm >> lane) & 1u) s_lane[wid][__popc(lm & lt)] = (unsigned char)lane;
+    __syncwarp();
+    const int nr = __popc(lm);
     for (int g = 0; g < nr; g += R) {
       long long ss[R];
       int LL[R];
+      int ln[R];
       H hh[R];
       CI c0[R], c1[R];
       VT v0[R], v1[R];
 #pragma unroll
+      for (int u = 0; u < R; ++u) ln[u] = g + u < nr ? int(s_lane[wid][g + u]) : 0;
+#pragma unroll
       for (int u = 0; u < R; ++u) {
-        ss[u] = __shfl_sync(kFull, s, (g + u) & 31);
-        const long long l = __shfl_sync(kFull, L, (g + u) & 31);
-        LL[u] = (g + u < nr && l <= XFAST) ? int(l) : 0;
-        hh[u] = Src::shfl(h, (g + u) & 31);
+        ss[u] = __shfl_sync(kFull, s, ln[u]);
+        const long long l = __shfl_sync(kFull, L, ln[u]);
+        LL[u] = g + u < nr ? int(l) : 0;
+        hh[u] = Src::shfl(h, ln[u]);
       }
 #pragma unroll
       for (int u = 0; u < R; ++u) {
@@ -402,8 +467,8 @@ __global__ void __launch_bounds__(XB, 4) k_xfill(Src src, long long nI, const lo
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         if (LL[u] == 0) continue;  // warp-uniform: empty, long or beyond the block
-        const long long ou = __shfl_sync(kFull, o, (g + u) & 31);
-        const long long eu = __shfl_sync(kFull, oe, (g + u) & 31);
+        const long long ou = __shfl_sync(kFull, o, ln[u]);
+        const long long eu = __shfl_sync(kFull, oe, ln[u]);
         const unsigned b0 = __ballot_sync(kFull, p0[u]), b1 = __ballot_sync(kFull, p1[u]);
         const int n0 = __popc(b0), nk = n0 + __popc(b1);
         if (nk != eu - ou) {  // the count disagrees with the fill (a library bug)
@@ -456,6 +521,7 @@ __global__ void __launch_bounds__(XB, 4) k_xfill(Src src, long long nI, const lo
         }
       }
     }
+    __syncwarp();  // s_lane is rewritten by the next block of rows
     // rows of more than XFAST source entries (up to SRC_LONG with Src::kLongCta): kept
     // entries in source order (ballot slots); their sort was queued above
     unsigned mid = __ballot_sync(kFull, L > XFAST && L <= kLong);

@@ -236,6 +236,22 @@ def test_extract_hubs(ctx):
     assert np.array_equal(kc.cpu().numpy(), oracle.kept_counts(to_oracle(A), I.numpy(), J.numpy()))
 
 
+@pytest.mark.parametrize("jorder", ["general", "ascending"])
+def test_extract_lane_rows(ctx, jorder):
+    """Rows of 0 .. 12 source entries around the fill's lane path (rows of at most 8
+    entries filled and sorted by their own lane), every row selected twice, J keeping
+    about half the columns; values include -0.0 and NaN payloads (moved bit for bit)."""
+    g = torch.Generator().manual_seed(12)
+    Ls = [int(x) for x in torch.randint(0, 13, (5000,), generator=g)]
+    A = special_values(boundary_matrix(Ls, 4000, seed=12))
+    I = torch.cat([torch.randperm(5000, generator=g), torch.randperm(5000, generator=g)])[:9000].to(torch.int32)
+    J = synth.random_subset(4000, 2000, 12, 1)
+    if jorder == "ascending":
+        J = torch.sort(J).values
+    B = ctx.sp_extract(to_dev(A), I.cuda(), J.cuda())
+    assert_same(B, oracle.extract(to_oracle(A), I.numpy(), J.numpy()), f"lane rows, {jorder} J")
+
+
 @pytest.mark.parametrize("shape", ["ascending", "consecutive", "consecutive_edge"])
 def test_extract_ordered_j(ctx, shape):
     """Ascending J (rows come out of the fill in order, no sort) and consecutive J (binary
