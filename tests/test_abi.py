@@ -54,3 +54,28 @@ def test_last_cuda_error_starts_clear(lib):
     assert lib.sp_last_cuda_error(ctypes.byref(where)) == 0
     assert (where.value or b"") == b""
     assert lib.sp_last_cuda_error(None) == 0
+
+
+def _enum(name):
+    """name -> value of the C enum typedef'd as `name` in the header."""
+    text = open(HEADER).read()
+    m = re.search(r"typedef enum " + name + r"\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(SP_[A-Z0-9_]+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_option_constants_match_header():
+    """The binding's option keys are the header's enum values (a drift would set the
+    wrong knob without any error)."""
+    import paper_2509_20776_gb300._binding as b
+    opts = _enum("sp_option")
+    assert "SP_OPT_OVERLAP" in opts
+    for name, value in opts.items():
+        assert getattr(b, name) == value, name
+
+
+def test_binding_assign_modes_match_header():
+    import paper_2509_20776_gb300._binding as b
+    for name, value in _enum("sp_assign_mode").items():
+        assert getattr(b, name) == value, name
