@@ -137,7 +137,7 @@ SP_API int sp_last_cuda_error(const char** where);
  *                          (SP_ERR_NOT_CANONICAL); default 0. */
 /* Kernel shapes (the autotuner's knobs; every value gives the same output, bit for bit):
  *   SP_OPT_TILE_SHAPE      row sort of short rows: 0 = tiles of 1024 entries holding rows
- *                          of at most 512, 128 threads, 8 CTAs per SM (default);
+ *                          of at most 512, 128 threads, 9 CTAs per SM (default);
  *                          1 = tiles of 2048 entries holding rows of at most 1024,
  *                          256 threads, 4 CTAs per SM;
  *   SP_OPT_HEAVY           a bucket of the row sort with more keys than this is written

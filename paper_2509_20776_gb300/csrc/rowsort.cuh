@@ -39,7 +39,7 @@ struct SsCfg {
   static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
   static_assert(B % 32 == 0 && B * MINB <= 2048, "whole warps, resident CTAs");
 };
-using SsTile = SsCfg<128, 1024, true, 8>;   // tiles of rows of at most 512 entries
+using SsTile = SsCfg<128, 1024, true, 9>;   // tiles of rows of at most 512 entries
 using SsTileL = SsCfg<256, 2048, true, 4>;  // tile shape 1: rows of at most 1024 entries
 // single runs of at most 4096 entries: with 4-byte values three CTAs of 384 threads fit
 // an SM (72 KB of shared memory each), with 8-byte values two of 512 (88 KB)
@@ -671,10 +671,11 @@ __global__ void __launch_bounds__(S::B, S::MINB)
 template <class Cfg, class VT>
 __host__ __device__ constexpr size_t ss_smem_bytes() {
   // values, keys in packed and bucket order, counters, bucket and source of each entry;
-  // tiles add the per-row tables, the row-start bitmap and the row of each entry
+  // tiles add the per-row tables and the row-start bitmap (an entry's row is its rank
+  // among the row starts, recomputed where needed: no per-entry row array, which keeps
+  // a tile CTA small enough for 9 per SM)
   return size_t(Cfg::CAP) * (sizeof(VT) + 4 * 2 + 2 * 2) + size_t(Cfg::CNT) * 4 +
-         (Cfg::kTiles ? size_t(Cfg::CAP) * 2 + size_t(Cfg::ROWS) * (4 * 2 + 2 * 2) + size_t(Cfg::WORDS) * 4 * 2
-                      : 0);
+         (Cfg::kTiles ? size_t(Cfg::ROWS) * (4 * 2 + 2 * 2) + size_t(Cfg::WORDS) * 4 * 2 : 0);
 }
 
 // In-place exclusive sum of a[0, n); thread t owns the ceil(n / B) consecutive entries
@@ -725,8 +726,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
   float* rsc = reinterpret_cast<float*>(rdel + ROWS);        // per row: bucket scale
   uint32_t* bits = rdel + 2 * ROWS;   // row starts
   uint32_t* wpre = bits + WORDS;      // row starts in earlier words
-  uint16_t* rowk = reinterpret_cast<uint16_t*>(wpre + WORDS);  // row of each packed entry
-  uint16_t* rps = rowk + CAP;         // per row: packed start
+  uint16_t* rps = reinterpret_cast<uint16_t*>(wpre + WORDS);  // per row: packed start
   uint16_t* rnm = rps + ROWS;         // per row: last bucket
   __shared__ uint32_t tmp32[B / 32 + 1];
   __shared__ uint32_t s_min, s_max;
@@ -891,7 +891,6 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
           skey[x] = key;
           sval[x] = vv[u];
           slot[x] = uint16_t(sl);
-          rowk[x] = uint16_t(kr[u]);
           atomicAdd(&cnt[sl], 1u);
         }
       }
@@ -967,7 +966,11 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
       const uint32_t x = tidx[p], k = tkey[p];
       const uint32_t s = slot[x];
       const uint32_t end = cnt[s], start = s ? cnt[s - 1] : 0u;
-      const uint32_t rd = Cfg::kTiles ? rdel[rowk[x]] : 0u;
+      uint32_t rd = 0u;
+      if constexpr (Cfg::kTiles) {  // the entry's row: the row starts at or before x
+        const int w = int(x >> 5);
+        rd = rdel[wpre[w] + __popc(bits[w] & (0xFFFFFFFFu >> (31 - (x & 31)))) - 1u];
+      }
       if (hv && end - start > uint32_t(heavy)) {
         st_stream(oc + rd + p, CI(k));
         st_stream(ov + rd + p, sval[x]);
