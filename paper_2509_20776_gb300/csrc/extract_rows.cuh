@@ -347,9 +347,7 @@ __device__ __forceinline__ void x_queue(long long o, long long k, int key_bits, 
                                         DevStatus* st) {
   if (k <= 1) return;
   if (k <= SS_RUN_MAX) {
-    const unsigned q = atomicAdd(fin_n, 1u);
-    if (q < fin_cap) fin[q] = FinalEntry{o, k, BUF_OUT, 0};
-    else dev_fail(st, SP_ERR_INTERNAL, -27);
+    queue_run(fin, fin_n, fin_cap, FinalEntry{o, k, BUF_OUT, 0}, st, -27);
   } else {
     queue_huge(huge, huge_n, huge_cap, HugeEntry{o, k, 0u, key_bits, BUF_OUT, 0}, st, -28);
   }

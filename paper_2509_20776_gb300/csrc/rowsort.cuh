@@ -29,11 +29,12 @@ constexpr int SS_PASSES = 3;                   // passes over queued heavy bucke
 // SM; a tile holds the rows whose partition coordinate starts in a window of
 // CP = CAP / 2, so at most ROWS = CP / SS_ROW_W rows (one thread each) of at most CP
 // entries.  A single run of L entries uses at most ss_nb(L) <= CAP / 2 bucket counters.
-template <int BLOCK_, int CAP_, bool TILES_, int MINB_>
+template <int BLOCK_, int CAP_, bool TILES_, int MINB_, bool BACK_ = false>
 struct SsCfg {
   static constexpr int B = BLOCK_, CAP = CAP_, CP = CAP_ / 2, ROWS = CP / SS_ROW_W, MINB = MINB_;
   static constexpr int WORDS = CAP_ / 32;  // row-start bitmap words
   static constexpr bool kTiles = TILES_;   // items are tiles (else: single runs)
+  static constexpr bool kBack = BACK_;     // runs: taken from the back of the run list
   static constexpr int CNT = TILES_ ? CAP_ : CAP_ / 2;  // bucket counters
   static_assert(!TILES_ || ROWS <= B, "one thread per row of a tile");
   static_assert(WORDS % 32 == 0, "one warp scans the bitmap");
@@ -45,6 +46,9 @@ using SsTileL = SsCfg<256, 2048, true, 4>;  // tile shape 1: rows of at most 102
 // an SM (72 KB of shared memory each), with 8-byte values two of 512 (88 KB)
 template <class VT>
 using SsRunT = std::conditional_t<sizeof(VT) == 4, SsCfg<384, 4096, false, 3>, SsCfg<512, 4096, false, 2>>;
+// runs of at most 1024 entries (the back of the run list): 128 threads, 8 CTAs per SM
+using SsRunS = SsCfg<128, 1024, false, 8, true>;
+constexpr int SS_SMALL_RUN = SsRunS::CAP;
 constexpr int SS_TILE_MAX = SsTile::CP;  // longest row a tile accepts (the smaller tile shape)
 constexpr int SS_RUN_MAX = 4096;         // longest row sorted alone
 static_assert(SsRunT<uint32_t>::CAP == SS_RUN_MAX && SsRunT<unsigned long long>::CAP == SS_RUN_MAX,
@@ -60,6 +64,17 @@ struct FinalEntry {  // a run of at most SS_RUN_MAX entries left to sort in plac
   int buf;
   int pad;
 };
+// The run list is filled from both ends: n[0] counts the runs at its front, n[1] the runs
+// of at most SS_SMALL_RUN entries at its back (k_seg_sort<SsRunS>, small CTAs, sorts those;
+// k_seg_sort<SsRunT> the front).  cap bounds all the runs a pass queues, so the two ends
+// never meet.
+__device__ __forceinline__ void queue_run(FinalEntry* list, unsigned* n, long long cap, const FinalEntry& e,
+                                          DevStatus* st, long long err) {
+  const bool small = e.len <= SS_SMALL_RUN;
+  const unsigned q = atomicAdd(n + (small ? 1 : 0), 1u);
+  if (q < cap) list[small ? cap - 1 - q : q] = e;
+  else dev_fail(st, SP_ERR_INTERNAL, err);
+}
 struct HugeEntry {  // a run longer than SS_RUN_MAX; coarse split: keys in [lo, lo + 2^wb)
   long long off;
   long long len;
@@ -146,9 +161,7 @@ struct RowsPartition {
     for (long long k = (o0 + GC_CH - 1) / GC_CH; k <= k_hi; ++k) chunk_first[k] = r;
     if (classify && L > tmax) {
       if (L <= SS_RUN_MAX) {
-        const unsigned q = atomicAdd(fin_n, 1u);
-        if (q < fin_cap) fin[q] = FinalEntry{o0, L, BUF_OUT, 0};
-        else dev_fail(st, SP_ERR_INTERNAL, -15);
+        queue_run(fin, fin_n, fin_cap, FinalEntry{o0, L, BUF_OUT, 0}, st, -15);
       } else {
         queue_huge(huge, huge_n, huge_cap, HugeEntry{o0, L, 0u, key_bits, BUF_OUT, 0}, st, -16);
       }
@@ -551,9 +564,7 @@ __global__ void __launch_bounds__(S::B, S::MINB)
       const uint32_t sb = hist[x], cc = bend(x) - sb;
       if (big) {
         if (cc <= uint32_t(SS_RUN_MAX)) {
-          const unsigned q = atomicAdd(fin_n, 1u);
-          if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, cc, dbuf, 0};
-          else dev_fail(st, SP_ERR_INTERNAL, -6);
+          queue_run(fin, fin_n, fin_cap, FinalEntry{g0 + sb, cc, dbuf, 0}, st, -6);
         } else {
           const unsigned q = atomicAdd(nxt_n, 1u);  // the fine split finds its key range itself
           if (q < nxt_cap) nxt[q] = HugeEntry{g0 + sb, cc, 0u, 0, dbuf, 0};
@@ -563,9 +574,7 @@ __global__ void __launch_bounds__(S::B, S::MINB)
         // reversed index of x+1 holds max over buckets >= x+1 of (L - start) -> min start
         const uint32_t nx = (x + 1 < NBM) ? nxb[NBM - 1 - (x + 1)] : 0u;
         const uint32_t end = nx ? uint32_t(L) - nx : uint32_t(L);
-        const unsigned q = atomicAdd(fin_n, 1u);
-        if (q < fin_cap) fin[q] = FinalEntry{g0 + sb, (long long)(end - sb), dbuf, 0};
-        else dev_fail(st, SP_ERR_INTERNAL, -6);
+        queue_run(fin, fin_n, fin_cap, FinalEntry{g0 + sb, (long long)(end - sb), dbuf, 0}, st, -6);
       }
     }
     __syncthreads();
@@ -698,9 +707,10 @@ __device__ __forceinline__ void ss_excl_sum(uint32_t* a, int n, uint32_t* tmp) {
   __syncthreads();
 }
 
-// Work items: tiles [0, *ntiles) of the partition, then runs fin[0, *fin_n) (rows of
-// SS_TILE_MAX < L <= SS_RUN_MAX entries, in the output arrays, and k_split's runs, in
-// the output or in the temporary arrays).  Every item's entries are loaded into shared memory
+// Work items: tiles [0, *ntiles) of the partition, or runs fin[0, *fin_n) (from the
+// back of the list, fin[cap - 1 - k], with Cfg::kBack): rows of SS_TILE_MAX < L <=
+// SS_RUN_MAX entries, in the output arrays, and k_split's runs, in the output or in the
+// temporary arrays.  Every item's entries are loaded into shared memory
 // before any of them is written back, so a run is sorted in place.  A bucket of more
 // than SS_HEAVY keys (skewed keys) is written in bucket order and queued in hv[] as a
 // run for a later pass, which buckets it over its own key range; without hv (the last
@@ -762,7 +772,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
       pf1 = tile_first[blockIdx.x + 1];
       prefetch_rows(true);
     } else {
-      pfe = fin[blockIdx.x];
+      pfe = fin[Cfg::kBack ? fin_cap - 1 - (long long)blockIdx.x : (long long)blockIdx.x];
     }
   }
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -840,7 +850,7 @@ __global__ void __launch_bounds__(Cfg::B, Cfg::MINB)
       prefetch_rows(nx < nitems);  // the next tile's row pointers arrive during this sort
     } else {
       const FinalEntry fe = pfe;
-      if (nx < nitems) pfe = fin[nx];
+      if (nx < nitems) pfe = fin[Cfg::kBack ? fin_cap - 1 - nx : nx];
       base = fe.off;
       buf = fe.buf;
       E = int(fe.len);
@@ -997,7 +1007,7 @@ struct RowsWs {
   long long* tile_first = nullptr;
   long long* chunk_first = nullptr;
   long long* ntiles = nullptr;
-  unsigned* counters = nullptr;  // [0] fin_n [1] spare [2] spare [3..4] tickets [5] spare
+  unsigned* counters = nullptr;  // [0..1] run list counts (front, back) [2] spare [3..4] tickets [5] spare
                                  // [6..7] heavy-run counts [8..9] zero (no tiles)
                                  // [10..11] huge list counts [12..13] nxt list counts
   FinalEntry* fin = nullptr;
@@ -1102,8 +1112,8 @@ sp_status split_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, CI* out_col
   return SP_OK;
 }
 
-// Sorts the runs queued in w.fin (counter 0), then the heavy buckets queued by any sort
-// pass (counters 6, 7), in place.
+// Sorts the runs queued in w.fin (counters 0 and 1: its two ends), then the heavy buckets
+// queued by any sort pass (counters 6, 7), in place.
 template <class CI, class VT>
 sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, CI* out_col, VT* out_val) {
   const int nsm = ctx->num_sms;
@@ -1111,7 +1121,16 @@ sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, 
   VT* tval = static_cast<VT*>(w.tval);
   const long long* no_tiles = reinterpret_cast<const long long*>(w.counters + 8);
   using SsRun = SsRunT<VT>;
-  constexpr size_t rsm = ss_smem_bytes<SsRun, VT>();
+  constexpr size_t rsm = ss_smem_bytes<SsRun, VT>(), ssm = ss_smem_bytes<SsRunS, VT>();
+  // the runs of at most SS_SMALL_RUN entries (the back of the list), then the others
+  SP_CUDA(set_smem(k_seg_sort<SsRunS, CI, VT>, ssm));
+  {
+    SP_PHASE(SP_PHASE_LONG);
+    k_seg_sort<SsRunS, CI, VT><<<SsRunS::MINB * nsm, SsRunS::B, ssm, s>>>(
+        nullptr, nullptr, no_tiles, w.fin, w.counters + 1, w.fin_cap, w.tkey, tval, out_col, out_val, w.hv[0],
+        w.counters + 6, w.hv_cap, key_bits, heavy, ctx->dstatus);
+  }
+  SP_CUDA(cudaGetLastError());
   SP_CUDA(set_smem(k_seg_sort<SsRun, CI, VT>, rsm));
   {
     SP_PHASE(SP_PHASE_LONG);
@@ -1136,7 +1155,7 @@ sp_status sort_runs(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, 
   return SP_OK;
 }
 
-// Sorts in place the rows a caller queued itself in w.fin / w.huge (counter 0 and
+// Sorts in place the rows a caller queued itself in w.fin / w.huge (counters 0, 1 and
 // w.huge_n(), zeroed with the rest of w.counters before the caller queued them).
 template <class CI, class VT>
 sp_status sort_queued(sp_ctx* ctx, cudaStream_t s, const RowsWs& w, int key_bits, CI* out_col, VT* out_val) {
