@@ -1,5 +1,6 @@
 """Full-size workloads on the GPU, checked against the oracle on sampled rows plus
-properties that hold at any size (row pointer, canonical rows, nnz, round trips).
+properties that hold at any size (row pointer, canonical rows, nnz, round trips), and one
+workload of 46 M entries compared whole.
 
 The sampled rows always include the longest output rows (the hub rows that go through
 the huge-row kernel), the first and last rows and a seeded random set.
@@ -10,6 +11,7 @@ import torch
 
 import oracle
 import synth
+from helpers import assert_same, to_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +94,28 @@ def test_cfg2_permute_scale25(ctx):
             assert np.array_equal(gc, wc), f"{name} row {i}"
             assert np.array_equal(gv.view(np.uint32), wv.view(np.uint32)), f"{name} row {i}"
         del B
+
+
+def test_whole_arrays_rmat20(ctx):
+    """Every output array compared whole with the oracle (not sampled rows) at a size whose
+    paths are the scale paths: R-MAT scale 20, edge factor 24 (46 M entries), with a hub row
+    of 84 K entries (taken first from the back of the key-range split's list), 1351 rows
+    longer than 4096 entries (the split, beside the tile sort), runs of both run
+    configurations, and the extraction of half the rows and columns."""
+    A = synth.rmat_csr(20, 24, seed=3, symmetrize=True, value_kind="f32u01", device="cuda")
+    n = A.nrows
+    L = A.rowptr[1:] - A.rowptr[:-1]
+    assert int(L.max()) >= 65536 and int((L > 4096).sum()) > 1000, "needs hub and split rows"
+    Ao = to_oracle(A)
+    p = synth.random_permutation(n, 3, 0, device="cuda")
+    q = synth.random_permutation(n, 3, 1, device="cuda")
+    B = ctx.sp_permute(dev_csr(A), p, q)
+    assert_same(B, oracle.permute(Ao, p.cpu().numpy(), q.cpu().numpy()), "P A Q^T, scale 20")
+    del B
+    I = synth.random_subset(n, n // 2, 3, 2, device="cuda")
+    J = synth.random_subset(n, n // 2, 3, 3, device="cuda")
+    E = ctx.sp_extract(dev_csr(A), I, J)
+    assert_same(E, oracle.extract(Ao, I.cpu().numpy(), J.cpu().numpy()), "A(I, J), scale 20")
 
 
 def test_cfg3_extract_er_2pow26(ctx):
